@@ -1,0 +1,149 @@
+/*
+ * Exact vertex cover on one GB300 (sm_103a): C ABI.
+ *
+ * The solver is the component-aware parallel branch-and-reduce of
+ * "Faster Vertex Cover Algorithms on GPUs with Component-Aware Parallel
+ * Branching" (arXiv 2512.18334):
+ *   - the graph is reduced at the root and an induced subgraph is built on
+ *     the device (Section 4.2),
+ *   - persistent workers pop search-tree nodes (degree arrays of the induced
+ *     subgraph, Section 4.1) from a private stack or a shared worklist
+ *     (Section 2.3), apply the degree-one, degree-two-triangle and high-degree
+ *     rules (Section 2.2), prune with the stopping condition (Algorithm 1),
+ *     find connected components (Section 3.2) and branch on them
+ *     (Algorithm 2, Section 3.3) through a component-branch registry whose
+ *     last descendant aggregates the result (Section 3.3); cliques and
+ *     chordless cycles are closed directly (Section 3.4).
+ *
+ * Input graphs are simple and undirected, in CSR form:
+ *   row_ptr  int32[n + 1], row_ptr[0] = 0, non-decreasing
+ *   col      int32[row_ptr[n]], each row sorted strictly ascending,
+ *            symmetric (v in row u iff u in row v), no self-loops.
+ * Anything else is rejected with VC_EINVAL (checked on the device).
+ *
+ * Cover outputs are vertex ids of the caller's numbering, sorted ascending,
+ * in caller-owned host arrays of capacity n.  Every function returns VC_OK
+ * (0) or a negative status; vc_strerror() names it.
+ *
+ * Threading: a vc_graph handle owns device memory and a CUDA stream binding;
+ * it is not thread-safe.  Use one handle per host thread / stream.
+ */
+#ifndef VC_GB300_H
+#define VC_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define VC_OK 0
+#define VC_EINVAL (-1)     /* malformed CSR, bad argument                        */
+#define VC_ENOMEM (-2)     /* a device or pinned-host allocation failed          */
+#define VC_ECAPACITY (-3)  /* stack, worklist or registry full after retries     */
+#define VC_ETIMEOUT (-4)   /* a bounded device wait expired (no progress)        */
+#define VC_ECUDA (-5)      /* a CUDA runtime call failed                         */
+#define VC_EBUDGET (-6)    /* node budget exhausted before the search finished   */
+
+typedef struct vc_graph vc_graph;
+
+/* Solver options.  Zero-initialised fields mean "automatic / default";
+ * vc_options_default() fills the defaults explicitly. */
+typedef struct vc_options {
+    int32_t use_components;   /* 1: branch on components (Algorithm 2); 0: Algorithm 1 */
+    int32_t team;             /* threads per worker: 0 auto, 32 (one warp per
+                                 worker) or 128/256/512/1024 (one block per worker) */
+    int32_t dtype_bytes;      /* degree-array entry size: 0 auto, 1, 2 or 4 (Section 4.4) */
+    int32_t stack_depth;      /* private stack slots per worker, 0 auto             */
+    int32_t worklist_capacity;/* shared worklist slots, 0 auto                      */
+    int32_t registry_capacity;/* component-branch registry entries, 0 auto          */
+    int32_t load_balance;     /* 1: offload to the shared worklist; 0: only the
+                                 root is shared, workers keep what they create      */
+    int32_t idle_timeout_ms;  /* abort with VC_ETIMEOUT after this long without
+                                 any worker making progress; 0 = 60000              */
+    int64_t node_budget;      /* 0 = unlimited; else stop with VC_EBUDGET           */
+} vc_options;
+
+/* What a solve did.  All counters are totals over the launch. */
+typedef struct vc_stats {
+    int64_t nodes;              /* search-tree nodes processed                      */
+    int64_t component_branches; /* nodes that branched on >= 2 components           */
+    int64_t leaves;             /* nodes whose graph had no edges left              */
+    int64_t pruned;             /* nodes cut by the stopping condition              */
+    int64_t offloaded;          /* nodes pushed to the shared worklist              */
+    int64_t trivial_components; /* components closed by the clique / cycle rules    */
+    int64_t comp_hist[16];      /* branches on c components, c = 2..16 (16 = >=16)  */
+    int32_t n;                  /* vertices of the input graph                      */
+    int32_t n_induced;          /* vertices of the induced subgraph searched        */
+    int32_t m_induced;          /* edges of the induced subgraph                    */
+    int32_t forced;             /* vertices put in the cover by the root reduction  */
+    int32_t greedy_size;        /* initial upper bound (whole graph)                */
+    int32_t dtype_bytes;        /* degree-array entry size used                     */
+    int32_t team;               /* threads per worker used                          */
+    int32_t workers;            /* persistent workers launched                      */
+    int32_t max_stack;          /* deepest private stack seen                       */
+    int32_t reserved;
+    double ms_root;             /* root reduction + induced subgraph (device)       */
+    double ms_search;           /* persistent search kernel (device)                */
+    double ms_total;            /* whole call, host wall clock                      */
+} vc_stats;
+
+/* Fill *opt with the defaults. */
+int vc_options_default(vc_options *opt);
+
+/* Copy a CSR graph from HOST memory to the device and return a handle.
+ * `cuda_stream` is a cudaStream_t (NULL = the legacy default stream); every
+ * later call on the handle runs on it.  The caller keeps ownership of its
+ * arrays.  The graph is validated here (VC_EINVAL on a malformed CSR).
+ * Cost: one host-to-device copy of (n + 1 + row_ptr[n]) int32 values. */
+int vc_load_csr(int32_t n, const int32_t *row_ptr, const int32_t *col,
+                void *cuda_stream, vc_graph **out);
+
+/* As vc_load_csr, but row_ptr / col are DEVICE pointers (already resident in
+ * HBM); they are copied device-to-device so the caller may free them. */
+int vc_load_csr_device(int32_t n, const int32_t *d_row_ptr, const int32_t *d_col,
+                       void *cuda_stream, vc_graph **out);
+
+/* Minimum vertex cover (MVC, Section 2.1).  Writes the minimum size to
+ * *cover_size and, when `cover` is non-NULL, a minimum cover (ascending
+ * original ids, capacity n) and its length to *cover_len.  `opt` and `stats`
+ * may be NULL. */
+int vc_solve_min(vc_graph *g, const vc_options *opt, int32_t *cover_size,
+                 int32_t *cover, int32_t *cover_len, vc_stats *stats);
+
+/* Parameterized vertex cover (PVC, Section 2.1): is there a cover of size at
+ * most k?  *is_yes = 1 with a cover of size <= k (when `cover` is non-NULL),
+ * or *is_yes = 0 and *cover_len = 0.  k < 0 is VC_EINVAL; k = 0 is "yes iff
+ * the graph has no edge". */
+int vc_solve_k(vc_graph *g, int32_t k, const vc_options *opt, int32_t *is_yes,
+               int32_t *cover, int32_t *cover_len, vc_stats *stats);
+
+/* Many queries in one root launch and one persistent search launch (a
+ * build extension; the paper solves one graph per launch).  Query i is graph
+ * graphs[i] with ks == NULL or ks[i] < 0 meaning "minimum cover" and
+ * ks[i] >= 0 meaning "is there a cover of size <= ks[i]?".  A graph may
+ * appear in several queries (e.g. at two values of k).  Per query:
+ *   out_size[i]    minimum size (MVC), size of the cover found (PVC yes) or -1
+ *   out_yes[i]     PVC answer (1 for MVC)
+ *   out_status[i]  VC_OK or the status that stopped it
+ *   covers[i]      (nullable array, nullable entries) host array of capacity
+ *                  n_i receiving the cover, ascending original ids
+ *   cover_lens[i]  (nullable) its length
+ * The launch runs on graphs[0]'s stream with graphs[0]'s workspace.
+ * `stats` (nullable) sums over the batch. */
+int vc_solve_batch(int32_t count, vc_graph *const *graphs, const int32_t *ks,
+                   const vc_options *opt, int32_t *out_size, int32_t *out_yes,
+                   int32_t *out_status, int32_t *const *covers, int32_t *cover_lens,
+                   vc_stats *stats);
+
+/* Release the handle and all device memory it owns.  NULL is a no-op. */
+void vc_free(vc_graph *g);
+
+/* Static string naming a status code. */
+const char *vc_strerror(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* VC_GB300_H */

@@ -1,0 +1,157 @@
+"""Exact vertex cover on one GB300: Python binding of libvc_gb300.so.
+
+Argument marshalling only; every step of the solve runs in the CUDA library
+(see ``include/vc_gb300.h``).  The library must be built first
+(``python -m paper_2512_18334_gb300.build`` or ``__graft_entry__.build()``);
+importing this package never falls back to anything else.
+
+    import paper_2512_18334_gb300 as vc
+    g = vc.Graph.from_csr(row_ptr, col)          # host numpy arrays
+    size, cover, stats = vc.solve_min(g)
+    yes, cover, stats = vc.solve_k(g, k)
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import _lib as _L
+from ._lib import (VC_OK, VC_EINVAL, VC_ENOMEM, VC_ECAPACITY, VC_ETIMEOUT, VC_ECUDA, VC_EBUDGET,
+                   VcError, Options, Stats, lib_path)
+
+__all__ = [
+    "Graph", "solve_min", "solve_k", "solve_batch", "options", "VcError", "lib_path",
+    "VC_OK", "VC_EINVAL", "VC_ENOMEM", "VC_ECAPACITY", "VC_ETIMEOUT", "VC_ECUDA", "VC_EBUDGET",
+]
+
+
+def _stream_handle(stream) -> ctypes.c_void_p:
+    if stream is None:
+        return ctypes.c_void_p(0)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(int(stream.cuda_stream))   # torch.cuda.Stream
+
+
+def options(**kw) -> Options:
+    """vc_options with the library defaults, overridden by keyword."""
+    o = Options()
+    _L.check(_L.lib().vc_options_default(ctypes.byref(o)))
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise TypeError(f"unknown option {k}")
+        setattr(o, k, v)
+    return o
+
+
+class Graph:
+    """A CSR graph resident on the device (owns a vc_graph handle)."""
+
+    def __init__(self, handle, n: int, m2: int):
+        self._h = handle
+        self.n = n
+        self.m2 = m2
+
+    @classmethod
+    def from_csr(cls, row_ptr, col, stream=None) -> "Graph":
+        """Copy host CSR arrays (int32) to the device (vc_load_csr)."""
+        rp = np.ascontiguousarray(row_ptr, dtype=np.int32)
+        c = np.ascontiguousarray(col, dtype=np.int32)
+        n = int(rp.size - 1)
+        h = ctypes.c_void_p()
+        _L.check(_L.lib().vc_load_csr(n, rp.ctypes.data_as(ctypes.c_void_p),
+                                      c.ctypes.data_as(ctypes.c_void_p) if c.size else None,
+                                      _stream_handle(stream), ctypes.byref(h)))
+        return cls(h, n, int(rp[-1]) if n >= 0 else 0)
+
+    @classmethod
+    def from_device(cls, row_ptr, col, stream=None) -> "Graph":
+        """CSR already in HBM: torch int32 CUDA tensors (vc_load_csr_device)."""
+        if row_ptr.dtype.itemsize != 4 or col.dtype.itemsize != 4:
+            raise TypeError("row_ptr and col must be int32")
+        if not (row_ptr.is_cuda and col.is_cuda):
+            raise TypeError("from_device expects CUDA tensors")
+        rp = row_ptr.contiguous()
+        c = col.contiguous()
+        n = int(rp.numel() - 1)
+        h = ctypes.c_void_p()
+        _L.check(_L.lib().vc_load_csr_device(n, ctypes.c_void_p(rp.data_ptr()),
+                                             ctypes.c_void_p(c.data_ptr()) if c.numel() else None,
+                                             _stream_handle(stream), ctypes.byref(h)))
+        return cls(h, n, int(c.numel()))
+
+    def close(self):
+        if self._h is not None and self._h.value:
+            _L.lib().vc_free(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _opts(opts, kw):
+    if opts is None:
+        return options(**kw)
+    if kw:
+        raise TypeError("pass either an Options object or keywords")
+    return opts
+
+
+def solve_min(g: Graph, opts: Options | None = None, want_cover: bool = True, **kw):
+    """Minimum vertex cover: (size, cover int32 array or None, stats dict)."""
+    o = _opts(opts, kw)
+    size = ctypes.c_int32(-1)
+    cover = np.zeros(max(g.n, 1), np.int32)
+    clen = ctypes.c_int32(0)
+    st = Stats()
+    _L.check(_L.lib().vc_solve_min(g._h, ctypes.byref(o), ctypes.byref(size),
+                                   cover.ctypes.data_as(ctypes.c_void_p) if want_cover else None,
+                                   ctypes.byref(clen), ctypes.byref(st)))
+    return size.value, (cover[:clen.value].copy() if want_cover else None), st.to_dict()
+
+
+def solve_k(g: Graph, k: int, opts: Options | None = None, want_cover: bool = True, **kw):
+    """Is there a cover of size <= k?  (yes, cover or None, stats dict)."""
+    o = _opts(opts, kw)
+    yes = ctypes.c_int32(0)
+    cover = np.zeros(max(g.n, 1), np.int32)
+    clen = ctypes.c_int32(0)
+    st = Stats()
+    _L.check(_L.lib().vc_solve_k(g._h, int(k), ctypes.byref(o), ctypes.byref(yes),
+                                 cover.ctypes.data_as(ctypes.c_void_p) if want_cover else None,
+                                 ctypes.byref(clen), ctypes.byref(st)))
+    return bool(yes.value), (cover[:clen.value].copy() if want_cover and yes.value else None), st.to_dict()
+
+
+def solve_batch(graphs, ks=None, opts: Options | None = None, want_covers: bool = True,
+                raise_on_error: bool = True, **kw):
+    """Many queries in one launch.  ks[i] < 0 (or ks None) asks for the minimum
+    cover of graphs[i]; ks[i] >= 0 asks whether a cover <= ks[i] exists.
+    Returns (sizes, yes, status, covers list or None, stats dict)."""
+    o = _opts(opts, kw)
+    count = len(graphs)
+    arr = (ctypes.c_void_p * count)(*[gr._h for gr in graphs])
+    ks_arr = None
+    if ks is not None:
+        ks_np = np.ascontiguousarray(ks, dtype=np.int32)
+        ks_arr = ks_np.ctypes.data_as(ctypes.c_void_p)
+    sizes = np.zeros(count, np.int32)
+    yes = np.zeros(count, np.int32)
+    status = np.zeros(count, np.int32)
+    lens = np.zeros(count, np.int32)
+    bufs = [np.zeros(max(gr.n, 1), np.int32) for gr in graphs] if want_covers else None
+    cov_ptrs = (ctypes.c_void_p * count)(*[b.ctypes.data for b in bufs]) if want_covers else None
+    st = Stats()
+    rc = _L.lib().vc_solve_batch(count, arr, ks_arr, ctypes.byref(o),
+                                 sizes.ctypes.data_as(ctypes.c_void_p), yes.ctypes.data_as(ctypes.c_void_p),
+                                 status.ctypes.data_as(ctypes.c_void_p), cov_ptrs,
+                                 lens.ctypes.data_as(ctypes.c_void_p), ctypes.byref(st))
+    if raise_on_error:
+        _L.check(rc)
+    covers = [b[:l].copy() for b, l in zip(bufs, lens)] if want_covers else None
+    return sizes, yes.astype(bool), status, covers, st.to_dict()

@@ -1,0 +1,121 @@
+"""ctypes declarations of include/vc_gb300.h.  Loads the in-tree library and
+fails loudly when it is missing."""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_FILE = os.path.join(HERE, "libvc_gb300.so")
+
+VC_OK = 0
+VC_EINVAL = -1
+VC_ENOMEM = -2
+VC_ECAPACITY = -3
+VC_ETIMEOUT = -4
+VC_ECUDA = -5
+VC_EBUDGET = -6
+
+_lock = threading.Lock()
+_lib = None
+
+
+class VcError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{msg} (status {status})")
+        self.status = status
+
+
+class Options(ctypes.Structure):
+    _fields_ = [
+        ("use_components", ctypes.c_int32),
+        ("team", ctypes.c_int32),
+        ("dtype_bytes", ctypes.c_int32),
+        ("stack_depth", ctypes.c_int32),
+        ("worklist_capacity", ctypes.c_int32),
+        ("registry_capacity", ctypes.c_int32),
+        ("load_balance", ctypes.c_int32),
+        ("idle_timeout_ms", ctypes.c_int32),
+        ("node_budget", ctypes.c_int64),
+    ]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [
+        ("nodes", ctypes.c_int64),
+        ("component_branches", ctypes.c_int64),
+        ("leaves", ctypes.c_int64),
+        ("pruned", ctypes.c_int64),
+        ("offloaded", ctypes.c_int64),
+        ("trivial_components", ctypes.c_int64),
+        ("comp_hist", ctypes.c_int64 * 16),
+        ("n", ctypes.c_int32),
+        ("n_induced", ctypes.c_int32),
+        ("m_induced", ctypes.c_int32),
+        ("forced", ctypes.c_int32),
+        ("greedy_size", ctypes.c_int32),
+        ("dtype_bytes", ctypes.c_int32),
+        ("team", ctypes.c_int32),
+        ("workers", ctypes.c_int32),
+        ("max_stack", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
+        ("ms_root", ctypes.c_double),
+        ("ms_search", ctypes.c_double),
+        ("ms_total", ctypes.c_double),
+    ]
+
+    def to_dict(self) -> dict:
+        d = {}
+        for name, _ in self._fields_:
+            v = getattr(self, name)
+            if name == "comp_hist":
+                d[name] = {i + 2: int(v[i]) for i in range(16) if v[i]}
+            elif name != "reserved":
+                d[name] = v
+        return d
+
+
+# Every symbol the header declares, with its ctypes signature.
+_P = ctypes.c_void_p
+_I = ctypes.c_int32
+SIGNATURES = {
+    "vc_options_default": (ctypes.c_int, [_P]),
+    "vc_load_csr": (ctypes.c_int, [_I, _P, _P, _P, _P]),
+    "vc_load_csr_device": (ctypes.c_int, [_I, _P, _P, _P, _P]),
+    "vc_solve_min": (ctypes.c_int, [_P, _P, _P, _P, _P, _P]),
+    "vc_solve_k": (ctypes.c_int, [_P, _I, _P, _P, _P, _P, _P]),
+    "vc_solve_batch": (ctypes.c_int, [_I, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
+    "vc_free": (None, [_P]),
+    "vc_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+}
+
+
+def lib_path() -> str:
+    return _LIB_FILE
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(_LIB_FILE):
+                raise ImportError(
+                    f"{_LIB_FILE} is missing: build it with "
+                    "`python -m paper_2512_18334_gb300.build` (there is no fallback)")
+            L = ctypes.CDLL(_LIB_FILE)
+            for name, (res, args) in SIGNATURES.items():
+                fn = getattr(L, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = L
+        return _lib
+
+
+def strerror(status: int) -> str:
+    return lib().vc_strerror(int(status)).decode()
+
+
+def check(status: int) -> None:
+    if status != VC_OK:
+        raise VcError(int(status), strerror(status))

@@ -1,0 +1,527 @@
+// C ABI of the GB300 vertex-cover solver (declared in include/vc_gb300.h).
+//
+// A solve is three device phases on the handle's stream:
+//   1. root_kernel      one block per query: root reduction, greedy bound,
+//                       induced subgraph (Section 4.2);
+//   2. search_kernel    persistent workers over every query that still needs
+//                       a search (Sections 2.3, 3, 4);
+//   3. finalize_kernel  one block per query: cover in original ids.
+// The host reads the small query descriptors between 1 and 2 to size the
+// search (degree dtype, worker shape, capacities) and once at the end.
+#include <algorithm>
+#include <chrono>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "vc_internal.h"
+
+using namespace vcg;
+
+namespace {
+
+#define VC_CK(call)                                                  \
+    do {                                                             \
+        cudaError_t e_ = (call);                                     \
+        if (e_ != cudaSuccess) {                                     \
+            last_cuda_error() = e_;                                  \
+            return e_ == cudaErrorMemoryAllocation ? VC_ENOMEM : VC_ECUDA; \
+        }                                                            \
+    } while (0)
+
+cudaError_t &last_cuda_error()
+{
+    static thread_local cudaError_t e = cudaSuccess;
+    return e;
+}
+
+// Growable device buffer.
+struct DevBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+    int ensure(size_t want)
+    {
+        if (want <= bytes) return VC_OK;
+        if (p) cudaFree(p);
+        p = nullptr;
+        bytes = 0;
+        if (cudaMalloc(&p, want) != cudaSuccess) return VC_ENOMEM;
+        bytes = want;
+        return VC_OK;
+    }
+    void release()
+    {
+        if (p) cudaFree(p);
+        p = nullptr;
+        bytes = 0;
+    }
+    template <class X>
+    X *as() const { return (X *)p; }
+};
+
+struct HostBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+    int ensure(size_t want)
+    {
+        if (want <= bytes) return VC_OK;
+        if (p) cudaFreeHost(p);
+        p = nullptr;
+        bytes = 0;
+        if (cudaMallocHost(&p, want) != cudaSuccess) return VC_ENOMEM;
+        bytes = want;
+        return VC_OK;
+    }
+    void release()
+    {
+        if (p) cudaFreeHost(p);
+        p = nullptr;
+        bytes = 0;
+    }
+};
+
+// Search workspace: node slots, worklist, registry, scratch, control block.
+struct Workspace {
+    DevBuf stack, wl, wl_seq, reg, reg_words, comp_scratch, ctl, root_slot, queries, qscratch;
+    HostBuf hq, hctl, hcov;
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    int init()
+    {
+        for (auto &e : ev)
+            if (!e && cudaEventCreate(&e) != cudaSuccess) return VC_ECUDA;
+        return VC_OK;
+    }
+    void release()
+    {
+        for (DevBuf *b : {&stack, &wl, &wl_seq, &reg, &reg_words, &comp_scratch, &ctl, &root_slot, &queries,
+                          &qscratch})
+            b->release();
+        hq.release();
+        hctl.release();
+        hcov.release();
+        for (auto &e : ev)
+            if (e) { cudaEventDestroy(e); e = nullptr; }
+    }
+};
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// Per-query device scratch of the root phase and the final answer.
+size_t query_scratch_bytes(int n, int m2)
+{
+    const size_t ni = (size_t)(n > 0 ? n : 1);
+    return 6 * align256(ni * 4)                   // deg aux fr0 fr1 flag forced_list
+           + 2 * align256(ni)                     // st cover_flags
+           + align256((ni + 1) * 4)               // rp2
+           + align256((size_t)(m2 > 0 ? m2 : 1) * 4)  // col2
+           + 2 * align256(ni * 4);                // orig cover_list
+}
+
+void carve_query_scratch(QueryDesc &Q, char *base)
+{
+    const size_t ni = (size_t)(Q.n > 0 ? Q.n : 1);
+    char *p = base;
+    auto take = [&](size_t b) { char *r = p; p += align256(b); return r; };
+    Q.deg = (int *)take(ni * 4);
+    Q.aux = (int *)take(ni * 4);
+    Q.fr0 = (int *)take(ni * 4);
+    Q.fr1 = (int *)take(ni * 4);
+    Q.flag = (int *)take(ni * 4);
+    Q.forced_list = (int *)take(ni * 4);
+    Q.st = (uint8_t *)take(ni);
+    Q.cover_flags = (uint8_t *)take(ni);
+    Q.rp2 = (int *)take((ni + 1) * 4);
+    Q.col2 = (int *)take((size_t)(Q.m2 > 0 ? Q.m2 : 1) * 4);
+    Q.orig = (int *)take(ni * 4);
+    Q.cover_list = (int *)take(ni * 4);
+}
+
+int next_pow2(int x)
+{
+    int p = 1;
+    while (p < x) p <<= 1;
+    return p;
+}
+
+}  // namespace
+
+struct vc_graph {
+    int device = 0;
+    int sms = 0;
+    cudaStream_t stream = nullptr;
+    int n = 0;
+    int m2 = 0;
+    DevBuf rp, col, err;
+    Workspace ws;
+};
+
+namespace {
+
+struct QueryRef {
+    vc_graph *g;
+    int k;
+};
+
+struct QueryOut {
+    int status, size, yes, cover_len;
+};
+
+// Run a set of queries in one root launch + one persistent search launch.
+// covers (nullable) / cover_lens receive the covers.
+int solve_queries(vc_graph *g0, const std::vector<QueryRef> &qs, const vc_options *opt_in,
+                  std::vector<QueryOut> &out, int32_t *const *covers, int32_t *cover_lens, vc_stats *stats)
+{
+    const auto t_start = std::chrono::steady_clock::now();
+    vc_options opt;
+    vc_options_default(&opt);
+    if (opt_in) {
+        opt = *opt_in;
+        vc_options defaults;
+        vc_options_default(&defaults);
+        if (opt.idle_timeout_ms <= 0) opt.idle_timeout_ms = defaults.idle_timeout_ms;
+    }
+    const int nq = (int)qs.size();
+    out.assign(nq, QueryOut{VC_OK, -1, 0, 0});
+    if (nq == 0) return VC_OK;
+    Workspace &ws = g0->ws;
+    cudaStream_t s = g0->stream;
+    int rc;
+    if ((rc = ws.init()) != VC_OK) return rc;
+
+    // ---- query descriptors + per-query scratch
+    size_t scratch = 0;
+    std::vector<size_t> offs(nq);
+    for (int i = 0; i < nq; i++) {
+        offs[i] = scratch;
+        scratch += query_scratch_bytes(qs[i].g->n, qs[i].g->m2);
+    }
+    if ((rc = ws.qscratch.ensure(scratch)) != VC_OK) return rc;
+    if ((rc = ws.queries.ensure(sizeof(QueryDesc) * nq)) != VC_OK) return rc;
+    if ((rc = ws.hq.ensure(sizeof(QueryDesc) * nq)) != VC_OK) return rc;
+    QueryDesc *hq = (QueryDesc *)ws.hq.p;
+    for (int i = 0; i < nq; i++) {
+        QueryDesc &Q = hq[i];
+        memset(&Q, 0, sizeof(Q));
+        Q.n = qs[i].g->n;
+        Q.m2 = qs[i].g->m2;
+        Q.rp = qs[i].g->rp.as<int>();
+        Q.col = qs[i].g->col.as<int>();
+        Q.k = qs[i].k;
+        Q.status = VC_OK;
+        carve_query_scratch(Q, ws.qscratch.as<char>() + offs[i]);
+    }
+    QueryDesc *dq = ws.queries.as<QueryDesc>();
+    VC_CK(cudaMemcpyAsync(dq, hq, sizeof(QueryDesc) * nq, cudaMemcpyHostToDevice, s));
+
+    // ---- phase 1: root reduction and induced subgraphs
+    VC_CK(cudaEventRecord(ws.ev[0], s));
+    VC_CK(root_run(dq, nq, s));
+    VC_CK(cudaEventRecord(ws.ev[1], s));
+    VC_CK(cudaMemcpyAsync(hq, dq, sizeof(QueryDesc) * nq, cudaMemcpyDeviceToHost, s));
+    VC_CK(cudaStreamSynchronize(s));
+
+    int max_np = 0, max_deg = 0, nroots = 0;
+    std::vector<int> root_slot(nq, -1);
+    for (int i = 0; i < nq; i++) {
+        const QueryDesc &Q = hq[i];
+        if (Q.status != VC_OK || Q.answered || Q.np == 0) continue;
+        root_slot[i] = nroots++;
+        max_np = std::max(max_np, Q.np);
+        max_deg = std::max(max_deg, Q.maxdeg);
+    }
+
+    float ms_search = 0.f;
+    SearchPlan pl{};
+    SearchParams P{};
+    unsigned long long hctl_local[kCtlWords] = {};
+    if (nroots > 0) {
+        // ---- phase 2: size and run the persistent search
+        int dtype = opt.dtype_bytes;
+        const int need = max_deg <= 255 ? 1 : (max_deg <= 65535 ? 2 : 4);
+        if (dtype != 1 && dtype != 2 && dtype != 4) dtype = need;
+        if (dtype < need) dtype = need;
+        const int ncap = (max_np + 16 + 15) / 16 * 16;
+        const int wcap = max_np / 32 + 2;
+        if ((rc = search_plan(dtype, opt.team, ncap, wcap, g0->sms, &pl)) != VC_OK) {
+            if (rc == VC_ECUDA) last_cuda_error() = cudaGetLastError();
+            return rc;
+        }
+        int depth = opt.stack_depth > 0 ? opt.stack_depth : std::min(max_np + 2, 4096);
+        // keep the private stacks within ~24 GB of HBM
+        const size_t stack_budget = (size_t)24 << 30;
+        const size_t per_worker_slot = (size_t)pl.workers * pl.slot_bytes;
+        if ((size_t)depth * per_worker_slot > stack_budget)
+            depth = (int)std::max<size_t>(8, stack_budget / per_worker_slot);
+        int wl_cap = opt.worklist_capacity > 0 ? next_pow2(opt.worklist_capacity)
+                                               : next_pow2(std::max(4 * pl.workers, 1024));
+        wl_cap = std::max(wl_cap, next_pow2(nroots));
+        int reg_cap = opt.registry_capacity > 0 ? opt.registry_capacity
+                                                : std::max(1 << 16, 64 * pl.workers);
+        const size_t reg_word_budget = (size_t)16 << 30;
+        if ((size_t)reg_cap * wcap * 4 > reg_word_budget) reg_cap = (int)(reg_word_budget / ((size_t)wcap * 4));
+        reg_cap += nq;
+
+        if ((rc = ws.stack.ensure((size_t)pl.workers * depth * pl.slot_bytes)) != VC_OK) return rc;
+        if ((rc = ws.wl.ensure((size_t)wl_cap * pl.slot_bytes)) != VC_OK) return rc;
+        if ((rc = ws.wl_seq.ensure((size_t)wl_cap * 4)) != VC_OK) return rc;
+        if ((rc = ws.reg.ensure((size_t)reg_cap * sizeof(RegEntry))) != VC_OK) return rc;
+        if ((rc = ws.reg_words.ensure((size_t)reg_cap * wcap * 4)) != VC_OK) return rc;
+        if ((rc = ws.comp_scratch.ensure((size_t)pl.workers * 5 * ncap * 4)) != VC_OK) return rc;
+        if ((rc = ws.ctl.ensure(kCtlWords * 8)) != VC_OK) return rc;
+        if ((rc = ws.root_slot.ensure((size_t)nq * 4)) != VC_OK) return rc;
+        if ((rc = ws.hctl.ensure(kCtlWords * 8 + (size_t)nq * 4)) != VC_OK) return rc;
+        int *h_root_slot = (int *)((char *)ws.hctl.p + kCtlWords * 8);
+        memcpy(h_root_slot, root_slot.data(), (size_t)nq * 4);
+        VC_CK(cudaMemcpyAsync(ws.root_slot.p, h_root_slot, (size_t)nq * 4, cudaMemcpyHostToDevice, s));
+
+        P.queries = dq;
+        P.nq = nq;
+        P.team = pl.warp_team ? 32 : pl.threads;
+        P.workers = pl.workers;
+        P.ncap = ncap;
+        P.wcap = wcap;
+        P.slot_bytes = pl.slot_bytes;
+        P.stack_depth = depth;
+        P.stack_slots = ws.stack.as<char>();
+        P.wl_slots = ws.wl.as<char>();
+        P.wl_seq = ws.wl_seq.as<unsigned>();
+        P.wl_cap = wl_cap;
+        P.wl_low = opt.load_balance ? std::max(8, pl.workers / 2) : 0;
+        P.reg = ws.reg.as<RegEntry>();
+        P.reg_words = ws.reg_words.as<uint32_t>();
+        P.reg_cap = reg_cap;
+        P.comp_scratch = ws.comp_scratch.as<int>();
+        P.ctl = ws.ctl.as<unsigned long long>();
+        P.node_budget = opt.node_budget;
+        P.idle_timeout_ns = (long long)opt.idle_timeout_ms * 1000000ll;
+        P.use_components = opt.use_components;
+        P.load_balance = opt.load_balance;
+        VC_CK(search_run(pl, P, ws.root_slot.as<int>(), nq, nroots, s, ws.ev[2], ws.ev[3]));
+        VC_CK(finalize_run(dq, nq, P.reg, P.reg_words, wcap, s));
+        VC_CK(cudaMemcpyAsync(ws.hctl.p, P.ctl, kCtlWords * 8, cudaMemcpyDeviceToHost, s));
+    } else {
+        VC_CK(finalize_run(dq, nq, nullptr, nullptr, 0, s));
+    }
+    VC_CK(cudaMemcpyAsync(hq, dq, sizeof(QueryDesc) * nq, cudaMemcpyDeviceToHost, s));
+    VC_CK(cudaStreamSynchronize(s));
+    if (nroots > 0) {
+        memcpy(hctl_local, ws.hctl.p, kCtlWords * 8);
+        VC_CK(cudaEventElapsedTime(&ms_search, ws.ev[2], ws.ev[3]));
+    }
+    float ms_root = 0.f;
+    VC_CK(cudaEventElapsedTime(&ms_root, ws.ev[0], ws.ev[1]));
+
+    const int kstatus = (int)(int64_t)hctl_local[kStatus];
+    // ---- covers: one device-to-host copy of every cover list
+    size_t total = 0;
+    std::vector<size_t> coff(nq);
+    for (int i = 0; i < nq; i++) {
+        coff[i] = total;
+        total += (size_t)std::max(hq[i].cover_len, 0);
+    }
+    const bool want_cov = covers != nullptr;
+    if (want_cov && total > 0 && kstatus == 0) {
+        if ((rc = ws.hcov.ensure(total * 4)) != VC_OK) return rc;
+        int32_t *hc = (int32_t *)ws.hcov.p;
+        for (int i = 0; i < nq; i++)
+            if (hq[i].cover_len > 0 && covers[i])
+                VC_CK(cudaMemcpyAsync(hc + coff[i], hq[i].cover_list, (size_t)hq[i].cover_len * 4,
+                                      cudaMemcpyDeviceToHost, s));
+        VC_CK(cudaStreamSynchronize(s));
+        for (int i = 0; i < nq; i++)
+            if (covers[i] && hq[i].cover_len > 0) memcpy(covers[i], hc + coff[i], (size_t)hq[i].cover_len * 4);
+    }
+    for (int i = 0; i < nq; i++) {
+        QueryOut &o = out[i];
+        const QueryDesc &Q = hq[i];
+        o.status = Q.status != VC_OK ? Q.status : (root_slot[i] >= 0 && kstatus ? kstatus : VC_OK);
+        o.size = Q.result;
+        o.yes = Q.yes;
+        o.cover_len = (o.status == VC_OK) ? Q.cover_len : 0;
+        if (cover_lens) cover_lens[i] = o.cover_len;
+    }
+    if (stats) {
+        memset(stats, 0, sizeof(*stats));
+        stats->nodes = (int64_t)hctl_local[kNodes];
+        stats->component_branches = (int64_t)hctl_local[kCompBranches];
+        stats->leaves = (int64_t)hctl_local[kLeaves];
+        stats->pruned = (int64_t)hctl_local[kPruned];
+        stats->offloaded = (int64_t)hctl_local[kOffloaded];
+        stats->trivial_components = (int64_t)hctl_local[kTrivial];
+        for (int b = 0; b < 16 && b < kHistBins; b++) stats->comp_hist[b] = (int64_t)hctl_local[kHist + b];
+        for (int i = 0; i < nq; i++) {
+            stats->n += hq[i].n;
+            stats->n_induced += hq[i].np;
+            stats->m_induced += hq[i].m2p / 2;
+            stats->forced += hq[i].forced;
+            stats->greedy_size += hq[i].greedy;
+        }
+        stats->dtype_bytes = nroots ? pl.dtype : 0;
+        stats->team = nroots ? (pl.warp_team ? 32 : pl.threads) : 0;
+        stats->workers = nroots ? pl.workers : 0;
+        stats->max_stack = (int32_t)hctl_local[kMaxStack];
+        stats->ms_root = ms_root;
+        stats->ms_search = ms_search;
+        stats->ms_total =
+            std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
+    }
+    return kstatus ? kstatus : VC_OK;
+}
+
+int load_common(int32_t n, const int32_t *rp, const int32_t *col, bool device_ptrs, void *stream,
+                vc_graph **out)
+{
+    if (!out) return VC_EINVAL;
+    *out = nullptr;
+    if (n < 0 || (n > 0 && !rp)) return VC_EINVAL;
+    vc_graph *g = new vc_graph();
+    g->stream = (cudaStream_t)stream;
+    if (cudaGetDevice(&g->device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&g->sms, cudaDevAttrMultiProcessorCount, g->device) != cudaSuccess) {
+        delete g;
+        return VC_ECUDA;
+    }
+    int m2 = 0;
+    if (n > 0) {
+        if (device_ptrs) {
+            if (cudaMemcpy(&m2, rp + n, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) {
+                delete g;
+                return VC_ECUDA;
+            }
+        } else {
+            m2 = rp[n];
+        }
+    }
+    if (m2 < 0 || (m2 > 0 && !col) || (m2 & 1)) { delete g; return VC_EINVAL; }
+    g->n = n;
+    g->m2 = m2;
+    int rc;
+    if ((rc = g->rp.ensure((size_t)(n + 1) * 4)) != VC_OK || (rc = g->col.ensure((size_t)std::max(m2, 1) * 4)) != VC_OK ||
+        (rc = g->err.ensure(16))) {
+        vc_free(g);
+        return rc;
+    }
+    const cudaMemcpyKind kind = device_ptrs ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    cudaStream_t s = g->stream;
+    bool ok = true;
+    if (n > 0) {
+        ok = ok && cudaMemcpyAsync(g->rp.p, rp, (size_t)(n + 1) * 4, kind, s) == cudaSuccess;
+        if (m2 > 0) ok = ok && cudaMemcpyAsync(g->col.p, col, (size_t)m2 * 4, kind, s) == cudaSuccess;
+    } else {
+        ok = ok && cudaMemsetAsync(g->rp.p, 0, 4, s) == cudaSuccess;
+    }
+    int herr[2] = {0, 0};
+    if (ok && n > 0) {
+        ok = validate_run(n, m2, g->rp.as<int>(), g->col.as<int>(), g->err.as<int>(), s) == cudaSuccess;
+        ok = ok && cudaMemcpyAsync(herr, g->err.p, 8, cudaMemcpyDeviceToHost, s) == cudaSuccess;
+    }
+    ok = ok && cudaStreamSynchronize(s) == cudaSuccess;
+    if (!ok) { vc_free(g); return VC_ECUDA; }
+    if (herr[0] != 0 || (long long)herr[1] * 2 != m2) { vc_free(g); return VC_EINVAL; }
+    *out = g;
+    return VC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int vc_options_default(vc_options *opt)
+{
+    if (!opt) return VC_EINVAL;
+    memset(opt, 0, sizeof(*opt));
+    opt->use_components = 1;
+    opt->load_balance = 1;
+    opt->idle_timeout_ms = 60000;
+    return VC_OK;
+}
+
+int vc_load_csr(int32_t n, const int32_t *row_ptr, const int32_t *col, void *cuda_stream, vc_graph **out)
+{
+    return load_common(n, row_ptr, col, false, cuda_stream, out);
+}
+
+int vc_load_csr_device(int32_t n, const int32_t *d_row_ptr, const int32_t *d_col, void *cuda_stream,
+                       vc_graph **out)
+{
+    return load_common(n, d_row_ptr, d_col, true, cuda_stream, out);
+}
+
+int vc_solve_min(vc_graph *g, const vc_options *opt, int32_t *cover_size, int32_t *cover, int32_t *cover_len,
+                 vc_stats *stats)
+{
+    if (!g || !cover_size) return VC_EINVAL;
+    std::vector<QueryRef> qs{{g, -1}};
+    std::vector<QueryOut> out;
+    int32_t *covers[1] = {cover};
+    int32_t len = 0;
+    int rc = solve_queries(g, qs, opt, out, cover ? covers : nullptr, &len, stats);
+    if (rc != VC_OK) return rc;
+    if (out[0].status != VC_OK) return out[0].status;
+    *cover_size = out[0].size;
+    if (cover_len) *cover_len = len;
+    return VC_OK;
+}
+
+int vc_solve_k(vc_graph *g, int32_t k, const vc_options *opt, int32_t *is_yes, int32_t *cover, int32_t *cover_len,
+               vc_stats *stats)
+{
+    if (!g || !is_yes || k < 0) return VC_EINVAL;
+    std::vector<QueryRef> qs{{g, k}};
+    std::vector<QueryOut> out;
+    int32_t *covers[1] = {cover};
+    int32_t len = 0;
+    int rc = solve_queries(g, qs, opt, out, cover ? covers : nullptr, &len, stats);
+    if (rc != VC_OK) return rc;
+    if (out[0].status != VC_OK) return out[0].status;
+    *is_yes = out[0].yes;
+    if (cover_len) *cover_len = out[0].yes ? len : 0;
+    return VC_OK;
+}
+
+int vc_solve_batch(int32_t count, vc_graph *const *graphs, const int32_t *ks, const vc_options *opt,
+                   int32_t *out_size, int32_t *out_yes, int32_t *out_status, int32_t *const *covers,
+                   int32_t *cover_lens, vc_stats *stats)
+{
+    if (count < 0 || (count > 0 && !graphs)) return VC_EINVAL;
+    if (count == 0) return VC_OK;
+    std::vector<QueryRef> qs(count);
+    for (int i = 0; i < count; i++) {
+        if (!graphs[i]) return VC_EINVAL;
+        qs[i] = {graphs[i], ks && ks[i] >= 0 ? ks[i] : -1};
+    }
+    std::vector<QueryOut> out;
+    int rc = solve_queries(graphs[0], qs, opt, out, covers, cover_lens, stats);
+    for (int i = 0; i < count; i++) {
+        if (out_size) out_size[i] = out.empty() ? -1 : out[i].size;
+        if (out_yes) out_yes[i] = out.empty() ? 0 : out[i].yes;
+        if (out_status) out_status[i] = out.empty() ? rc : out[i].status;
+    }
+    return rc;
+}
+
+void vc_free(vc_graph *g)
+{
+    if (!g) return;
+    g->rp.release();
+    g->col.release();
+    g->err.release();
+    g->ws.release();
+    delete g;
+}
+
+const char *vc_strerror(int status)
+{
+    switch (status) {
+    case VC_OK: return "ok";
+    case VC_EINVAL: return "invalid argument or malformed CSR graph";
+    case VC_ENOMEM: return "device or pinned host allocation failed";
+    case VC_ECAPACITY: return "stack, worklist, registry or shared memory capacity exceeded";
+    case VC_ETIMEOUT: return "a bounded device wait expired without progress";
+    case VC_ECUDA: return "CUDA runtime error";
+    case VC_EBUDGET: return "search-tree node budget exhausted";
+    default: return "unknown status";
+    }
+}
+
+}  // extern "C"

@@ -1,0 +1,363 @@
+// Shared device-side definitions of the GB300 vertex-cover solver.
+//
+// Layout in HBM (all device memory, owned by the library):
+//   per query:   input CSR, root-phase scratch (degrees, states, frontiers),
+//                induced CSR (rp2, col2) and the map back to original ids;
+//   per launch:  node slots (private stacks + shared worklist), the
+//                component-branch registry and its witness bitmaps.
+//
+// A search-tree node is a degree array over a window of the induced graph
+// plus a cover bitmap (Section 4.1 "degree array"; Section 4.3 "bounds on
+// non-zero entries").  Node slot = NodeHdr | degrees [lo, hi] (T each,
+// 16-byte aligned) | cover words of the context window.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/vc_gb300.h"
+
+namespace vcg {
+
+// ------------------------------------------------------------------ limits
+
+constexpr int kMaxBlock = 1024;
+constexpr unsigned kFull = 0xffffffffu;
+constexpr int kHistBins = 16;
+
+// ------------------------------------------------------------------ queries
+
+// One solve request: a graph and a mode (MVC, or PVC with k).  Written by the
+// host (inputs, buffer pointers) and by the root-phase kernel (outputs).
+struct QueryDesc {
+    // input graph (device copies owned by the vc_graph handle)
+    int n;
+    int m2;              // row_ptr[n] = 2|E|
+    const int *rp;
+    const int *col;
+    int k;               // -1: minimum cover; >= 0: is there a cover <= k?
+    int pad0;
+
+    // root-phase scratch (device, >= n entries each unless noted)
+    int *deg;            // live degree
+    int *aux;            // marks / greedy states
+    int *fr0;            // frontier lists
+    int *fr1;
+    int *flag;           // frontier membership
+    int *forced_list;    // vertices forced into the cover at the root (>= n)
+    uint8_t *st;         // 0 live, 1 forced into the cover, 2 greedy cover
+    uint8_t *cover_flags;// final cover, original numbering (n bytes)
+
+    // induced subgraph (device): rp2[np+1], col2[m2p], orig[np]
+    int *rp2;
+    int *col2;
+    int *orig;
+
+    // root-phase outputs
+    int status;          // VC_OK or a negative status
+    int forced;          // |F|
+    int greedy;          // greedy cover size of the whole graph (-1: not computed)
+    int bound;           // cover size the search must beat (whole graph)
+    int np;              // vertices of the induced subgraph
+    int m2p;             // 2 |E(induced)|
+    int maxdeg;          // max degree of the induced subgraph
+    int answered;        // 1: the root phase already settled the answer
+
+    // search outputs / final answer
+    int root_entry;      // registry entry of the induced graph's context
+    int result;          // MVC: minimum size; PVC: size found (yes) or -1
+    int yes;             // PVC answer (1 for MVC)
+    int improved;        // 1: the search found a cover better than `bound`
+    int cover_len;       // entries written to cover_list
+    int done;            // set once when the query is finished during the search
+    int *cover_list;     // ascending original ids (device, >= n)
+};
+
+// ------------------------------------------------------------------ nodes
+
+struct NodeHdr {            // 64 bytes; the payload after it stays 16-aligned
+    int32_t S;              // cover vertices chosen in this component context
+    int32_t comp;           // registry entry of the enclosing component context
+    int32_t lo, hi;         // degree window stored in the slot (lo % vec == 0)
+    int32_t clo, chi;       // component context window (cover bitmap range)
+    int32_t op;             // -1, or v: apply "G - N(v)" when the node is loaded
+    int32_t q;              // query id
+    int32_t cov_empty;      // 1: cover bitmap not stored (all zero)
+    int32_t depth;          // search-tree depth (statistics only)
+    int32_t pad[6];
+};
+static_assert(sizeof(NodeHdr) == 64, "node header must stay 64 bytes");
+
+// ------------------------------------------------------------------ registry
+
+// One entry of the component-branch registry (Section 3.3).  A "component"
+// entry holds {Best, LiveNodes, ParentIdx}; a "parent" entry holds
+// {Sum, LiveComps, AncestorIdx}.  The query's induced graph itself is a
+// component entry whose parent is -1.
+struct RegEntry {
+    int32_t val;     // Best (component) or Sum (parent)
+    int32_t live;    // LiveNodes (component) or LiveComps (parent)
+    int32_t link;    // ParentIdx (component) or AncestorIdx (parent)
+    int32_t lock;    // witness-bitmap lock (component entries)
+    int32_t has_w;   // 1: the witness bitmap holds a cover of size val
+    int32_t wlo;     // first bitmap word (vertex wlo*32 is bit 0 of word 0)
+    int32_t nw;      // bitmap words in use
+    int32_t q;       // query id
+    int32_t next;    // free-list link
+    int32_t kind;    // 0 component, 1 parent
+    int32_t pad[6];
+};
+static_assert(sizeof(RegEntry) == 64, "registry entry must stay 64 bytes");
+
+// ------------------------------------------------------------------ launch
+
+struct SearchParams {
+    QueryDesc *queries;
+    int nq;
+    int team;                 // threads per worker
+    int workers;
+    int ncap;                 // degree-array capacity (elements, multiple of 16)
+    int wcap;                 // cover-bitmap capacity (words)
+    int slot_bytes;           // bytes per node slot
+    int stack_depth;          // private slots per worker
+
+    char *stack_slots;        // workers * stack_depth * slot_bytes
+    char *wl_slots;           // wl_cap * slot_bytes
+    unsigned *wl_seq;         // wl_cap
+    int wl_cap;               // power of two
+    int wl_low;               // offload when the worklist holds fewer items
+
+    RegEntry *reg;            // reg_cap entries
+    uint32_t *reg_words;      // reg_cap * wcap words
+    int reg_cap;
+
+    int *comp_scratch;        // workers * 5 * ncap ints (per-component statistics)
+
+    unsigned long long *ctl;  // control block, see Ctl below
+    long long node_budget;
+    long long idle_timeout_ns;
+    int use_components;
+    int load_balance;
+};
+
+// Control block words (unsigned long long each).
+enum Ctl : int {
+    kWlCount = 0,     // items reserved in the worklist (signed)
+    kWlHead = 1,      // dequeue ticket
+    kWlTail = 2,      // enqueue ticket
+    kRegHead = 3,     // registry free-list head {tag:32 | idx:32}
+    kRemaining = 4,   // queries not finished
+    kAbort = 5,       // nonzero: stop everything
+    kStatus = 6,      // first error status (as unsigned of a negative int)
+    kProgress = 7,    // progress ticks (for the idle timeout)
+    kNodes = 8,       // statistics ...
+    kCompBranches = 9,
+    kLeaves = 10,
+    kPruned = 11,
+    kOffloaded = 12,
+    kTrivial = 13,
+    kMaxStack = 14,
+    kHist = 16,       // kHistBins words
+    kCtlWords = 32
+};
+
+// ------------------------------------------------------------------ helpers
+
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long *p)
+{
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ int ld_acquire(const int *p)
+{
+    int v;
+    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *p)
+{
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ int ld_relaxed(const int *p)
+{
+    int v;
+    asm volatile("ld.relaxed.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release(int *p, int v)
+{
+    asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ void st_release_u32(unsigned *p, unsigned v)
+{
+    asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ int atom_add_acq_rel(int *p, int v)
+{
+    int old;
+    asm volatile("atom.acq_rel.gpu.global.add.s32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+    return old;
+}
+
+__device__ __forceinline__ unsigned long long globaltimer()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void set_error(unsigned long long *ctl, int status)
+{
+    atomicCAS(&ctl[kStatus], 0ull, (unsigned long long)(unsigned)status);
+    atomicExch(&ctl[kAbort], 1ull);
+}
+
+__device__ __forceinline__ bool aborted(const unsigned long long *ctl)
+{
+    return *(volatile const unsigned long long *)&ctl[kAbort] != 0ull;
+}
+
+// ------------------------------------------------------------------ teams
+//
+// A worker is a "team" of threads that processes one search-tree node at a
+// time: one warp (Team<32>) for small induced graphs, or one thread block
+// (Team<0>, size = blockDim.x) for large ones.  Every team-wide operation
+// below must be reached by all threads of the team.
+
+template <int WARP_TEAM>
+struct Team;
+
+template <>
+struct Team<1> {   // one warp per worker
+    int rank;      // lane
+    __device__ __forceinline__ int size() const { return 32; }
+    __device__ __forceinline__ void sync() const { __syncwarp(); }
+    __device__ __forceinline__ bool leader() const { return rank == 0; }
+    __device__ __forceinline__ int sum(int x) const { return __reduce_add_sync(kFull, x); }
+    __device__ __forceinline__ int max(int x) const { return __reduce_max_sync(kFull, x); }
+    __device__ __forceinline__ int min(int x) const { return __reduce_min_sync(kFull, x); }
+    __device__ __forceinline__ unsigned umax(unsigned x) const { return __reduce_max_sync(kFull, x); }
+    __device__ __forceinline__ long long lmax(long long x) const
+    {
+        for (int o = 16; o > 0; o >>= 1) {
+            long long y = __shfl_xor_sync(kFull, x, o);
+            x = y > x ? y : x;
+        }
+        return x;
+    }
+    __device__ __forceinline__ long long lsum(long long x) const
+    {
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(kFull, x, o);
+        return x;
+    }
+    __device__ __forceinline__ int bcast(int x) const { return __shfl_sync(kFull, x, 0); }
+    // exclusive prefix of flag over the team; returns the team total in *tot
+    __device__ __forceinline__ int excl_scan(int x, int *tot) const
+    {
+        int inc = x;
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(kFull, inc, o);
+            if (rank >= o) inc += y;
+        }
+        *tot = __shfl_sync(kFull, inc, 31);
+        return inc - x;
+    }
+};
+
+template <>
+struct Team<0> {   // one block per worker
+    int rank;
+    int nthreads;
+    long long *red;   // shared scratch, >= 34 long longs
+    __device__ __forceinline__ int size() const { return nthreads; }
+    __device__ __forceinline__ void sync() const { __syncthreads(); }
+    __device__ __forceinline__ bool leader() const { return rank == 0; }
+
+    template <class Op>
+    __device__ __forceinline__ long long reduce(long long x, long long ident, Op op) const
+    {
+        for (int o = 16; o > 0; o >>= 1) x = op(x, (long long)__shfl_xor_sync(kFull, x, o));
+        const int w = rank >> 5, l = rank & 31, nw = (nthreads + 31) >> 5;
+        __syncthreads();
+        if (l == 0) red[w] = x;
+        __syncthreads();
+        if (w == 0) {
+            long long y = l < nw ? red[l] : ident;
+            for (int o = 16; o > 0; o >>= 1) y = op(y, (long long)__shfl_xor_sync(kFull, y, o));
+            if (l == 0) red[33] = y;
+        }
+        __syncthreads();
+        return red[33];
+    }
+    __device__ __forceinline__ int sum(int x) const
+    {
+        return (int)reduce(x, 0, [](long long a, long long b) { return a + b; });
+    }
+    __device__ __forceinline__ long long lsum(long long x) const
+    {
+        return reduce(x, 0, [](long long a, long long b) { return a + b; });
+    }
+    __device__ __forceinline__ int max(int x) const
+    {
+        return (int)reduce(x, INT32_MIN, [](long long a, long long b) { return a > b ? a : b; });
+    }
+    __device__ __forceinline__ unsigned umax(unsigned x) const
+    {
+        return (unsigned)reduce((long long)x, 0, [](long long a, long long b) { return a > b ? a : b; });
+    }
+    __device__ __forceinline__ int min(int x) const
+    {
+        return (int)reduce(x, INT32_MAX, [](long long a, long long b) { return a < b ? a : b; });
+    }
+    __device__ __forceinline__ long long lmax(long long x) const
+    {
+        return reduce(x, LLONG_MIN, [](long long a, long long b) { return a > b ? a : b; });
+    }
+    __device__ __forceinline__ int bcast(int x) const
+    {
+        __syncthreads();
+        if (rank == 0) red[32] = x;
+        __syncthreads();
+        int r = (int)red[32];
+        __syncthreads();
+        return r;
+    }
+    __device__ __forceinline__ int excl_scan(int x, int *tot) const
+    {
+        const int w = rank >> 5, l = rank & 31, nw = (nthreads + 31) >> 5;
+        int inc = x;
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(kFull, inc, o);
+            if (l >= o) inc += y;
+        }
+        __syncthreads();
+        if (l == 31) red[w] = inc;
+        __syncthreads();
+        if (w == 0) {
+            long long y = l < nw ? red[l] : 0;
+            long long s = y;
+            for (int o = 1; o < 32; o <<= 1) {
+                long long z = __shfl_up_sync(kFull, s, o);
+                if (l >= o) s += z;
+            }
+            if (l < nw) red[l] = s - y;   // exclusive warp offsets
+            if (l == 31) red[33] = s;
+        }
+        __syncthreads();
+        int r = (int)red[w] + inc - x;
+        *tot = (int)red[33];
+        __syncthreads();
+        return r;
+    }
+};
+
+}  // namespace vcg

@@ -1,0 +1,1240 @@
+// Persistent component-aware branch-and-reduce search (Algorithm 2 of the
+// paper, parallelised as in Sections 2.3 and 3).
+//
+// A worker is a team of threads (a warp, or a whole block for large induced
+// graphs).  It pops a node (private stack first, then the shared worklist),
+// stages its degree window and cover bitmap in shared memory, and then loops:
+//   reduce  - degree-one, degree-two-triangle and high-degree rules in
+//             synchronous rounds until a fixpoint (Section 2.2);
+//   prune   - |S| >= B or |E| > (B - |S| - 1)^2 with B the Best of the
+//             enclosing component (Algorithm 1, line 3);
+//   leaf    - |E| = 0: a new best cover of the component (Algorithm 1, 5-7);
+//   split   - union-find over the live vertices finds the components
+//             (Section 3.2); cliques and chordless cycles are closed at once
+//             (Section 3.4); with >= 2 others the node branches on components
+//             through the registry (Section 3.3);
+//   branch  - on the lowest-index vertex of maximum degree: the right child
+//             G - N(v) is stored (private stack or worklist), the left child
+//             G - v continues in shared memory (Algorithm 1, lines 9-11).
+// Completion decrements LiveNodes of the enclosing component entry; the last
+// descendant adds the component's Best into its parent's Sum and, when the
+// parent's LiveComps reaches zero, updates the ancestor's Best and continues
+// upward (Section 3.3).
+#include <climits>
+
+#include "vc_common.cuh"
+
+namespace vcg {
+
+// ---------------------------------------------------------------- sizes
+
+template <typename T>
+struct Vec {
+    static constexpr int kPer16 = 16 / sizeof(T);   // elements per 16-byte vector
+};
+
+__host__ __device__ inline int align_up(int x, int a) { return (x + a - 1) / a * a; }
+__host__ __device__ inline int align_down(int x, int a) { return x / a * a; }
+
+template <typename T>
+__host__ __device__ inline int deg_region_bytes(int ncap) { return align_up(ncap * (int)sizeof(T), 16); }
+
+template <typename T>
+__host__ __device__ inline int slot_bytes_for(int ncap, int wcap)
+{
+    return (int)sizeof(NodeHdr) + deg_region_bytes<T>(ncap) + align_up(wcap * 4, 16);
+}
+
+// shared-memory bytes of one worker (team)
+template <typename T>
+__host__ __device__ inline int worker_smem_bytes(int ncap, int wcap)
+{
+    return deg_region_bytes<T>(ncap) + align_up(ncap, 16) + ncap * 4 + align_up(wcap * 4, 16) + 64 + 34 * 8;
+}
+
+// ---------------------------------------------------------------- registry
+
+// Load that bypasses L1: registry entries and node slots are written by other
+// SMs and recycled, so a stale L1 line must never be read.
+template <class X>
+__device__ __forceinline__ X vld(const X &x) { return *(volatile const X *)&x; }
+
+__device__ int reg_alloc(const SearchParams &P)
+{
+    unsigned long long *head = &P.ctl[kRegHead];
+    for (int it = 0; it < (1 << 20); it++) {
+        unsigned long long h = atomicAdd(head, 0ull);
+        int idx = (int)(h & 0xffffffffull);
+        if (idx < 0) return -1;
+        int nx = *(volatile int *)&P.reg[idx].next;
+        unsigned long long nh = ((h >> 32) + 1) << 32 | (unsigned)nx;
+        if (atomicCAS(head, h, nh) == h) return idx;
+    }
+    return -1;
+}
+
+__device__ void reg_free(const SearchParams &P, int idx)
+{
+    unsigned long long *head = &P.ctl[kRegHead];
+    for (int it = 0; it < (1 << 20); it++) {
+        unsigned long long h = atomicAdd(head, 0ull);
+        *(volatile int *)&P.reg[idx].next = (int)(h & 0xffffffffull);
+        __threadfence();
+        unsigned long long nh = ((h >> 32) + 1) << 32 | (unsigned)idx;
+        if (atomicCAS(head, h, nh) == h) return;
+    }
+    set_error(P.ctl, VC_ETIMEOUT);
+}
+
+__device__ bool reg_lock(const SearchParams &P, int e)
+{
+    int *l = &P.reg[e].lock;
+    for (int it = 0; it < (1 << 24); it++) {
+        if (atomicCAS(l, 0, 1) == 0) {
+            __threadfence();
+            return true;
+        }
+        if (aborted(P.ctl)) return false;
+        __nanosleep(64);
+    }
+    set_error(P.ctl, VC_ETIMEOUT);
+    return false;
+}
+
+__device__ void reg_unlock(const SearchParams &P, int e)
+{
+    __threadfence();
+    atomicExch(&P.reg[e].lock, 0);
+}
+
+__device__ inline uint32_t *reg_words(const SearchParams &P, int e)
+{
+    return P.reg_words + (size_t)e * P.wcap;
+}
+
+// The query finished (its induced graph's entry completed, or PVC found a
+// cover <= k).  Counted once.
+__device__ void query_done(const SearchParams &P, int q)
+{
+    if (atomicExch(&P.queries[q].done, 1) == 0) atomicAdd(&P.ctl[kRemaining], (unsigned long long)-1ll);
+}
+
+__device__ inline bool query_is_done(const SearchParams &P, int q)
+{
+    return *(volatile int *)&P.queries[q].done != 0;
+}
+
+// ---------------------------------------------------------------- worker
+
+template <typename T, int WT>
+struct Worker {
+    const SearchParams &P;
+    Team<WT> tm;
+    int wid;
+
+    // shared-memory arrays of this worker
+    T *d;             // degrees of vertices [wlo, wlo + ncap)
+    uint8_t *mark;    // mark bytes, same indexing
+    int *lab;         // union-find labels / mark list
+    uint32_t *cov;    // cover bitmap of the context window
+    int *sc;          // scalars
+
+    // node state (uniform across the team)
+    int q, np;
+    const int *rp, *col;
+    int S, comp, lo, hi, clo, chi, wlo, whi, depth;
+    int cntbuf;       // double-buffer index of the mark counter
+
+    // private stack
+    char *stack;
+    int top;
+    long long nodes_local, last_flush;
+    int max_top;
+
+    __device__ Worker(const SearchParams &p, Team<WT> t, int w, char *smem) : P(p), tm(t), wid(w)
+    {
+        const int ncap = P.ncap, wcap = P.wcap;
+        char *s = smem;
+        d = (T *)s;                s += deg_region_bytes<T>(ncap);
+        mark = (uint8_t *)s;       s += align_up(ncap, 16);
+        lab = (int *)s;            s += ncap * 4;
+        cov = (uint32_t *)s;       s += align_up(wcap * 4, 16);
+        sc = (int *)s;             s += 64;
+        if constexpr (WT == 0) tm.red = (long long *)s;
+        stack = P.stack_slots + (size_t)wid * P.stack_depth * P.slot_bytes;
+        top = 0;
+        nodes_local = 0;
+        last_flush = 0;
+        max_top = 0;
+        cntbuf = 0;
+        if (tm.leader()) { sc[0] = 0; sc[1] = 0; }
+        tm.sync();
+    }
+
+    // ------------------------------------------------------------ accessors
+
+    __device__ __forceinline__ int dg(int u) const
+    {
+        return (u >= wlo && u <= whi) ? (int)d[u - wlo] : 0;
+    }
+
+    __device__ __forceinline__ bool marked(int u) const
+    {
+        return u >= wlo && u <= whi && mark[u - wlo] != 0;
+    }
+
+    __device__ __forceinline__ void dec(int u)
+    {
+        const int off = u - wlo;
+        if constexpr (sizeof(T) == 1) {
+            unsigned *w = (unsigned *)((char *)d + (off & ~3));
+            atomicSub(w, 1u << (8 * (off & 3)));
+        } else if constexpr (sizeof(T) == 2) {
+            unsigned *w = (unsigned *)((char *)d + 2 * (off & ~1));
+            atomicSub(w, 1u << (16 * (off & 1)));
+        } else {
+            atomicSub((unsigned *)&d[off], 1u);
+        }
+    }
+
+    // queue u for the cover in this round (deduplicated); list in lab[]
+    __device__ __forceinline__ void mark_vertex(int u)
+    {
+        const int off = u - wlo;
+        unsigned *w = (unsigned *)(mark + (off & ~3));
+        unsigned bit = 1u << (8 * (off & 3));
+        if (!(atomicOr(w, bit) & bit)) {
+            int pos = atomicAdd(&sc[cntbuf], 1);
+            lab[pos] = u;
+        }
+    }
+
+    __device__ __forceinline__ void cov_set(int v)
+    {
+        atomicOr(&cov[(v >> 5) - (clo >> 5)], 1u << (v & 31));
+    }
+
+    __device__ __forceinline__ bool adjacent(int a, int b) const
+    {
+        const int *row = col + rp[a];
+        int l = 0, h = rp[a + 1] - rp[a] - 1;
+        while (l <= h) {
+            int mid = (l + h) >> 1;
+            int x = __ldg(row + mid);
+            if (x == b) return true;
+            if (x < b) l = mid + 1; else h = mid - 1;
+        }
+        return false;
+    }
+
+    // ------------------------------------------------------------ marks
+
+    // Put every marked vertex (list lab[0..c)) in the cover: G - M, S + M.
+    __device__ void apply_marks(int c)
+    {
+        for (int i = tm.rank; i < c; i += tm.size()) {
+            const int u = lab[i];
+            cov_set(u);
+            for (int e = rp[u]; e < rp[u + 1]; e++) {
+                const int x = __ldg(col + e);
+                if (dg(x) > 0 && !marked(x)) dec(x);
+            }
+        }
+        tm.sync();
+        for (int i = tm.rank; i < c; i += tm.size()) {
+            const int u = lab[i];
+            d[u - wlo] = 0;
+            mark[u - wlo] = 0;
+        }
+        S += c;
+        tm.sync();
+    }
+
+    __device__ int take_count()
+    {
+        tm.sync();
+        int c = sc[cntbuf];
+        if (tm.leader()) sc[cntbuf ^ 1] = 0;
+        cntbuf ^= 1;
+        tm.sync();
+        return c;
+    }
+
+    // ------------------------------------------------------------ reduce
+
+    struct Stats {
+        long long e2;    // sum of live degrees
+        int live;        // live vertices
+        int dmax;        // maximum degree
+        int vmax;        // lowest-index vertex of maximum degree
+        int lo, hi;      // live window
+        int pruned;      // budget exhausted during reduction
+    };
+
+    // Rules of Section 2.2 in synchronous rounds until no vertex is marked.
+    __device__ Stats reduce(int B)
+    {
+        Stats st;
+        for (;;) {
+            const int bud = B - S - 1;
+            if (bud < 0) { st.pruned = 1; return st; }
+            long long e2 = 0;
+            int live = 0;
+            long long key = -1;
+            int nlo = INT_MAX, nhi = -1;
+            for (int v = lo + tm.rank; v <= hi; v += tm.size()) {
+                const int dv = (int)d[v - wlo];
+                if (dv == 0) continue;
+                live++;
+                e2 += dv;
+                const long long k = ((long long)dv << 32) | (unsigned)(0x7fffffff - v);
+                key = k > key ? k : key;
+                nlo = min(nlo, v);
+                nhi = max(nhi, v);
+                if (dv == 1) {
+                    int u = -1;
+                    for (int e = rp[v]; e < rp[v + 1]; e++) {
+                        int x = __ldg(col + e);
+                        if (dg(x) > 0) { u = x; break; }
+                    }
+                    if (u >= 0 && !(dg(u) == 1 && u < v)) mark_vertex(u);
+                } else if (dv == 2) {
+                    int u = -1, w = -1;
+                    for (int e = rp[v]; e < rp[v + 1]; e++) {
+                        int x = __ldg(col + e);
+                        if (dg(x) > 0) {
+                            if (u < 0) u = x; else { w = x; break; }
+                        }
+                    }
+                    if (w >= 0 && adjacent(u, w)) {
+                        if (!((dg(u) == 2 && u < v) || (dg(w) == 2 && w < v))) {
+                            mark_vertex(u);
+                            mark_vertex(w);
+                        }
+                    }
+                }
+                if (dv > bud) mark_vertex(v);
+            }
+            const int c = take_count();
+            if (c == 0) {
+                st.e2 = tm.lsum(e2);
+                st.live = tm.sum(live);
+                long long kk = tm.lmax(key);
+                st.dmax = kk < 0 ? 0 : (int)(kk >> 32);
+                st.vmax = kk < 0 ? -1 : 0x7fffffff - (int)(kk & 0xffffffffll);
+                st.lo = tm.min(nlo);
+                st.hi = tm.max(nhi);
+                st.pruned = 0;
+                return st;
+            }
+            apply_marks(c);
+        }
+    }
+
+    // ------------------------------------------------------------ slots
+
+    __device__ char *stack_slot(int i) const { return stack + (size_t)i * P.slot_bytes; }
+
+    // Write the current node (or a component child) into a slot.
+    //   kind 0: the current array with a pending op (right child G - N(op))
+    //   kind 1: component child: only vertices whose label is `root` (rel.)
+    __device__ void write_slot(char *slot, int kind, int op, int root, int clo_c, int chi_c, int comp_c,
+                               int S_c, int hi_c)
+    {
+        constexpr int V = Vec<T>::kPer16;
+        const int slo = align_down(kind == 0 ? lo : clo_c, V);
+        const int shi = kind == 0 ? hi : hi_c;
+        const int nvec = (align_up(shi + 1, V) - slo) / V;
+        NodeHdr *h = (NodeHdr *)slot;
+        if (tm.leader()) {
+            h->S = S_c;
+            h->comp = comp_c;
+            h->lo = slo;
+            h->hi = shi;
+            h->clo = clo_c;
+            h->chi = chi_c;
+            h->op = op;
+            h->q = q;
+            h->cov_empty = kind == 1;
+            h->depth = depth + 1;
+        }
+        uint4 *dst = (uint4 *)(slot + sizeof(NodeHdr));
+        if (kind == 0) {
+            const uint4 *src = (const uint4 *)(d + (slo - wlo));
+            for (int i = tm.rank; i < nvec; i += tm.size()) dst[i] = src[i];
+            const int w0 = clo >> 5, nw = (chi >> 5) - w0 + 1;
+            uint32_t *cdst = (uint32_t *)(slot + sizeof(NodeHdr) + deg_region_bytes<T>(P.ncap));
+            for (int i = tm.rank; i < nw; i += tm.size()) cdst[i] = cov[i];
+        } else {
+            for (int i = tm.rank; i < nvec; i += tm.size()) {
+                union { uint4 v; T e[V]; } u;
+                const int base = slo + i * V;
+                #pragma unroll
+                for (int j = 0; j < V; j++) {
+                    const int v = base + j;
+                    int val = 0;
+                    if (v >= lo && v <= hi && lab[v - lo] == root) val = (int)d[v - wlo];
+                    u.e[j] = (T)val;
+                }
+                dst[i] = u.v;
+            }
+        }
+    }
+
+    // Load a node from a slot into shared memory.
+    __device__ void read_slot(const char *slot)
+    {
+        constexpr int V = Vec<T>::kPer16;
+        const NodeHdr *h = (const NodeHdr *)slot;
+        // every thread reads the header (broadcast loads, L2 only: the slot
+        // may have been written by another SM)
+        S = __ldcg(&h->S); comp = __ldcg(&h->comp); wlo = __ldcg(&h->lo); whi = __ldcg(&h->hi);
+        clo = __ldcg(&h->clo); chi = __ldcg(&h->chi); q = __ldcg(&h->q); depth = __ldcg(&h->depth);
+        const int op = __ldcg(&h->op), cov_empty = __ldcg(&h->cov_empty);
+        lo = wlo; hi = whi;
+        const int nvec = (align_up(whi + 1, V) - wlo) / V;
+        const uint4 *src = (const uint4 *)(slot + sizeof(NodeHdr));
+        uint4 *dst = (uint4 *)d;
+        for (int i = tm.rank; i < nvec; i += tm.size()) dst[i] = __ldcg(src + i);
+        uint4 z = make_uint4(0, 0, 0, 0);
+        uint4 *mk = (uint4 *)mark;
+        const int mvec = align_up(nvec * V, 16) / 16;
+        for (int i = tm.rank; i < mvec; i += tm.size()) mk[i] = z;
+        const int w0 = clo >> 5, nw = (chi >> 5) - w0 + 1;
+        const uint32_t *csrc = (const uint32_t *)(slot + sizeof(NodeHdr) + deg_region_bytes<T>(P.ncap));
+        for (int i = tm.rank; i < nw; i += tm.size()) cov[i] = cov_empty ? 0u : __ldcg(csrc + i);
+        const QueryDesc &Q = P.queries[q];
+        rp = Q.rp2;
+        col = Q.col2;
+        np = Q.np;
+        tm.sync();
+        if (op >= 0) {
+            // right child of a vertex branch: G - N(op), S + N(op)
+            for (int e = rp[op] + tm.rank; e < rp[op + 1]; e += tm.size()) {
+                const int x = __ldg(col + e);
+                if (dg(x) > 0) mark_vertex(x);
+            }
+            const int c = take_count();
+            apply_marks(c);
+        }
+    }
+
+    // ------------------------------------------------------------ worklist
+
+    // Reserve a worklist slot; returns the ticket or -1 when full.
+    __device__ long long wl_reserve()
+    {
+        int ok = 0;
+        long long t = -1;
+        if (tm.leader()) {
+            long long old = (long long)atomicAdd(&P.ctl[kWlCount], 1ull);
+            if (old >= P.wl_cap) {
+                atomicAdd(&P.ctl[kWlCount], (unsigned long long)-1ll);
+            } else {
+                ok = 1;
+                t = (long long)atomicAdd(&P.ctl[kWlTail], 1ull);
+                const unsigned slot = (unsigned)t & (P.wl_cap - 1);
+                int it = 0;
+                while (ld_acquire_u32(&P.wl_seq[slot]) != (unsigned)t) {
+                    if (++it > (1 << 24) || aborted(P.ctl)) { set_error(P.ctl, VC_ETIMEOUT); ok = 0; break; }
+                    __nanosleep(32);
+                }
+            }
+            sc[4] = ok;
+            sc[5] = (int)(t & 0x7fffffff);
+            sc[6] = (int)(t >> 31);
+        }
+        tm.sync();
+        ok = sc[4];
+        long long tt = ((long long)sc[6] << 31) | (unsigned)sc[5];
+        tm.sync();
+        return ok ? tt : -1;
+    }
+
+    __device__ void wl_publish(long long t)
+    {
+        __threadfence();
+        tm.sync();
+        if (tm.leader()) {
+            const unsigned slot = (unsigned)t & (P.wl_cap - 1);
+            st_release_u32(&P.wl_seq[slot], (unsigned)t + 1u);
+            atomicAdd(&P.ctl[kOffloaded], 1ull);
+        }
+    }
+
+    __device__ char *wl_slot(long long t) const
+    {
+        return P.wl_slots + (size_t)((unsigned)t & (P.wl_cap - 1)) * P.slot_bytes;
+    }
+
+    // Try to take a node from the worklist into shared memory.
+    __device__ bool wl_pop()
+    {
+        int ok = 0;
+        if (tm.leader()) {
+            long long old = (long long)atomicAdd(&P.ctl[kWlCount], (unsigned long long)-1ll);
+            if (old <= 0) {
+                atomicAdd(&P.ctl[kWlCount], 1ull);
+            } else {
+                const long long t = (long long)atomicAdd(&P.ctl[kWlHead], 1ull);
+                const unsigned slot = (unsigned)t & (P.wl_cap - 1);
+                int it = 0;
+                ok = 1;
+                while (ld_acquire_u32(&P.wl_seq[slot]) != (unsigned)t + 1u) {
+                    if (++it > (1 << 24) || aborted(P.ctl)) { set_error(P.ctl, VC_ETIMEOUT); ok = 0; break; }
+                    __nanosleep(32);
+                }
+                sc[5] = (int)(t & 0x7fffffff);
+                sc[6] = (int)(t >> 31);
+            }
+            sc[4] = ok;
+        }
+        tm.sync();
+        ok = sc[4];
+        const long long t = ((long long)sc[6] << 31) | (unsigned)sc[5];
+        tm.sync();
+        if (!ok) return false;
+        read_slot(wl_slot(t));
+        tm.sync();
+        if (tm.leader()) {
+            const unsigned slot = (unsigned)t & (P.wl_cap - 1);
+            st_release_u32(&P.wl_seq[slot], (unsigned)t + (unsigned)P.wl_cap);
+        }
+        return true;
+    }
+
+    // Store a child: the worklist when it is hungry (load balancing,
+    // Section 2.3), else the private stack, else the worklist.  Returns false
+    // on overflow (error already recorded).
+    __device__ bool push_child(int kind, int op, int root, int clo_c, int chi_c, int comp_c, int S_c, int hi_c)
+    {
+        int to_wl = 0;
+        if (P.load_balance && tm.leader()) {
+            const long long cnt = (long long)*(volatile unsigned long long *)&P.ctl[kWlCount];
+            to_wl = cnt < P.wl_low;
+        }
+        to_wl = tm.bcast(to_wl);   // uniform decision: the team must take one path
+        if (!to_wl && top < P.stack_depth) {
+            write_slot(stack_slot(top), kind, op, root, clo_c, chi_c, comp_c, S_c, hi_c);
+            top++;
+            max_top = max(max_top, top);
+            tm.sync();
+            return true;
+        }
+        long long t = wl_reserve();
+        if (t < 0) {
+            if (top < P.stack_depth) {
+                write_slot(stack_slot(top), kind, op, root, clo_c, chi_c, comp_c, S_c, hi_c);
+                top++;
+                max_top = max(max_top, top);
+                tm.sync();
+                return true;
+            }
+            if (tm.leader()) set_error(P.ctl, VC_ECAPACITY);
+            tm.sync();
+            return false;
+        }
+        write_slot(wl_slot(t), kind, op, root, clo_c, chi_c, comp_c, S_c, hi_c);
+        wl_publish(t);
+        tm.sync();
+        return true;
+    }
+
+    // ------------------------------------------------------------ registry ops
+
+    // A leaf with cover size S in context `comp`: Best = min(Best, S) and the
+    // witness bitmap follows (under the entry's lock).
+    __device__ void improve()
+    {
+        int go = 0;
+        if (tm.leader()) {
+            RegEntry &E = P.reg[comp];
+            if (S < ld_relaxed(&E.val) && reg_lock(P, comp)) {
+                if (S < *(volatile int *)&E.val) go = 1;
+                else reg_unlock(P, comp);
+            }
+            sc[7] = go;
+        }
+        tm.sync();
+        go = sc[7];
+        tm.sync();
+        if (!go) return;
+        uint32_t *w = reg_words(P, comp);
+        const int nw = (chi >> 5) - (clo >> 5) + 1;
+        for (int i = tm.rank; i < nw; i += tm.size()) w[i] = cov[i];
+        __threadfence();
+        tm.sync();
+        if (tm.leader()) {
+            RegEntry &E = P.reg[comp];
+            E.has_w = 1;
+            atomicExch(&E.val, S);
+            reg_unlock(P, comp);
+            if (vld(E.link) < 0 && P.queries[q].k >= 0) query_done(P, q);   // PVC: a cover <= k exists
+        }
+        tm.sync();
+    }
+
+    // One node of context c completed (Section 3.3).  The last descendant of
+    // a component adds its Best into the parent's Sum; the last component of a
+    // parent updates the ancestor's Best and counts as its completion.
+    __device__ void complete(int c)
+    {
+        for (int guard = 0;; guard++) {
+            if (guard > (1 << 22)) {      // the registry chain is acyclic; never expected
+                if (tm.leader()) set_error(P.ctl, VC_ETIMEOUT);
+                tm.sync();
+                return;
+            }
+            int r = 0;
+            if (tm.leader()) r = atom_add_acq_rel(&P.reg[c].live, -1) - 1;
+            r = tm.bcast(r);
+            if (r != 0) return;
+            // component entry c is finished
+            const RegEntry &C = P.reg[c];
+            const int par = vld(C.link);
+            if (par < 0) {
+                if (tm.leader()) query_done(P, q);
+                tm.sync();
+                return;
+            }
+            const int bestc = vld(C.val);
+            const int hw = vld(C.has_w);
+            const RegEntry &Pe = P.reg[par];
+            if (hw) {
+                const uint32_t *src = reg_words(P, c);
+                const int cnw = vld(C.nw);
+                uint32_t *dst = reg_words(P, par) + (vld(C.wlo) - vld(Pe.wlo));
+                for (int i = tm.rank; i < cnw; i += tm.size()) atomicOr(&dst[i], __ldcg(src + i));
+                __threadfence();
+            }
+            tm.sync();
+            int r2 = 0;
+            if (tm.leader()) {
+                atomicAdd(&P.reg[par].val, bestc);
+                reg_free(P, c);
+                r2 = atom_add_acq_rel(&P.reg[par].live, -1) - 1;
+            }
+            r2 = tm.bcast(r2);
+            if (r2 != 0) return;
+            // parent entry `par` is finished: Algorithm 2 line 20 for its ancestor
+            const int anc = vld(Pe.link);
+            const int sum = vld(Pe.val);
+            int go = 0;
+            if (tm.leader()) {
+                RegEntry &A = P.reg[anc];
+                if (sum < ld_relaxed(&A.val) && reg_lock(P, anc)) {
+                    if (sum < *(volatile int *)&A.val) go = 1;
+                    else reg_unlock(P, anc);
+                }
+            }
+            go = tm.bcast(go);
+            if (go) {
+                const RegEntry &A = P.reg[anc];
+                const uint32_t *src = reg_words(P, par);
+                const int pnw = vld(Pe.nw);
+                uint32_t *dst = reg_words(P, anc) + (vld(Pe.wlo) - vld(A.wlo));
+                for (int i = tm.rank; i < pnw; i += tm.size()) dst[i] = __ldcg(src + i);
+                __threadfence();
+                tm.sync();
+                if (tm.leader()) {
+                    RegEntry &Aw = P.reg[anc];
+                    Aw.has_w = 1;
+                    atomicExch(&Aw.val, sum);
+                    reg_unlock(P, anc);
+                    if (vld(Aw.link) < 0 && P.queries[q].k >= 0) query_done(P, q);
+                }
+            }
+            tm.sync();
+            if (tm.leader()) reg_free(P, par);
+            tm.sync();
+            c = anc;
+        }
+    }
+
+    // ------------------------------------------------------------ components
+
+    __device__ __forceinline__ int uf_find(int x)
+    {
+        int p = ((volatile int *)lab)[x];
+        while (p != x) {
+            int g = ((volatile int *)lab)[p];
+            if (g != p) ((volatile int *)lab)[x] = g;   // path halving (benign race)
+            x = p;
+            p = g;
+        }
+        return x;
+    }
+
+    __device__ void uf_unite(int a, int b)
+    {
+        for (;;) {
+            a = uf_find(a);
+            b = uf_find(b);
+            if (a == b) return;
+            if (a > b) { int t = a; a = b; b = t; }
+            int old = atomicCAS(&lab[b], b, a);
+            if (old == b) return;
+            b = old;
+        }
+    }
+
+    // Connected components of the live vertices in [lo, hi]; afterwards
+    // lab[i] (i = v - lo) is the smallest relative index of v's component.
+    // Returns the number of components.
+    __device__ int find_components()
+    {
+        const int W = hi - lo + 1;
+        for (int i = tm.rank; i < W; i += tm.size()) lab[i] = d[lo + i - wlo] > 0 ? i : -1;
+        tm.sync();
+        for (int i = tm.rank; i < W; i += tm.size()) {
+            const int v = lo + i;
+            if (d[v - wlo] == 0) continue;
+            for (int e = rp[v]; e < rp[v + 1]; e++) {
+                const int u = __ldg(col + e);
+                if (u > v && u <= hi && d[u - wlo] > 0) uf_unite(i, u - lo);
+            }
+        }
+        tm.sync();
+        int roots = 0;
+        for (int i = tm.rank; i < W; i += tm.size()) {
+            if (lab[i] < 0) continue;
+            int r = uf_find(i);
+            lab[i] = r;
+            roots += (r == i);
+        }
+        tm.sync();
+        return tm.sum(roots);
+    }
+
+    // Cover of a chordless cycle component starting at vertex s: every other
+    // vertex along the cycle (ceil(L/2) of them).  One thread.
+    __device__ void cover_cycle(int s)
+    {
+        int prev = -1, cur = s, k = 0;
+        for (int guard = 0; guard <= np; guard++) {
+            if ((k & 1) == 0) cov_set(cur);
+            int next = -1;
+            for (int e = rp[cur]; e < rp[cur + 1]; e++) {
+                const int x = __ldg(col + e);
+                if (x != prev && dg(x) > 0) { next = x; break; }
+            }
+            prev = cur;
+            cur = next;
+            k++;
+            if (cur == s || cur < 0) break;
+        }
+    }
+
+    // Vertex of maximum degree (lowest index) among live vertices.
+    __device__ int find_vmax()
+    {
+        long long key = -1;
+        for (int v = lo + tm.rank; v <= hi; v += tm.size()) {
+            const int dv = (int)d[v - wlo];
+            if (dv == 0) continue;
+            const long long k = ((long long)dv << 32) | (unsigned)(0x7fffffff - v);
+            key = k > key ? k : key;
+        }
+        long long kk = tm.lmax(key);
+        return kk < 0 ? -1 : 0x7fffffff - (int)(kk & 0xffffffffll);
+    }
+
+    // Narrow [lo, hi] to the live vertices.
+    __device__ void shrink_window()
+    {
+        int nlo = INT_MAX, nhi = -1;
+        for (int v = lo + tm.rank; v <= hi; v += tm.size())
+            if (d[v - wlo] > 0) { nlo = min(nlo, v); nhi = max(nhi, v); }
+        nlo = tm.min(nlo);
+        nhi = tm.max(nhi);
+        if (nhi >= 0) { lo = nlo; hi = nhi; }
+    }
+
+    enum { kComplete = 0, kVertexBranch = 1, kHandedOff = 2, kError = 3 };
+
+    // Branch on >= 2 components, or close the trivial ones.  Returns
+    //   kComplete      the node is finished (pruned or a leaf),
+    //   kVertexBranch  one non-trivial component is left: branch on a vertex,
+    //   kHandedOff     a branch on components was registered; the parent
+    //                  entry now stands for this node (Section 3.3),
+    //   kError         capacity exhausted (recorded in the control block).
+    __device__ int handle_components(int B)
+    {
+        const int W = hi - lo + 1;
+        int *scr = P.comp_scratch + (size_t)wid * 5 * P.ncap;
+        int *csize = scr, *csum = scr + P.ncap, *cmin = scr + 2 * P.ncap, *cmax = scr + 3 * P.ncap,
+            *chiv = scr + 4 * P.ncap;
+        for (int i = tm.rank; i < W; i += tm.size()) {
+            if (lab[i] == i) { csize[i] = 0; csum[i] = 0; cmin[i] = INT_MAX; cmax[i] = 0; chiv[i] = i; }
+        }
+        __threadfence_block();
+        tm.sync();
+        for (int i = tm.rank; i < W; i += tm.size()) {
+            const int r = lab[i];
+            if (r < 0) continue;
+            const int dv = (int)d[lo + i - wlo];
+            atomicAdd(&csize[r], 1);
+            atomicAdd(&csum[r], dv);
+            atomicMin(&cmin[r], dv);
+            atomicMax(&cmax[r], dv);
+            atomicMax(&chiv[r], i);
+        }
+        __threadfence();
+        tm.sync();
+        // classify: trivial (clique / cycle) components are closed here
+        int s_triv = 0, lb_sum = 0, nontriv = 0;
+        for (int i = tm.rank; i < W; i += tm.size()) {
+            if (lab[i] != i) continue;
+            const int sz = __ldcg(csize + i), mn = __ldcg(cmin + i), mx = __ldcg(cmax + i);
+            const bool clique = mn == sz - 1 && mx == sz - 1;
+            const bool cyc = mn == 2 && mx == 2;
+            if (clique || cyc) {
+                s_triv += clique ? sz - 1 : (sz + 1) / 2;
+            } else {
+                nontriv++;
+                const int m = __ldcg(csum + i) / 2;
+                lb_sum += (m + mx - 1) / mx;
+            }
+        }
+        s_triv = tm.sum(s_triv);
+        lb_sum = tm.sum(lb_sum);
+        nontriv = tm.sum(nontriv);
+        if (S + s_triv + lb_sum >= B) {       // even the lower bounds reach Best
+            if (tm.leader()) atomicAdd(&P.ctl[kPruned], 1ull);
+            return kComplete;
+        }
+        if (s_triv > 0) {
+            // cliques: all but the highest vertex; cycles: every other vertex
+            for (int i = tm.rank; i < W; i += tm.size()) {
+                const int r = lab[i];
+                if (r < 0) continue;
+                const int sz = __ldcg(csize + r), mn = __ldcg(cmin + r), mx = __ldcg(cmax + r);
+                const bool clique = mn == sz - 1 && mx == sz - 1;
+                if (clique && i != __ldcg(chiv + r)) cov_set(lo + i);
+            }
+            int ntriv = 0;
+            for (int i = tm.rank; i < W; i += tm.size()) {
+                if (lab[i] != i) continue;
+                const int sz = __ldcg(csize + i), mn = __ldcg(cmin + i), mx = __ldcg(cmax + i);
+                const bool clique = mn == sz - 1 && mx == sz - 1;
+                const bool cyc = mn == 2 && mx == 2;
+                if (cyc && !clique) cover_cycle(lo + i);
+                ntriv += (clique || cyc);
+            }
+            tm.sync();
+            for (int i = tm.rank; i < W; i += tm.size()) {
+                const int r = lab[i];
+                if (r < 0) continue;
+                const int sz = __ldcg(csize + r), mn = __ldcg(cmin + r), mx = __ldcg(cmax + r);
+                if ((mn == sz - 1 && mx == sz - 1) || (mn == 2 && mx == 2)) {
+                    d[lo + i - wlo] = 0;
+                    lab[i] = -1;
+                }
+            }
+            ntriv = tm.sum(ntriv);
+            S += s_triv;
+            if (tm.leader()) atomicAdd(&P.ctl[kTrivial], (unsigned long long)ntriv);
+            tm.sync();
+        }
+        if (nontriv == 0) {                    // all edges covered: a leaf
+            if (tm.leader()) atomicAdd(&P.ctl[kLeaves], 1ull);
+            improve();
+            return kComplete;
+        }
+        if (nontriv == 1) {
+            shrink_window();
+            return kVertexBranch;
+        }
+
+        // ---- branch on components (Algorithm 2 lines 14-20, Section 3.3)
+        // parent entry: Sum = |S| (this node's cover, trivial components
+        // included), LiveComps = number of components, witness = S
+        int pidx = -1;
+        if (tm.leader()) {
+            pidx = reg_alloc(P);
+            if (pidx < 0) set_error(P.ctl, VC_ECAPACITY);
+        }
+        pidx = tm.bcast(pidx);
+        if (pidx < 0) return kError;
+        {
+            RegEntry &E = P.reg[pidx];
+            if (tm.leader()) {
+                E.val = S;
+                E.live = nontriv;
+                E.link = comp;
+                E.lock = 0;
+                E.has_w = 0;
+                E.wlo = clo >> 5;
+                E.nw = (chi >> 5) - (clo >> 5) + 1;
+                E.q = q;
+                E.kind = 1;
+            }
+            uint32_t *w = reg_words(P, pidx);
+            const int nw = (chi >> 5) - (clo >> 5) + 1;
+            for (int i = tm.rank; i < nw; i += tm.size()) w[i] = cov[i];
+        }
+        // child entries {Best_i, LiveNodes = 1, ParentIdx}, one per
+        // non-trivial component in index order; each child node is written by
+        // the whole team (sequential over components, parallel within one)
+        for (int base = 0; base < W; base += tm.size()) {
+            const int i = base + tm.rank;
+            bool isroot = false;
+            if (i < W && lab[i] == i) isroot = true;
+            // rank the roots of this stripe
+            int tot;
+            int pos = tm.excl_scan(isroot ? 1 : 0, &tot);
+            for (int j = 0; j < tot; j++) {
+                // the thread holding the j-th root broadcasts it
+                int mine = (isroot && pos == j) ? i : -1;
+                int r = tm.max(mine);
+                const int sz = __ldcg(csize + r), mx = __ldcg(cmax + r);
+                const int m = __ldcg(csum + r) / 2;
+                const int lb = (m + mx - 1) / mx;
+                int bi = B - S - (lb_sum - lb);
+                if (bi > sz - 1) bi = sz - 1;
+                const int clo_c = lo + r, chi_c = lo + __ldcg(chiv + r);
+                int cidx = -1;
+                if (tm.leader()) {
+                    cidx = reg_alloc(P);
+                    if (cidx < 0) set_error(P.ctl, VC_ECAPACITY);
+                }
+                cidx = tm.bcast(cidx);
+                if (cidx < 0) return kError;
+                RegEntry &C = P.reg[cidx];
+                const int has = bi == sz - 1;
+                const int cw0 = clo_c >> 5, cnw = (chi_c >> 5) - cw0 + 1;
+                if (tm.leader()) {
+                    C.val = bi;
+                    C.live = 1;
+                    C.link = pidx;
+                    C.lock = 0;
+                    C.has_w = has;
+                    C.wlo = cw0;
+                    C.nw = cnw;
+                    C.q = q;
+                    C.kind = 0;
+                }
+                if (has) {
+                    // every vertex of the component but its highest one
+                    uint32_t *w = reg_words(P, cidx);
+                    for (int x = tm.rank; x < cnw; x += tm.size()) {
+                        uint32_t bits = 0;
+                        for (int b = 0; b < 32; b++) {
+                            const int v = (cw0 + x) * 32 + b;
+                            if (v >= lo + r && v < chi_c && lab[v - lo] == r) bits |= 1u << b;
+                        }
+                        w[x] = bits;
+                    }
+                }
+                __threadfence();
+                tm.sync();
+                if (!push_child(1, -1, r, clo_c, chi_c, cidx, 0, chi_c)) return kError;
+            }
+        }
+        if (tm.leader()) {
+            atomicAdd(&P.ctl[kCompBranches], 1ull);
+            int b = min(nontriv, kHistBins) - 2;
+            if (b >= 0) atomicAdd(&P.ctl[kHist + b], 1ull);
+        }
+        tm.sync();
+        return kHandedOff;
+    }
+
+    // ------------------------------------------------------------ node
+
+    // Process the node now in shared memory and all its left descendants.
+    __device__ void process()
+    {
+        for (;;) {
+            nodes_local++;
+            int B = 0;
+            if (tm.leader()) B = aborted(P.ctl) ? INT_MIN : ld_relaxed(&P.reg[comp].val);
+            B = tm.bcast(B);
+            if (B == INT_MIN) return;   // aborted (decided by the leader for the whole team)
+            Stats st = reduce(B);
+            if (st.pruned) {
+                if (tm.leader()) atomicAdd(&P.ctl[kPruned], 1ull);
+                complete(comp);
+                return;
+            }
+            const long long bud = (long long)B - S - 1;
+            if (S >= B || st.e2 / 2 > bud * bud) {      // stopping condition
+                if (tm.leader()) atomicAdd(&P.ctl[kPruned], 1ull);
+                complete(comp);
+                return;
+            }
+            if (st.e2 == 0) {                            // a new best cover
+                if (tm.leader()) atomicAdd(&P.ctl[kLeaves], 1ull);
+                improve();
+                complete(comp);
+                return;
+            }
+            lo = st.lo;
+            hi = st.hi;
+            int vmax = st.vmax;
+            if (P.use_components) {
+                const int ncomp = find_components();
+                const bool clique = (long long)st.live * (st.live - 1) == st.e2;
+                const bool cycle = st.dmax == 2 && st.e2 == 2ll * st.live;
+                if (ncomp >= 2 || clique || cycle) {
+                    const int r = handle_components(B);
+                    if (r == kComplete) { complete(comp); return; }
+                    if (r != kVertexBranch) return;
+                    vmax = find_vmax();
+                }
+            }
+            // ---- branch on v_max (Algorithm 1 lines 9-11)
+            if (vmax < lo || vmax > hi) {                         // cannot happen with edges left
+                if (tm.leader()) set_error(P.ctl, VC_ECAPACITY);
+                tm.sync();
+                return;
+            }
+            if (tm.leader()) atomicAdd(&P.reg[comp].live, 1);    // two children replace one node
+            tm.sync();
+            if (!push_child(0, vmax, -1, clo, chi, comp, S, hi)) return;
+            if (tm.rank == 0) mark_vertex(vmax);
+            const int c = take_count();
+            apply_marks(c);
+            depth++;
+        }
+    }
+
+    // ------------------------------------------------------------ main loop
+
+    __device__ void flush_counters()
+    {
+        if (tm.leader()) {
+            atomicAdd(&P.ctl[kNodes], (unsigned long long)(nodes_local - last_flush));
+            atomicAdd(&P.ctl[kProgress], 1ull);
+            atomicMax(&P.ctl[kMaxStack], (unsigned long long)max_top);
+        }
+        last_flush = nodes_local;
+    }
+
+    __device__ void run()
+    {
+        unsigned long long idle_since = 0, seen_progress = ~0ull;
+        int backoff = 32;
+        for (;;) {
+            int ab = tm.leader() ? (int)aborted(P.ctl) : 0;
+            if (tm.bcast(ab)) break;
+            bool got = false;
+            if (top > 0) {
+                top--;
+                read_slot(stack_slot(top));
+                got = true;
+            } else {
+                got = wl_pop();
+            }
+            if (got) {
+                backoff = 32;
+                idle_since = 0;
+                int qd = tm.leader() ? (int)query_is_done(P, q) : 0;
+                if (tm.bcast(qd)) { tm.sync(); continue; }   // PVC answered meanwhile
+                process();
+                if (nodes_local - last_flush >= 64) {
+                    flush_counters();
+                    if (P.node_budget > 0 &&
+                        (long long)*(volatile unsigned long long *)&P.ctl[kNodes] > P.node_budget) {
+                        if (tm.leader()) set_error(P.ctl, VC_EBUDGET);
+                    }
+                }
+                tm.sync();
+                continue;
+            }
+            // idle
+            int stop = 0;
+            if (tm.leader() && *(volatile unsigned long long *)&P.ctl[kRemaining] == 0ull) stop = 2;
+            if (tm.leader() && !stop) {
+                const unsigned long long prog = *(volatile unsigned long long *)&P.ctl[kProgress];
+                const unsigned long long now = globaltimer();
+                if (prog != seen_progress || idle_since == 0) { seen_progress = prog; idle_since = now; }
+                else if ((long long)(now - idle_since) > P.idle_timeout_ns) { set_error(P.ctl, VC_ETIMEOUT); stop = 1; }
+                __nanosleep(backoff);
+            }
+            backoff = min(backoff * 2, 2048);
+            stop = tm.bcast(stop);
+            if (stop) break;
+        }
+        flush_counters();
+    }
+};
+
+// ---------------------------------------------------------------- kernels
+
+template <typename T, int WT>
+__global__ void search_kernel(const __grid_constant__ SearchParams P)
+{
+    extern __shared__ __align__(16) char smem[];
+    if constexpr (WT == 1) {
+        const int warp = threadIdx.x >> 5;
+        const int wpb = blockDim.x >> 5;
+        const int wid = blockIdx.x * wpb + warp;
+        Team<1> t;
+        t.rank = threadIdx.x & 31;
+        char *mine = smem + (size_t)warp * align_up(worker_smem_bytes<T>(P.ncap, P.wcap), 16);
+        Worker<T, 1> w(P, t, wid, mine);
+        w.run();
+    } else {
+        Team<0> t;
+        t.rank = threadIdx.x;
+        t.nthreads = blockDim.x;
+        t.red = nullptr;
+        Worker<T, 0> w(P, t, blockIdx.x, smem);
+        w.run();
+    }
+}
+
+// Registry free list over [first, cap) and each query's root entry + node.
+template <typename T>
+__global__ void search_init_kernel(SearchParams P, int first)
+{
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+    const int nth = gridDim.x * blockDim.x;
+    for (int e = first + tid; e < P.reg_cap; e += nth) {
+        P.reg[e].next = e + 1 < P.reg_cap ? e + 1 : -1;
+        P.reg[e].lock = 0;
+    }
+    for (int s = tid; s < P.wl_cap; s += nth) P.wl_seq[s] = (unsigned)s;
+    if (tid == 0) {
+        for (int i = 0; i < kCtlWords; i++) P.ctl[i] = 0;
+        P.ctl[kRegHead] = first < P.reg_cap ? (unsigned)first : 0xffffffffu;
+    }
+}
+
+// One block per query: its root registry entry and root node (worklist).
+template <typename T>
+__global__ void search_roots_kernel(SearchParams P, const int *root_slot)
+{
+    const int qi = blockIdx.x;
+    QueryDesc &Q = P.queries[qi];
+    const int slot = root_slot[qi];
+    if (slot < 0) return;
+    constexpr int V = Vec<T>::kPer16;
+    const int np = Q.np;
+    if (threadIdx.x == 0) {
+        RegEntry &R = P.reg[qi];
+        R.val = Q.bound - Q.forced;
+        R.live = 1;
+        R.link = -1;
+        R.lock = 0;
+        R.has_w = 0;
+        R.wlo = 0;
+        R.nw = (np - 1) / 32 + 1;
+        R.q = qi;
+        R.kind = 0;
+        R.next = -1;
+        Q.root_entry = qi;
+        Q.done = 0;
+    }
+    char *s = P.wl_slots + (size_t)slot * P.slot_bytes;
+    NodeHdr *h = (NodeHdr *)s;
+    if (threadIdx.x == 0) {
+        h->S = 0; h->comp = qi; h->lo = 0; h->hi = np - 1; h->clo = 0; h->chi = np - 1;
+        h->op = -1; h->q = qi; h->cov_empty = 1; h->depth = 0;
+    }
+    T *dd = (T *)(s + sizeof(NodeHdr));
+    const int lim = align_up(np, V);
+    for (int v = threadIdx.x; v < lim; v += blockDim.x)
+        dd[v] = v < np ? (T)(Q.rp2[v + 1] - Q.rp2[v]) : (T)0;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) P.wl_seq[slot] = (unsigned)slot + 1u;
+}
+
+__global__ void search_roots_publish(SearchParams P, int nroots)
+{
+    P.ctl[kWlTail] = (unsigned long long)nroots;
+    P.ctl[kWlCount] = (unsigned long long)nroots;
+    P.ctl[kRemaining] = (unsigned long long)nroots;
+}
+
+}  // namespace vcg
+
+// ---------------------------------------------------------------- host side
+
+#include "vc_internal.h"
+
+namespace vcg {
+
+template <typename T, int WT>
+static cudaError_t plan_one(int threads, size_t smem, int *blocks_per_sm)
+{
+    cudaError_t e = cudaFuncSetAttribute(search_kernel<T, WT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, search_kernel<T, WT>, threads, smem);
+}
+
+template <typename T>
+static int plan_t(int team_req, int ncap, int wcap, int sms, SearchPlan *pl)
+{
+    const int wsm = align_up(worker_smem_bytes<T>(ncap, wcap), 16);
+    const int kMaxSmem = 227 * 1024;
+    pl->dtype = sizeof(T);
+    pl->slot_bytes = slot_bytes_for<T>(ncap, wcap);
+    bool warp = team_req == 32 || (team_req == 0 && wsm <= 12 * 1024);
+    int bps = 0;
+    if (warp) {
+        int wpb = kMaxSmem / wsm;
+        if (wpb > 8) wpb = 8;
+        if (wpb < 1) return VC_ECAPACITY;
+        pl->warp_team = 1;
+        pl->threads = 32 * wpb;
+        pl->smem = (size_t)wpb * wsm;
+        if (plan_one<T, 1>(pl->threads, pl->smem, &bps) != cudaSuccess) return VC_ECUDA;
+    } else {
+        if (wsm > kMaxSmem) return VC_ECAPACITY;
+        int th = team_req >= 64 ? team_req : (ncap > 4096 ? 512 : 256);
+        pl->warp_team = 0;
+        pl->threads = th;
+        pl->smem = (size_t)wsm;
+        if (plan_one<T, 0>(pl->threads, pl->smem, &bps) != cudaSuccess) return VC_ECUDA;
+    }
+    if (bps < 1) return VC_ECAPACITY;
+    pl->blocks = bps * sms;
+    pl->workers = pl->blocks * (pl->warp_team ? pl->threads / 32 : 1);
+    return VC_OK;
+}
+
+int search_plan(int dtype, int team_req, int ncap, int wcap, int sms, SearchPlan *out)
+{
+    switch (dtype) {
+    case 1: return plan_t<uint8_t>(team_req, ncap, wcap, sms, out);
+    case 2: return plan_t<uint16_t>(team_req, ncap, wcap, sms, out);
+    default: return plan_t<uint32_t>(team_req, ncap, wcap, sms, out);
+    }
+}
+
+template <typename T>
+static cudaError_t run_t(const SearchPlan &pl, SearchParams &P, const int *d_root_slot, int nq, int nroots,
+                         cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1)
+{
+    search_init_kernel<T><<<256, 256, 0, s>>>(P, nq);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    search_roots_kernel<T><<<nq, 256, 0, s>>>(P, d_root_slot);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    search_roots_publish<<<1, 1, 0, s>>>(P, nroots);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (ev0) cudaEventRecord(ev0, s);
+    if (pl.warp_team)
+        search_kernel<T, 1><<<pl.blocks, pl.threads, pl.smem, s>>>(P);
+    else
+        search_kernel<T, 0><<<pl.blocks, pl.threads, pl.smem, s>>>(P);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (ev1) cudaEventRecord(ev1, s);
+    return cudaSuccess;
+}
+
+cudaError_t search_run(const SearchPlan &pl, SearchParams &P, const int *d_root_slot, int nq, int nroots,
+                       cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1)
+{
+    switch (pl.dtype) {
+    case 1: return run_t<uint8_t>(pl, P, d_root_slot, nq, nroots, s, ev0, ev1);
+    case 2: return run_t<uint16_t>(pl, P, d_root_slot, nq, nroots, s, ev0, ev1);
+    default: return run_t<uint32_t>(pl, P, d_root_slot, nq, nroots, s, ev0, ev1);
+    }
+}
+
+}  // namespace vcg

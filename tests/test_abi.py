@@ -1,0 +1,93 @@
+"""The C-ABI library builds for sm_103a, loads, and exports every function the
+public header declares; the ctypes structs match the C layout.  No GPU
+needed (no compute call is made)."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "vc_gb300.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2512_18334_gb300 import build
+    build.build()
+    import paper_2512_18334_gb300._lib as L
+    return L
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(vc_[a-z_]+)\s*\(", text)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for must in ["vc_load_csr", "vc_solve_min", "vc_solve_k", "vc_free", "vc_strerror",
+                 "vc_solve_batch", "vc_load_csr_device", "vc_options_default"]:
+        assert must in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    out = subprocess.run(["nm", "-D", "--defined-only", lib.lib_path()], capture_output=True,
+                         text=True, check=True).stdout
+    exported = set(re.findall(r"\bT (vc_\w+)", out))
+    missing = [f for f in declared_functions() if f not in exported]
+    assert not missing, missing
+    L = lib.lib()
+    for f in declared_functions():
+        assert hasattr(L, f)
+        assert f in lib.SIGNATURES, f"binding lacks a signature for {f}"
+
+
+def test_build_targets_sm_103a_only():
+    from paper_2512_18334_gb300 import build
+    assert build.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
+
+
+def test_strerror_without_gpu(lib):
+    L = lib.lib()
+    assert L.vc_strerror(0).decode() == "ok"
+    assert "malformed" in L.vc_strerror(-1).decode()
+    assert L.vc_strerror(-99).decode() == "unknown status"
+
+
+def test_struct_layout_matches_header(lib, tmp_path):
+    src = tmp_path / "layout.c"
+    src.write_text(r'''
+#include <stdio.h>
+#include <stddef.h>
+#include "vc_gb300.h"
+int main(void) {
+  printf("%zu %zu %zu %zu %zu %zu\n", sizeof(vc_options), offsetof(vc_options, node_budget),
+         sizeof(vc_stats), offsetof(vc_stats, n), offsetof(vc_stats, ms_root),
+         offsetof(vc_stats, comp_hist));
+  return 0;
+}
+''')
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    vals = [int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True,
+                                           check=True).stdout.split()]
+    O, S = lib.Options, lib.Stats
+    assert vals == [ctypes.sizeof(O), O.node_budget.offset, ctypes.sizeof(S), S.n.offset,
+                    S.ms_root.offset, S.comp_hist.offset]
+
+
+def test_options_default_without_gpu(lib):
+    import paper_2512_18334_gb300 as vc
+    o = vc.options()
+    assert o.use_components == 1 and o.load_balance == 1 and o.idle_timeout_ms == 60000
+
+
+def test_missing_library_fails_loudly(tmp_path, monkeypatch):
+    import paper_2512_18334_gb300._lib as L
+    monkeypatch.setattr(L, "_LIB_FILE", str(tmp_path / "nope.so"))
+    monkeypatch.setattr(L, "_lib", None)
+    with pytest.raises(ImportError):
+        L.lib()

@@ -1,0 +1,224 @@
+"""GPU parity: the CUDA solver (through the C ABI) against the CPU oracle.
+
+Answers (minimum cover size, PVC yes/no) must match bit-exactly; covers are
+not unique, so every returned cover is verified edge by edge and its size
+checked against the answer.
+"""
+import numpy as np
+import pytest
+
+import graphgen as gg
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def vc():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    from paper_2512_18334_gb300 import build
+    build.build()
+    import paper_2512_18334_gb300 as m
+    return m
+
+
+def check_cover(g, cover, size):
+    flags = np.zeros(max(g.n, 1), np.uint8)
+    flags[cover] = 1
+    assert len(cover) == size
+    assert len(np.unique(cover)) == len(cover)
+    assert np.all(np.diff(cover) > 0)                       # ascending ids
+    assert oracle.verify_cover(g.n, g.row_ptr, g.col, flags[:g.n])
+
+
+def gpu_min(vc, g, **kw):
+    dg = vc.Graph.from_csr(g.row_ptr, g.col)
+    try:
+        size, cover, st = vc.solve_min(dg, **kw)
+    finally:
+        dg.close()
+    check_cover(g, cover, size)
+    return size, st
+
+
+# ------------------------------------------------ Erdos-Renyi G(80, 200)
+
+@pytest.mark.parametrize("seed", range(24))
+def test_gnm_80_200(vc, seed):
+    g = gg.gnm(80, 200, seed)
+    want = oracle.mvc(g.n, g.row_ptr, g.col)[0]
+    assert gpu_min(vc, g)[0] == want
+
+
+def test_brute_force_small_random(vc):
+    rng = np.random.default_rng(11)
+    for seed in range(120):
+        n = int(rng.integers(8, 23))
+        g = gg.gnp(n, [0.1, 0.2, 0.3, 0.45, 0.6][seed % 5], seed)
+        assert gpu_min(vc, g)[0] == oracle.brute_mvc(g.n, g.row_ptr, g.col)[0], (n, seed)
+
+
+def test_closed_forms(vc):
+    cases = [(gg.path(2001), 1000), (gg.cycle(1001), 501), (gg.cycle(1000), 500),
+             (gg.complete(40), 39), (gg.complete_bipartite(30, 45), 30), (gg.petersen(), 6),
+             (gg.star(500), 1), (gg.complete(2), 1), (gg.cycle(3), 2), (gg.cycle(5), 3)]
+    for g, want in cases:
+        assert gpu_min(vc, g)[0] == want, g.name
+
+
+def test_forests(vc):
+    for seed in range(6):
+        g = gg.random_forest(5000, 1 + 3 * seed, seed)
+        assert gpu_min(vc, g)[0] == oracle.mvc(g.n, g.row_ptr, g.col)[0]
+
+
+def test_components_cliques_cycles(vc):
+    parts = [gg.cycle(5), gg.cycle(7), gg.cycle(4), gg.complete(4), gg.complete(6),
+             gg.cycle(9), gg.complete(3), gg.petersen(), gg.gnm(30, 70, 3), gg.gnm(25, 60, 4)]
+    u = gg.disjoint_union(parts)
+    want = oracle.mvc(u.n, u.row_ptr, u.col)[0]
+    assert gpu_min(vc, u)[0] == want
+    # hang the parts off one hub so the split happens inside the search
+    uu, vv = gg.edges_of(u)
+    hub = u.n
+    offs = np.cumsum([0] + [p.n for p in parts[:-1]])
+    h = gg.from_edges(u.n + 1, np.concatenate([uu, np.full(len(parts), hub)]),
+                      np.concatenate([vv, offs]))
+    assert gpu_min(vc, h)[0] == oracle.mvc(h.n, h.row_ptr, h.col)[0]
+
+
+def test_edge_cases(vc):
+    empty = gg.from_edges(0, [], [])
+    dg = vc.Graph.from_csr(empty.row_ptr, empty.col)
+    assert vc.solve_min(dg)[0] == 0
+    dg.close()
+    iso = gg.from_edges(7, [], [])
+    assert gpu_min(vc, iso)[0] == 0
+    assert gpu_min(vc, gg.path(2))[0] == 1
+    k2s = gg.disjoint_union([gg.path(2)] * 9 + [gg.from_edges(3, [], [])])
+    assert gpu_min(vc, k2s)[0] == 9
+
+
+@pytest.mark.parametrize("copies,copy_n,chain", [(8, 48, 4), (16, 48, 4), (32, 48, 6)])
+def test_component_heavy_small(vc, copies, copy_n, chain):
+    g = gg.component_heavy(1, copies=copies, copy_n=copy_n, p=0.12, chain=chain)
+    want = oracle.mvc(g.n, g.row_ptr, g.col, node_budget=5_000_000)[0]
+    size, st = gpu_min(vc, g)
+    assert size == want
+    assert st["component_branches"] > 0
+
+
+def test_chung_lu_50k(vc):
+    g = gg.chung_lu(50_000, 2.5, 6.0, 2000.0, 0)
+    want = oracle.mvc(g.n, g.row_ptr, g.col)[0]
+    size, st = gpu_min(vc, g)
+    assert size == want
+    assert st["n_induced"] <= 64
+
+
+def test_options_same_answers(vc):
+    for seed in range(6):
+        g = gg.gnm(80, 200, 100 + seed)
+        want = oracle.mvc(g.n, g.row_ptr, g.col)[0]
+        for kw in [dict(use_components=0), dict(team=32), dict(team=256), dict(dtype_bytes=2),
+                   dict(dtype_bytes=4), dict(load_balance=0), dict(stack_depth=2, worklist_capacity=64)]:
+            assert gpu_min(vc, g, **kw)[0] == want, kw
+
+
+def test_pvc_at_opt_and_opt_minus_one(vc):
+    for seed in range(10):
+        g = gg.gnm(80, 200, seed)
+        opt = oracle.mvc(g.n, g.row_ptr, g.col)[0]
+        dg = vc.Graph.from_csr(g.row_ptr, g.col)
+        yes, cover, _ = vc.solve_k(dg, opt)
+        assert yes
+        assert len(cover) <= opt
+        check_cover(g, cover, len(cover))
+        no, cover2, _ = vc.solve_k(dg, opt - 1)
+        assert not no and cover2 is None
+        assert vc.solve_k(dg, opt + 5)[0]
+        dg.close()
+
+
+def test_pvc_k_zero(vc):
+    g = gg.from_edges(5, [], [])
+    dg = vc.Graph.from_csr(g.row_ptr, g.col)
+    assert vc.solve_k(dg, 0)[0]
+    dg.close()
+    g = gg.path(3)
+    dg = vc.Graph.from_csr(g.row_ptr, g.col)
+    assert not vc.solve_k(dg, 0)[0]
+    with pytest.raises(vc.VcError):
+        vc.solve_k(dg, -1)
+    dg.close()
+
+
+def test_batch_matches_single(vc):
+    graphs = [gg.gnm(80, 200, s) for s in range(12)] + [gg.chung_lu(600, 2.5, 4.0, 100.0, s) for s in range(4)]
+    opts = [oracle.mvc(g.n, g.row_ptr, g.col)[0] for g in graphs]
+    dgs = [vc.Graph.from_csr(g.row_ptr, g.col) for g in graphs]
+    # each graph at minimum, at k = opt and at k = opt - 1
+    qg = dgs + dgs + dgs
+    ks = [-1] * len(dgs) + opts + [o - 1 for o in opts]
+    sizes, yes, status, covers, st = vc.solve_batch(qg, ks)
+    assert np.all(status == 0)
+    n = len(dgs)
+    for i, g in enumerate(graphs):
+        assert sizes[i] == opts[i]
+        check_cover(g, covers[i], sizes[i])
+        assert yes[n + i] and len(covers[n + i]) <= opts[i]
+        check_cover(g, covers[n + i], len(covers[n + i]))
+        assert not yes[2 * n + i] and len(covers[2 * n + i]) == 0
+    for d in dgs:
+        d.close()
+
+
+def test_device_resident_input(vc):
+    import torch
+    g = gg.gnm(80, 200, 5)
+    rp = torch.from_numpy(g.row_ptr).cuda()
+    col = torch.from_numpy(g.col).cuda()
+    dg = vc.Graph.from_device(rp, col)
+    size, cover, _ = vc.solve_min(dg)
+    dg.close()
+    assert size == oracle.mvc(g.n, g.row_ptr, g.col)[0]
+    check_cover(g, cover, size)
+
+
+def test_invalid_csr_rejected(vc):
+    bad = [
+        (np.array([0, 1, 1], np.int32), np.array([1], np.int32)),          # asymmetric
+        (np.array([0, 1, 2], np.int32), np.array([0, 1], np.int32)),       # self-loops
+        (np.array([0, 2, 4], np.int32), np.array([1, 1, 0, 0], np.int32)),  # duplicates
+        (np.array([0, 1, 2], np.int32), np.array([5, 0], np.int32)),       # out of range
+        (np.array([0, 2, 1], np.int32), np.array([1, 0], np.int32)),       # row_ptr decreasing
+    ]
+    for rp, col in bad:
+        with pytest.raises(vc.VcError) as ei:
+            vc.Graph.from_csr(rp, col)
+        assert ei.value.status == vc.VC_EINVAL
+
+
+def test_node_budget_reports_cleanly(vc):
+    g = gg.gnm(120, 330, 0)
+    dg = vc.Graph.from_csr(g.row_ptr, g.col)
+    with pytest.raises(vc.VcError) as ei:
+        vc.solve_min(dg, node_budget=1)
+    assert ei.value.status in (vc.VC_EBUDGET,)
+    # the handle stays usable
+    size, cover, _ = vc.solve_min(dg)
+    dg.close()
+    assert size == oracle.mvc(g.n, g.row_ptr, g.col)[0]
+
+
+def test_registry_exhaustion_reports_cleanly(vc):
+    g = gg.component_heavy(2, copies=16, copy_n=48, p=0.12, chain=4)
+    dg = vc.Graph.from_csr(g.row_ptr, g.col)
+    with pytest.raises(vc.VcError) as ei:
+        vc.solve_min(dg, registry_capacity=1)
+    assert ei.value.status == vc.VC_ECAPACITY
+    size, _, _ = vc.solve_min(dg)
+    dg.close()
+    assert size == oracle.mvc(g.n, g.row_ptr, g.col, node_budget=5_000_000)[0]
