@@ -1,0 +1,310 @@
+#!/usr/bin/env python
+"""Benchmark: exact minimum vertex cover on one GB300 per rank.
+
+Workload (one step = one exact MVC solve through the C ABI, root reduction,
+induced subgraph, search and witness included):
+    Chung-Lu power-law graph, n = 50,000, exponent 2.5, mean degree 6,
+    maximum degree 2,000, int32 CSR, seed 1000 + rank (synthetic; the paper's
+    datasets are not available).
+
+value   graphs/s over all ranks, CSR already resident in HBM, L2 flushed
+        (256 MiB write) before every timed step
+e2e     the same metric through vc_load_csr from pinned host memory, the
+        solve, and the cover read back to the host, every step
+roofline of the dominant kernel (root reduction), achieved algorithmic bytes
+        per launch / its CUDA-event duration vs the measured HBM copy peak
+cpu_baseline  the CPU oracle (sequential Algorithm 2 in C) on the same graph
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import graphgen as gg  # noqa: E402
+
+METRIC = "graphs/sec & search-tree nodes/sec at exact MVC; p99 latency; batched vs plain"
+WORKLOAD = dict(workload="chung_lu_50k", n=50_000, gamma=2.5, avg_deg=6.0, max_deg=2000.0)
+L2_FLUSH_BYTES = 256 << 20
+
+
+def make_graph(rank: int):
+    w = WORKLOAD
+    return gg.chung_lu(w["n"], w["gamma"], w["avg_deg"], w["max_deg"], 1000 + rank)
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ reference arm
+
+def cpu_oracle_run(steps: int, warmup: int):
+    """The oracle as it stands, on this host: one workload graph per step."""
+    import oracle
+    oracle.build()
+    g = make_graph(0)
+    for _ in range(warmup):
+        oracle.mvc(g.n, g.row_ptr, g.col)
+    t0 = time.perf_counter()
+    size = None
+    for _ in range(steps):
+        size = oracle.mvc(g.n, g.row_ptr, g.col)[0]
+    dt = time.perf_counter() - t0
+    return steps / dt, dt / steps * 1e3, size
+
+
+def reference_main(args, rank, world):
+    if rank != 0:
+        return
+    value, ms, size = cpu_oracle_run(args.steps, args.warmup)
+    sample = (f"full {WORKLOAD['workload']} graph (seed 1000), {args.steps} timed solves after "
+              f"{args.warmup} warm-up, single thread")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": round(value, 6), "unit": "graphs/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+        "data": "synthetic", "config": dict(WORKLOAD, seed=1000, answer=size),
+        "cpu_baseline": {"value": round(value, 6), "unit": "graphs/s", "cores": 1, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": round(value, 6), "unit": "graphs/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ our arm
+
+def root_algorithmic_bytes(g, st) -> int:
+    """Bytes the root phase must move at least once: read the CSR, write the
+    cover flags and the forced list, write the induced CSR and its id map."""
+    csr = 4 * (g.n + 1) + 4 * int(g.row_ptr[-1])
+    outs = g.n + 4 * st["forced"] + 4 * (st["n_induced"] + 1) + 8 * st["m_induced"] + 4 * st["n_induced"]
+    return csr + outs
+
+
+def ours_main(args, rank, world, local_rank):
+    import torch
+    import paper_2512_18334_gb300 as vc
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    g = make_graph(rank)
+    dg = vc.Graph.from_csr(g.row_ptr, g.col, stream=stream)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+
+    def barrier():
+        torch.cuda.synchronize(dev)
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize(dev)
+
+    # ---- warm-up (also checks the answer against the library's own verify path)
+    for _ in range(max(args.warmup, 3)):
+        size, cover, st = vc.solve_min(dg)
+    flags = np.zeros(g.n, np.uint8)
+    flags[cover] = 1
+    src = np.repeat(np.arange(g.n), np.diff(g.row_ptr))
+    assert len(cover) == size and np.all(flags[src] | flags[g.col]), "cover check failed"
+
+    # ---- timed: device-resident input, L2 flushed before each step
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    barrier()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    step_ms, root_ms, search_ms, nodes, launches = [], [], [], 0, 0
+    for _ in range(args.steps):
+        flush.fill_(0)
+        ev0.record(stream)
+        size_k, _, st = vc.solve_min(dg, want_cover=True)
+        ev1.record(stream)
+        ev1.synchronize()
+        step_ms.append(ev0.elapsed_time(ev1))
+        root_ms.append(st["ms_root"])
+        search_ms.append(st["ms_search"])
+        nodes += st["nodes"]
+        launches += st["launches"]       # the L2-flush fill is torch's kernel, not counted
+    barrier()
+    clk = clocks.stop()
+    total_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = world * args.steps / (total_ms / 1e3)
+    p99 = float(np.percentile(step_ms, 99))
+
+    # ---- e2e: pinned host CSR -> vc_load_csr -> solve -> cover to host -> free
+    rp_h = torch.from_numpy(g.row_ptr).pin_memory()
+    col_h = torch.from_numpy(g.col).pin_memory()
+    h2d = (rp_h.numel() + col_h.numel()) * 4
+    e2e_ms, d2h = [], 0
+    barrier()
+    for _ in range(args.steps):
+        flush.fill_(0)
+        ev0.record(stream)
+        h = vc.Graph.from_csr(rp_h.numpy(), col_h.numpy(), stream=stream)
+        s2, cov2, _ = vc.solve_min(h)
+        h.close()
+        ev1.record(stream)
+        ev1.synchronize()
+        e2e_ms.append(ev0.elapsed_time(ev1))
+        d2h = 4 * len(cov2) + 4
+    barrier()
+    e2e_total = sum(e2e_ms)
+    if world > 1:
+        t = torch.tensor([e2e_total], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_total = float(t.item())
+    e2e_value = world * args.steps / (e2e_total / 1e3)
+
+    # ---- roofline of the dominant kernel (root reduction), timed by the
+    # library with CUDA events on the launching stream
+    peak, peak_kind = load_peaks()
+    mean_root_ms = statistics.mean(root_ms)
+    achieved = root_algorithmic_bytes(g, st) / (mean_root_ms / 1e3) / 1e9
+    roofline = {"bound": "hbm", "kernel": "root_kernel", "achieved": round(achieved, 3),
+                "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
+                "frac": round(achieved / peak, 6), "traffic": None,
+                "algorithmic_bytes": root_algorithmic_bytes(g, st), "ms_per_launch": round(mean_root_ms, 4)}
+
+    # ---- CPU baseline: the oracle on a bounded sample (rank 0, N = 1 only)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, ms, osize = cpu_oracle_run(steps=2, warmup=0)
+        assert osize == size, (osize, size)
+        cpu = {"value": round(v, 6), "unit": "graphs/s", "cores": 1, "kind": "oracle",
+               "sample": "2 solves of the same workload graph (seed 1000), single thread"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": round(value, 3), "unit": "graphs/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(total_ms / args.steps, 4),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+            "data": "synthetic", "impl": "ours",
+            "config": dict(WORKLOAD, seed=1000 + rank, answer=size, n_induced=st["n_induced"],
+                           forced=st["forced"], l2="256 MiB write before every timed step",
+                           parallelism=f"replicas x{world}"),
+            "p99_ms": round(p99, 4),
+            "nodes_per_sec": round(nodes / (total_ms / 1e3), 1),
+            "ms_root_kernel": round(mean_root_ms, 4),
+            "ms_search_kernel": round(statistics.mean(search_ms), 4),
+            "root_rounds": st["root_rounds"], "root_cycles": st["root_cycles"],
+            "e2e": {"value": round(e2e_value, 3), "unit": "graphs/s", "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h},
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "clocks": clk,
+            "gpu_launches": launches,
+        }
+        print(json.dumps(line), flush=True)
+    dg.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    rank, world, local_rank = dist_env()
+    if args.impl == "reference":
+        reference_main(args, rank, world)
+    else:
+        ours_main(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    main()

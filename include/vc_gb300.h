@@ -82,10 +82,14 @@ typedef struct vc_stats {
     int32_t team;               /* threads per worker used                          */
     int32_t workers;            /* persistent workers launched                      */
     int32_t max_stack;          /* deepest private stack seen                       */
-    int32_t reserved;
+    int32_t err_where;          /* diagnostic site code of the first device error   */
+    int32_t launches;           /* kernels this call launched                       */
+    int32_t root_rounds;        /* synchronous rule rounds in the root phase        */
     double ms_root;             /* root reduction + induced subgraph (device)       */
     double ms_search;           /* persistent search kernel (device)                */
     double ms_total;            /* whole call, host wall clock                      */
+    int64_t root_cycles[4];     /* SM cycles in the root phase: rules without a
+                                   bound, greedy bound, rules with the bound, induce */
 } vc_stats;
 
 /* Fill *opt with the defaults. */

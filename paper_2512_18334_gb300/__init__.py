@@ -111,7 +111,7 @@ def solve_min(g: Graph, opts: Options | None = None, want_cover: bool = True, **
     st = Stats()
     _L.check(_L.lib().vc_solve_min(g._h, ctypes.byref(o), ctypes.byref(size),
                                    cover.ctypes.data_as(ctypes.c_void_p) if want_cover else None,
-                                   ctypes.byref(clen), ctypes.byref(st)))
+                                   ctypes.byref(clen), ctypes.byref(st)), st)
     return size.value, (cover[:clen.value].copy() if want_cover else None), st.to_dict()
 
 
@@ -124,7 +124,7 @@ def solve_k(g: Graph, k: int, opts: Options | None = None, want_cover: bool = Tr
     st = Stats()
     _L.check(_L.lib().vc_solve_k(g._h, int(k), ctypes.byref(o), ctypes.byref(yes),
                                  cover.ctypes.data_as(ctypes.c_void_p) if want_cover else None,
-                                 ctypes.byref(clen), ctypes.byref(st)))
+                                 ctypes.byref(clen), ctypes.byref(st)), st)
     return bool(yes.value), (cover[:clen.value].copy() if want_cover and yes.value else None), st.to_dict()
 
 
@@ -152,6 +152,6 @@ def solve_batch(graphs, ks=None, opts: Options | None = None, want_covers: bool 
                                  status.ctypes.data_as(ctypes.c_void_p), cov_ptrs,
                                  lens.ctypes.data_as(ctypes.c_void_p), ctypes.byref(st))
     if raise_on_error:
-        _L.check(rc)
+        _L.check(rc, st)
     covers = [b[:l].copy() for b, l in zip(bufs, lens)] if want_covers else None
     return sizes, yes.astype(bool), status, covers, st.to_dict()

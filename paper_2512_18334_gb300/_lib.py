@@ -22,9 +22,10 @@ _lib = None
 
 
 class VcError(RuntimeError):
-    def __init__(self, status: int, msg: str):
+    def __init__(self, status: int, msg: str, stats: dict | None = None):
         super().__init__(f"{msg} (status {status})")
         self.status = status
+        self.stats = stats
 
 
 class Options(ctypes.Structure):
@@ -59,10 +60,13 @@ class Stats(ctypes.Structure):
         ("team", ctypes.c_int32),
         ("workers", ctypes.c_int32),
         ("max_stack", ctypes.c_int32),
-        ("reserved", ctypes.c_int32),
+        ("err_where", ctypes.c_int32),
+        ("launches", ctypes.c_int32),
+        ("root_rounds", ctypes.c_int32),
         ("ms_root", ctypes.c_double),
         ("ms_search", ctypes.c_double),
         ("ms_total", ctypes.c_double),
+        ("root_cycles", ctypes.c_int64 * 4),
     ]
 
     def to_dict(self) -> dict:
@@ -71,7 +75,9 @@ class Stats(ctypes.Structure):
             v = getattr(self, name)
             if name == "comp_hist":
                 d[name] = {i + 2: int(v[i]) for i in range(16) if v[i]}
-            elif name != "reserved":
+            elif name == "root_cycles":
+                d[name] = [int(x) for x in v]
+            else:
                 d[name] = v
         return d
 
@@ -116,6 +122,6 @@ def strerror(status: int) -> str:
     return lib().vc_strerror(int(status)).decode()
 
 
-def check(status: int) -> None:
+def check(status: int, stats=None) -> None:
     if status != VC_OK:
-        raise VcError(int(status), strerror(status))
+        raise VcError(int(status), strerror(status), stats.to_dict() if stats is not None else None)

@@ -110,7 +110,7 @@ size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 size_t query_scratch_bytes(int n, int m2)
 {
     const size_t ni = (size_t)(n > 0 ? n : 1);
-    return 6 * align256(ni * 4)                   // deg aux fr0 fr1 flag forced_list
+    return 7 * align256(ni * 4)                   // deg aux fr0 fr1 flag forced_list heavy
            + 2 * align256(ni)                     // st cover_flags
            + align256((ni + 1) * 4)               // rp2
            + align256((size_t)(m2 > 0 ? m2 : 1) * 4)  // col2
@@ -128,6 +128,7 @@ void carve_query_scratch(QueryDesc &Q, char *base)
     Q.fr1 = (int *)take(ni * 4);
     Q.flag = (int *)take(ni * 4);
     Q.forced_list = (int *)take(ni * 4);
+    Q.heavy = (int *)take(ni * 4);
     Q.st = (uint8_t *)take(ni);
     Q.cover_flags = (uint8_t *)take(ni);
     Q.rp2 = (int *)take((ni + 1) * 4);
@@ -151,6 +152,7 @@ struct vc_graph {
     cudaStream_t stream = nullptr;
     int n = 0;
     int m2 = 0;
+    int maxdeg = 0;
     DevBuf rp, col, err;
     Workspace ws;
 };
@@ -207,6 +209,7 @@ int solve_queries(vc_graph *g0, const std::vector<QueryRef> &qs, const vc_option
         Q.rp = qs[i].g->rp.as<int>();
         Q.col = qs[i].g->col.as<int>();
         Q.k = qs[i].k;
+        Q.maxdeg_in = qs[i].g->maxdeg;
         Q.status = VC_OK;
         carve_query_scratch(Q, ws.qscratch.as<char>() + offs[i]);
     }
@@ -215,7 +218,12 @@ int solve_queries(vc_graph *g0, const std::vector<QueryRef> &qs, const vc_option
 
     // ---- phase 1: root reduction and induced subgraphs
     VC_CK(cudaEventRecord(ws.ev[0], s));
-    VC_CK(root_run(dq, nq, s));
+    int max_n_in = 0, max_deg_in = 0;
+    for (int i = 0; i < nq; i++) {
+        max_n_in = std::max(max_n_in, qs[i].g->n);
+        max_deg_in = std::max(max_deg_in, qs[i].g->maxdeg);
+    }
+    VC_CK(root_run(dq, nq, max_n_in, max_deg_in, s));
     VC_CK(cudaEventRecord(ws.ev[1], s));
     VC_CK(cudaMemcpyAsync(hq, dq, sizeof(QueryDesc) * nq, cudaMemcpyDeviceToHost, s));
     VC_CK(cudaStreamSynchronize(s));
@@ -255,10 +263,14 @@ int solve_queries(vc_graph *g0, const std::vector<QueryRef> &qs, const vc_option
         int wl_cap = opt.worklist_capacity > 0 ? next_pow2(opt.worklist_capacity)
                                                : next_pow2(std::max(4 * pl.workers, 1024));
         wl_cap = std::max(wl_cap, next_pow2(nroots));
-        int reg_cap = opt.registry_capacity > 0 ? opt.registry_capacity
-                                                : std::max(1 << 16, 64 * pl.workers);
-        const size_t reg_word_budget = (size_t)16 << 30;
-        if ((size_t)reg_cap * wcap * 4 > reg_word_budget) reg_cap = (int)(reg_word_budget / ((size_t)wcap * 4));
+        // registry entries are bump-allocated (nothing to initialise), so a
+        // large capacity only costs address space: up to ~8 GB or 4M entries
+        int reg_cap = opt.registry_capacity;
+        if (reg_cap <= 0) {
+            const size_t per_entry = sizeof(RegEntry) + (size_t)wcap * 4;
+            reg_cap = (int)std::min<size_t>((size_t)4 << 20, ((size_t)8 << 30) / per_entry);
+            reg_cap = std::max(reg_cap, 64 * pl.workers);
+        }
         reg_cap += nq;
 
         if ((rc = ws.stack.ensure((size_t)pl.workers * depth * pl.slot_bytes)) != VC_OK) return rc;
@@ -311,7 +323,7 @@ int solve_queries(vc_graph *g0, const std::vector<QueryRef> &qs, const vc_option
     float ms_root = 0.f;
     VC_CK(cudaEventElapsedTime(&ms_root, ws.ev[0], ws.ev[1]));
 
-    const int kstatus = (int)(int64_t)hctl_local[kStatus];
+    const int kstatus = (int)(int64_t)ctlw(hctl_local, kStatus);
     // ---- covers: one device-to-host copy of every cover list
     size_t total = 0;
     std::vector<size_t> coff(nq);
@@ -342,14 +354,16 @@ int solve_queries(vc_graph *g0, const std::vector<QueryRef> &qs, const vc_option
     }
     if (stats) {
         memset(stats, 0, sizeof(*stats));
-        stats->nodes = (int64_t)hctl_local[kNodes];
-        stats->component_branches = (int64_t)hctl_local[kCompBranches];
-        stats->leaves = (int64_t)hctl_local[kLeaves];
-        stats->pruned = (int64_t)hctl_local[kPruned];
-        stats->offloaded = (int64_t)hctl_local[kOffloaded];
-        stats->trivial_components = (int64_t)hctl_local[kTrivial];
-        for (int b = 0; b < 16 && b < kHistBins; b++) stats->comp_hist[b] = (int64_t)hctl_local[kHist + b];
+        stats->nodes = (int64_t)ctlw(hctl_local, kNodes);
+        stats->component_branches = (int64_t)ctlw(hctl_local, kCompBranches);
+        stats->leaves = (int64_t)ctlw(hctl_local, kLeaves);
+        stats->pruned = (int64_t)ctlw(hctl_local, kPruned);
+        stats->offloaded = (int64_t)ctlw(hctl_local, kOffloaded);
+        stats->trivial_components = (int64_t)ctlw(hctl_local, kTrivial);
+        for (int b = 0; b < 16 && b < kHistBins; b++) stats->comp_hist[b] = (int64_t)ctlw(hctl_local, kHist + b);
         for (int i = 0; i < nq; i++) {
+            stats->root_rounds += hq[i].rounds;
+            for (int c = 0; c < 4; c++) stats->root_cycles[c] += hq[i].root_cycles[c];
             stats->n += hq[i].n;
             stats->n_induced += hq[i].np;
             stats->m_induced += hq[i].m2p / 2;
@@ -359,7 +373,9 @@ int solve_queries(vc_graph *g0, const std::vector<QueryRef> &qs, const vc_option
         stats->dtype_bytes = nroots ? pl.dtype : 0;
         stats->team = nroots ? (pl.warp_team ? 32 : pl.threads) : 0;
         stats->workers = nroots ? pl.workers : 0;
-        stats->max_stack = (int32_t)hctl_local[kMaxStack];
+        stats->max_stack = (int32_t)ctlw(hctl_local, kMaxStack);
+        stats->err_where = (int32_t)ctlw(hctl_local, kErrWhere);
+        stats->launches = nroots > 0 ? 6 : 2;   // root [+ init, roots, publish, search] + finalize
         stats->ms_root = ms_root;
         stats->ms_search = ms_search;
         stats->ms_total =
@@ -410,14 +426,15 @@ int load_common(int32_t n, const int32_t *rp, const int32_t *col, bool device_pt
     } else {
         ok = ok && cudaMemsetAsync(g->rp.p, 0, 4, s) == cudaSuccess;
     }
-    int herr[2] = {0, 0};
+    int herr[3] = {0, 0, 0};
     if (ok && n > 0) {
         ok = validate_run(n, m2, g->rp.as<int>(), g->col.as<int>(), g->err.as<int>(), s) == cudaSuccess;
-        ok = ok && cudaMemcpyAsync(herr, g->err.p, 8, cudaMemcpyDeviceToHost, s) == cudaSuccess;
+        ok = ok && cudaMemcpyAsync(herr, g->err.p, 12, cudaMemcpyDeviceToHost, s) == cudaSuccess;
     }
     ok = ok && cudaStreamSynchronize(s) == cudaSuccess;
     if (!ok) { vc_free(g); return VC_ECUDA; }
     if (herr[0] != 0 || (long long)herr[1] * 2 != m2) { vc_free(g); return VC_EINVAL; }
+    g->maxdeg = herr[2];
     *out = g;
     return VC_OK;
 }

@@ -36,7 +36,7 @@ struct QueryDesc {
     const int *rp;
     const int *col;
     int k;               // -1: minimum cover; >= 0: is there a cover <= k?
-    int pad0;
+    int maxdeg_in;       // maximum degree of the input graph
 
     // root-phase scratch (device, >= n entries each unless noted)
     int *deg;            // live degree
@@ -45,6 +45,7 @@ struct QueryDesc {
     int *fr1;
     int *flag;           // frontier membership
     int *forced_list;    // vertices forced into the cover at the root (>= n)
+    int *heavy;          // long rows handed to whole warps (>= n)
     uint8_t *st;         // 0 live, 1 forced into the cover, 2 greedy cover
     uint8_t *cover_flags;// final cover, original numbering (n bytes)
 
@@ -70,6 +71,9 @@ struct QueryDesc {
     int improved;        // 1: the search found a cover better than `bound`
     int cover_len;       // entries written to cover_list
     int done;            // set once when the query is finished during the search
+    int rounds;          // root-phase rule rounds (diagnostics)
+    int pad2;
+    long long root_cycles[4];  // clock64 cycles: phase 1, greedy, phase 2, induce
     int *cover_list;     // ascending original ids (device, >= n)
 };
 
@@ -140,12 +144,14 @@ struct SearchParams {
     int load_balance;
 };
 
-// Control block words (unsigned long long each).
+// Control block: one unsigned long long per entry, each entry on its own
+// 128-byte line (kCtlStride words apart) so that idle workers polling the
+// worklist counter do not serialise with atomics on the other words.
 enum Ctl : int {
-    kWlCount = 0,     // items reserved in the worklist (signed)
+    kWlCount = 0,     // items reserved in the worklist (never negative)
     kWlHead = 1,      // dequeue ticket
     kWlTail = 2,      // enqueue ticket
-    kRegHead = 3,     // registry free-list head {tag:32 | idx:32}
+    kRegHead = 3,     // registry overflow free-list head {tag:32 | idx:32}
     kRemaining = 4,   // queries not finished
     kAbort = 5,       // nonzero: stop everything
     kStatus = 6,      // first error status (as unsigned of a negative int)
@@ -157,9 +163,18 @@ enum Ctl : int {
     kOffloaded = 12,
     kTrivial = 13,
     kMaxStack = 14,
-    kHist = 16,       // kHistBins words
-    kCtlWords = 32
+    kErrWhere = 15,   // where the first error was raised (diagnostics)
+    kRegBump = 16,    // next never-used registry entry
+    kHist = 17,       // kHistBins entries
+    kCtlEntries = 34
 };
+constexpr int kCtlStride = 16;
+constexpr int kCtlWords = kCtlEntries * kCtlStride;
+
+__host__ __device__ __forceinline__ unsigned long long &ctlw(unsigned long long *ctl, int e)
+{
+    return ctl[e * kCtlStride];
+}
 
 // ------------------------------------------------------------------ helpers
 
@@ -215,15 +230,17 @@ __device__ __forceinline__ unsigned long long globaltimer()
     return t;
 }
 
-__device__ __forceinline__ void set_error(unsigned long long *ctl, int status)
+// Record the first error (status and a site code) and stop every worker.
+__device__ __forceinline__ void set_error(unsigned long long *ctl, int status, int where = 0)
 {
-    atomicCAS(&ctl[kStatus], 0ull, (unsigned long long)(unsigned)status);
-    atomicExch(&ctl[kAbort], 1ull);
+    if (atomicCAS(&ctlw(ctl, kStatus), 0ull, (unsigned long long)(unsigned)status) == 0ull)
+        ctlw(ctl, kErrWhere) = (unsigned long long)where;
+    atomicExch(&ctlw(ctl, kAbort), 1ull);
 }
 
-__device__ __forceinline__ bool aborted(const unsigned long long *ctl)
+__device__ __forceinline__ bool aborted(unsigned long long *ctl)
 {
-    return *(volatile const unsigned long long *)&ctl[kAbort] != 0ull;
+    return *(volatile unsigned long long *)&ctlw(ctl, kAbort) != 0ull;
 }
 
 // ------------------------------------------------------------------ teams

@@ -10,7 +10,8 @@ namespace vcg {
 
 // ---- root phase (vc_root.cu)
 cudaError_t validate_run(int n, int m2, const int *rp, const int *col, int *d_err, cudaStream_t s);
-cudaError_t root_run(QueryDesc *d_q, int nq, cudaStream_t s);
+// max_n / max_deg: the largest input graph and degree among the queries
+cudaError_t root_run(QueryDesc *d_q, int nq, int max_n, int max_deg, cudaStream_t s);
 cudaError_t finalize_run(QueryDesc *d_q, int nq, const RegEntry *reg, const uint32_t *reg_words, int wcap,
                          cudaStream_t s);
 

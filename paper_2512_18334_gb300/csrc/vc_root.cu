@@ -68,13 +68,25 @@ __global__ void validate_col_kernel(int n, const int *rp, const int *col, int *e
     if ((threadIdx.x & 31) == 0 && up) atomicAdd(err + 1, up);
 }
 
+// err[2] = maximum degree (row length)
+__global__ void max_degree_kernel(int n, const int *rp, int *err)
+{
+    int dm = 0;
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x)
+        dm = max(dm, rp[v + 1] - rp[v]);
+    dm = __reduce_max_sync(kFull, dm);
+    if ((threadIdx.x & 31) == 0 && dm) atomicMax(err + 2, dm);
+}
+
 // ------------------------------------------------------------ root kernel
 
 constexpr int kRootThreads = 1024;
+constexpr int kHeavyRow = 32;   // rows longer than this are scanned by a whole warp
 
 struct RootShared {
     int cnt;        // marks in this round
     int fcnt;       // next-frontier size
+    int hcnt;       // heavy-row list size
     int forced;
     int delta;      // max live degree seen in the last full scan
     int red[33];
@@ -142,6 +154,21 @@ __device__ __forceinline__ int block_excl_scan(int x, int *red, int *tot)
     return r;
 }
 
+// Append val to list (slot from *counter) for every lane with pred set, with
+// one atomic per warp instead of one per lane.
+__device__ __forceinline__ void agg_append(int *counter, int *list, int val, bool pred)
+{
+    const unsigned act = __activemask();
+    const unsigned m = __ballot_sync(act, pred);
+    if (!pred) return;
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(m) - 1;
+    int base = 0;
+    if (lane == leader) base = atomicAdd(counter, __popc(m));
+    base = __shfl_sync(m, base, leader);
+    list[base + __popc(m & ((1u << lane) - 1))] = val;
+}
+
 __device__ __forceinline__ unsigned mix32(unsigned x)
 {
     x ^= x >> 16; x *= 0x7feb352du;
@@ -150,311 +177,467 @@ __device__ __forceinline__ unsigned mix32(unsigned x)
     return x;
 }
 
-// Queue u for the cover (once per round).
-__device__ __forceinline__ void root_mark(const QueryDesc &Q, RootShared &sh, int u)
-{
-    if (atomicExch(&Q.aux[u], 1) == 0) {
-        int pos = atomicAdd(&sh.cnt, 1);
-        Q.forced_list[sh.forced + pos] = u;
+// Where the per-vertex root state lives.
+// Global: int degrees, byte states, int mark / frontier flags in HBM (any n).
+struct GlobalStore {
+    int *deg;
+    uint8_t *st;
+    int *mark;
+    int *flag;
+    __device__ void bind(QueryDesc &Q, char *) { deg = Q.deg; st = Q.st; mark = Q.aux; flag = Q.flag; }
+    static __host__ __device__ size_t smem_bytes(int) { return 0; }
+    __device__ __forceinline__ int d(int v) const { return deg[v]; }
+    __device__ __forceinline__ void set_d(int v, int x) { deg[v] = x; }
+    __device__ __forceinline__ void dec(int v) { atomicSub(&deg[v], 1); }
+    __device__ __forceinline__ int s(int v) const { return st[v]; }
+    __device__ __forceinline__ void set_s(int v, int x) { st[v] = (uint8_t)x; }
+    __device__ __forceinline__ bool try_mark(int v) { return atomicExch(&mark[v], 1) == 0; }
+    __device__ __forceinline__ bool marked(int v) const { return ((volatile int *)mark)[v] != 0; }
+    __device__ __forceinline__ void reset_mark(int v) { mark[v] = 0; }
+    __device__ __forceinline__ bool try_flag(int v) { return atomicExch(&flag[v], 1) == 0; }
+    __device__ __forceinline__ void reset_flag(int v) { flag[v] = 0; }
+    __device__ void publish(QueryDesc &, int) {}
+};
+
+// Shared: 16-bit degrees, byte states and mark / frontier bitmaps in shared
+// memory (about 3.3 bytes per vertex); needs max degree <= 65535.
+struct SmemStore {
+    uint16_t *deg;
+    uint8_t *st;
+    uint32_t *mark;
+    uint32_t *flag;
+    static __host__ __device__ size_t smem_bytes(int n)
+    {
+        const size_t w = (size_t)(n + 31) / 32 * 4;
+        return ((size_t)n * 2 + 15) / 16 * 16 + ((size_t)n + 15) / 16 * 16 + 2 * ((w + 15) / 16 * 16);
     }
-}
+    __device__ void bind(QueryDesc &Q, char *smem)
+    {
+        const int n = Q.n;
+        const size_t w = (size_t)(n + 31) / 32 * 4;
+        char *p = smem;
+        deg = (uint16_t *)p;  p += ((size_t)n * 2 + 15) / 16 * 16;
+        st = (uint8_t *)p;    p += ((size_t)n + 15) / 16 * 16;
+        mark = (uint32_t *)p; p += (w + 15) / 16 * 16;
+        flag = (uint32_t *)p;
+        for (int i = threadIdx.x; i < (n + 31) / 32; i += blockDim.x) { mark[i] = 0; flag[i] = 0; }
+    }
+    __device__ __forceinline__ int d(int v) const { return deg[v]; }
+    __device__ __forceinline__ void set_d(int v, int x) { deg[v] = (uint16_t)x; }
+    __device__ __forceinline__ void dec(int v)
+    {
+        unsigned *w = (unsigned *)((char *)deg + 2 * (v & ~1));
+        atomicSub(w, 1u << (16 * (v & 1)));
+    }
+    __device__ __forceinline__ int s(int v) const { return st[v]; }
+    __device__ __forceinline__ void set_s(int v, int x) { st[v] = (uint8_t)x; }
+    __device__ __forceinline__ bool try_mark(int v)
+    {
+        const unsigned bit = 1u << (v & 31);
+        return !(atomicOr(&mark[v >> 5], bit) & bit);
+    }
+    __device__ __forceinline__ bool marked(int v) const { return ((volatile uint32_t *)mark)[v >> 5] >> (v & 31) & 1u; }
+    __device__ __forceinline__ void reset_mark(int v) { atomicAnd(&mark[v >> 5], ~(1u << (v & 31))); }
+    __device__ __forceinline__ bool try_flag(int v)
+    {
+        const unsigned bit = 1u << (v & 31);
+        return !(atomicOr(&flag[v >> 5], bit) & bit);
+    }
+    __device__ __forceinline__ void reset_flag(int v) { atomicAnd(&flag[v >> 5], ~(1u << (v & 31))); }
+    // the answer assembly reads the states from global memory
+    __device__ void publish(QueryDesc &Q, int n)
+    {
+        for (int v = threadIdx.x; v < n; v += blockDim.x) Q.st[v] = st[v];
+    }
+};
 
-__device__ __forceinline__ void root_push_frontier(const QueryDesc &Q, RootShared &sh, int *next, int x)
-{
-    if (atomicExch(&Q.flag[x], 1) == 0) next[atomicAdd(&sh.fcnt, 1)] = x;
-}
+template <class Store>
+struct Root {
+    QueryDesc &Q;
+    Store S;
+    RootShared &sh;
+    int n;
+    const int *rp, *col;
 
-// Examine vertex v against the rules; marks go to the round's list.
-__device__ __forceinline__ void root_examine(const QueryDesc &Q, RootShared &sh, int *next, int v,
-                                             int bud)
-{
-    if (Q.st[v] != 0) return;
-    const int d = Q.deg[v];
-    if (d == 0) return;
-    const int *col = Q.col;
-    const int a = Q.rp[v], b = Q.rp[v + 1];
-    if (d == 1) {
-        int u = -1;
-        for (int e = a; e < b; e++) {
-            int x = col[e];
-            if (Q.st[x] == 0 && Q.deg[x] > 0) { u = x; break; }
+    __device__ Root(QueryDesc &q, RootShared &s, char *smem) : Q(q), sh(s)
+    {
+        n = Q.n;
+        rp = Q.rp;
+        col = Q.col;
+        S.bind(Q, smem);
+    }
+
+    __device__ __forceinline__ bool live(int x) const { return S.s(x) == 0 && S.d(x) > 0; }
+
+    __device__ __forceinline__ void mark(int u)
+    {
+        agg_append(&sh.cnt, Q.forced_list + sh.forced, u, S.try_mark(u));
+    }
+
+    __device__ __forceinline__ void push_frontier(int *next, int x)
+    {
+        agg_append(&sh.fcnt, next, x, S.try_flag(x));
+    }
+
+    // The rule decision for v once its live neighbours u (and w) are known.
+    __device__ void decide(int *next, int v, int d, int u, int w)
+    {
+        if (d == 1) {
+            if (u < 0) return;
+            if (S.d(u) == 1 && u < v) push_frontier(next, u);   // u's rule fires instead
+            else mark(u);
+        } else if (d == 2) {
+            if (w < 0) return;
+            if (bsearch_row(col + __ldg(rp + u), __ldg(rp + u + 1) - __ldg(rp + u), w)) {
+                int p = INT_MAX;
+                if (S.d(u) == 2 && u < v) p = u;
+                if (S.d(w) == 2 && w < v && w < p) p = w;
+                if (p != INT_MAX) push_frontier(next, p);   // the lowest degree-two vertex fires
+                else { mark(u); mark(w); }
+            }
         }
-        if (u >= 0) {
-            if (Q.deg[u] == 1 && u < v) root_push_frontier(Q, sh, next, u);  // u's rule fires
-            else root_mark(Q, sh, u);
+    }
+
+    // Examine v against the rules; long rows of degree-1/2 vertices go to the
+    // heavy list for a warp to scan.
+    __device__ void examine(int *next, int *heavy, int v, int bud)
+    {
+        if (S.s(v) != 0) return;
+        const int d = S.d(v);
+        if (d == 0) return;
+        if (d > bud) mark(v);
+        if (d > 2) return;
+        const int a = __ldg(rp + v), b = __ldg(rp + v + 1);
+        if (b - a > kHeavyRow) {
+            agg_append(&sh.hcnt, heavy, v, true);
+            return;
         }
-    } else if (d == 2) {
         int u = -1, w = -1;
         for (int e = a; e < b; e++) {
-            int x = col[e];
-            if (Q.st[x] == 0 && Q.deg[x] > 0) {
-                if (u < 0) u = x; else { w = x; break; }
+            const int x = __ldg(col + e);
+            if (live(x)) {
+                if (u < 0) { u = x; if (d == 1) break; }
+                else { w = x; break; }
             }
         }
-        if (w >= 0 && bsearch_row(col + Q.rp[u], Q.rp[u + 1] - Q.rp[u], w)) {
-            int p = INT_MAX;
-            if (Q.deg[u] == 2 && u < v) p = u;
-            if (Q.deg[w] == 2 && w < v && w < p) p = w;
-            if (p != INT_MAX) root_push_frontier(Q, sh, next, p);
-            else { root_mark(Q, sh, u); root_mark(Q, sh, w); }
+        decide(next, v, d, u, w);
+    }
+
+    // Warp-cooperative: the first `need` live neighbours of v.
+    __device__ void warp_live_nbrs(int v, int need, int &u, int &w) const
+    {
+        const int lane = threadIdx.x & 31;
+        const int a = __ldg(rp + v), b = __ldg(rp + v + 1);
+        u = -1;
+        w = -1;
+        int found = 0;
+        for (int base = a; base < b && found < need; base += 32) {
+            const int e = base + lane;
+            const int x = e < b ? __ldg(col + e) : -1;
+            unsigned m = __ballot_sync(kFull, x >= 0 && live(x));
+            while (m && found < need) {
+                const int pos = __ffs(m) - 1;
+                const int val = __shfl_sync(kFull, x, pos);
+                if (found == 0) u = val; else w = val;
+                found++;
+                m &= m - 1;
+            }
         }
     }
-    if (d > bud) root_mark(Q, sh, v);
-}
 
-// Rounds of the rules until nothing is marked.  hd: use the high-degree rule
-// with budget bound - forced - 1.  Returns false when the budget went negative
-// (no cover smaller than `bound` can exist).
-__device__ bool root_reduce_rounds(QueryDesc &Q, RootShared &sh, bool hd, int bound)
-{
-    const int n = Q.n;
-    int *cur = Q.fr0, *next = Q.fr1;
-    int fsize = -1;   // -1: full scan
-    for (;;) {
-        const int bud = hd ? bound - sh.forced - 1 : INT_MAX;
-        if (hd && bud < 0) return false;
-        bool full = fsize < 0 || (hd && sh.delta > bud);
+    // Put u in the cover: lower the degrees of its live, unmarked neighbours.
+    __device__ void apply_row(int *next, int u, int lane, int stride)
+    {
+        const int a = __ldg(rp + u), b = __ldg(rp + u + 1);
+        for (int e = a + lane; e < b; e += stride) {
+            const int x = __ldg(col + e);
+            if (S.s(x) == 0 && S.d(x) > 0 && !S.marked(x)) {
+                S.dec(x);
+                push_frontier(next, x);
+            }
+        }
+    }
+
+    // Synchronous rounds of the rules until nothing is marked.  hd: use the
+    // high-degree rule with budget bound - forced - 1.  Returns false when the
+    // budget went negative (no cover smaller than `bound` can exist).
+    __device__ bool reduce_rounds(bool hd, int bound)
+    {
+        int *cur = Q.fr0, *next = Q.fr1, *heavy = Q.heavy;
+        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+        int fsize = -1;   // -1: full scan
+        for (;;) {
+            const int bud = hd ? bound - sh.forced - 1 : INT_MAX;
+            if (hd && bud < 0) return false;
+            const bool full = fsize < 0 || (hd && sh.delta > bud);
+            __syncthreads();
+            if (threadIdx.x == 0) { sh.cnt = 0; sh.fcnt = 0; sh.hcnt = 0; }
+            __syncthreads();
+            int dmax = 0;
+            if (full) {
+                for (int v = threadIdx.x; v < n; v += blockDim.x) {
+                    S.reset_flag(v);
+                    if (S.s(v) == 0) dmax = max(dmax, S.d(v));
+                }
+                __syncthreads();
+                for (int v = threadIdx.x; v < n; v += blockDim.x) examine(next, heavy, v, bud);
+            } else {
+                for (int i = threadIdx.x; i < fsize; i += blockDim.x) S.reset_flag(cur[i]);
+                __syncthreads();
+                for (int i = threadIdx.x; i < fsize; i += blockDim.x) examine(next, heavy, cur[i], bud);
+            }
+            __syncthreads();
+            // heavy rows: one warp per vertex
+            const int hcnt = sh.hcnt;
+            for (int i = warp; i < hcnt; i += nwarps) {
+                const int v = heavy[i];
+                const int d = S.d(v);
+                int u, w;
+                warp_live_nbrs(v, d, u, w);
+                if (lane == 0) decide(next, v, d, u, w);
+            }
+            if (full) {
+                const int dm = block_max(dmax, sh.red);
+                if (threadIdx.x == 0) sh.delta = dm;
+            }
+            __syncthreads();
+            const int cnt = sh.cnt;
+            const int base = sh.forced;
+            if (threadIdx.x == 0) Q.rounds++;
+            if (cnt == 0 && sh.fcnt == 0) return true;
+            __syncthreads();
+            if (threadIdx.x == 0) sh.hcnt = 0;
+            __syncthreads();
+            // apply: lower the degrees of the marked vertices' live neighbours
+            for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
+                const int u = Q.forced_list[base + i];
+                const bool hv = __ldg(rp + u + 1) - __ldg(rp + u) > kHeavyRow;
+                agg_append(&sh.hcnt, heavy, u, hv);
+                if (!hv) apply_row(next, u, 0, 1);
+            }
+            __syncthreads();
+            const int hc2 = sh.hcnt;
+            for (int i = warp; i < hc2; i += nwarps) apply_row(next, heavy[i], lane, 32);
+            __syncthreads();
+            for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
+                const int u = Q.forced_list[base + i];
+                S.set_s(u, 1);
+                S.set_d(u, 0);
+            }
+            __syncthreads();
+            if (threadIdx.x == 0) sh.forced = base + cnt;
+            fsize = sh.fcnt;
+            int *t = cur; cur = next; next = t;
+            __syncthreads();
+            if (fsize == 0 && !(hd && sh.delta > bound - sh.forced - 1)) return true;
+        }
+    }
+
+    __device__ int live_edges2()
+    {
+        int e2 = 0;
+        for (int v = threadIdx.x; v < n; v += blockDim.x)
+            if (S.s(v) == 0) e2 += S.d(v);
+        return block_sum(e2, sh.red);
+    }
+
+    // Greedy cover of the live graph: the complement of a maximal independent
+    // set chosen by static priority (degree, hash(id)), lowest first.  aux[v]:
+    // 0 undecided, 1 in the set, 2 in the cover, 3 not live, 4 joining.
+    // Flags the whole cover (forced + greedy) in cover_flags; returns the
+    // number of live vertices it puts in the cover.
+    __device__ int greedy()
+    {
+        int *aux = Q.aux, *join = Q.fr0;
+        for (int v = threadIdx.x; v < n; v += blockDim.x) aux[v] = live(v) ? 0 : 3;
         __syncthreads();
-        if (threadIdx.x == 0) { sh.cnt = 0; sh.fcnt = 0; }
-        __syncthreads();
-        int dmax = 0;
-        if (full) {
+        for (;;) {
+            __syncthreads();
+            if (threadIdx.x == 0) sh.flag = 0;
+            __syncthreads();
             for (int v = threadIdx.x; v < n; v += blockDim.x) {
-                Q.flag[v] = 0;
-                if (Q.st[v] == 0) dmax = max(dmax, Q.deg[v]);
+                if (aux[v] != 0) continue;
+                const unsigned long long pv = ((unsigned long long)S.d(v) << 32) | mix32((unsigned)v);
+                bool j = true;
+                for (int e = __ldg(rp + v); e < __ldg(rp + v + 1) && j; e++) {
+                    const int x = __ldg(col + e);
+                    const int ax = aux[x];
+                    if (ax == 1) j = false;
+                    else if (ax == 0) {
+                        const unsigned long long px = ((unsigned long long)S.d(x) << 32) | mix32((unsigned)x);
+                        if (px < pv || (px == pv && x < v)) j = false;
+                    }
+                }
+                join[v] = j;
             }
             __syncthreads();
-            for (int v = threadIdx.x; v < n; v += blockDim.x) root_examine(Q, sh, next, v, bud);
-        } else {
-            for (int i = threadIdx.x; i < fsize; i += blockDim.x) Q.flag[cur[i]] = 0;
+            for (int v = threadIdx.x; v < n; v += blockDim.x)
+                if (aux[v] == 0 && join[v]) { aux[v] = 4; sh.flag = 1; }
             __syncthreads();
-            for (int i = threadIdx.x; i < fsize; i += blockDim.x) root_examine(Q, sh, next, cur[i], bud);
-        }
-        if (full) {
-            int dm = block_max(dmax, sh.red);
-            if (threadIdx.x == 0) sh.delta = dm;
-        }
-        __syncthreads();
-        const int cnt = sh.cnt;
-        const int base = sh.forced;
-        if (cnt == 0) {
-            if (sh.fcnt == 0) return true;
-            // only tie-break partners were queued: examine them next round
-        }
-        // apply: lower the degrees of the marked vertices' live neighbours
-        for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
-            int u = Q.forced_list[base + i];
-            for (int e = Q.rp[u]; e < Q.rp[u + 1]; e++) {
-                int x = Q.col[e];
-                if (Q.st[x] == 0 && Q.aux[x] == 0 && Q.deg[x] > 0) {
-                    atomicSub(&Q.deg[x], 1);
-                    root_push_frontier(Q, sh, next, x);
+            if (!sh.flag) break;
+            for (int v = threadIdx.x; v < n; v += blockDim.x) {
+                if (aux[v] != 4) continue;
+                for (int e = __ldg(rp + v); e < __ldg(rp + v + 1); e++) {
+                    const int x = __ldg(col + e);
+                    if (aux[x] == 0) aux[x] = 2;
                 }
             }
+            __syncthreads();
+            for (int v = threadIdx.x; v < n; v += blockDim.x)
+                if (aux[v] == 4) aux[v] = 1;
         }
         __syncthreads();
-        for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
-            int u = Q.forced_list[base + i];
-            Q.st[u] = 1;
-            Q.deg[u] = 0;
-            Q.aux[u] = 0;
+        int c = 0;
+        for (int v = threadIdx.x; v < n; v += blockDim.x) {
+            const bool g = aux[v] == 2 || aux[v] == 0;
+            Q.cover_flags[v] = (S.s(v) == 1 || g) ? 1 : 0;
+            c += g;
         }
+        const int tot = block_sum(c, sh.red);
+        for (int v = threadIdx.x; v < n; v += blockDim.x) aux[v] = 0;
         __syncthreads();
-        if (threadIdx.x == 0) sh.forced = base + cnt;
-        fsize = sh.fcnt;
-        int *t = cur; cur = next; next = t;
-        __syncthreads();
-        if (fsize == 0 && !(hd && sh.delta > bound - sh.forced - 1)) return true;
+        return tot;
     }
-}
 
-// Greedy cover of the live graph: the complement of a maximal independent
-// set chosen by static priority (degree, hash(id)), lowest first.  aux[v]:
-// 0 undecided, 1 in the independent set, 2 in the cover.  Returns the number
-// of live vertices put in the cover; flags them in cover_flags.
-__device__ int root_greedy(QueryDesc &Q, RootShared &sh)
-{
-    const int n = Q.n;
-    for (int v = threadIdx.x; v < n; v += blockDim.x)
-        Q.aux[v] = (Q.st[v] == 0 && Q.deg[v] > 0) ? 0 : 3;   // 3: not part of the live graph
-    __syncthreads();
-    for (int round = 0;; round++) {
-        __syncthreads();
-        if (threadIdx.x == 0) sh.flag = 0;
-        __syncthreads();
-        // a vertex joins when every undecided neighbour has a larger priority
-        for (int v = threadIdx.x; v < n; v += blockDim.x) {
-            if (Q.aux[v] != 0) continue;
-            const unsigned long long pv =
-                ((unsigned long long)Q.deg[v] << 32) | mix32((unsigned)v);
-            bool join = true;
-            for (int e = Q.rp[v]; e < Q.rp[v + 1] && join; e++) {
-                int x = Q.col[e];
-                int ax = Q.aux[x];
-                if (ax == 1 || ax == 4) join = false;
-                else if (ax == 0) {
-                    unsigned long long px = ((unsigned long long)Q.deg[x] << 32) | mix32((unsigned)x);
-                    if (px < pv || (px == pv && x < v)) join = false;
-                }
-            }
-            if (join) Q.fr0[v] = 1; else Q.fr0[v] = 0;
-        }
-        __syncthreads();
-        for (int v = threadIdx.x; v < n; v += blockDim.x)
-            if (Q.aux[v] == 0 && Q.fr0[v]) { Q.aux[v] = 4; sh.flag = 1; }   // 4: joined this round
-        __syncthreads();
-        if (!sh.flag) break;
-        for (int v = threadIdx.x; v < n; v += blockDim.x) {
-            if (Q.aux[v] != 4) continue;
-            for (int e = Q.rp[v]; e < Q.rp[v + 1]; e++) {
-                int x = Q.col[e];
-                if (Q.aux[x] == 0) Q.aux[x] = 2;
+    // Induce the subgraph on the live vertices with non-zero degree,
+    // relabelled in increasing original id (rows stay sorted).
+    __device__ void induce()
+    {
+        const int T = blockDim.x;
+        const int chunk = (n + T - 1) / T;
+        const int beg = min(n, (int)threadIdx.x * chunk), end = min(n, beg + chunk);
+        int cnt = 0, dsum = 0, dmax = 0;
+        for (int v = beg; v < end; v++)
+            if (live(v)) { cnt++; dsum += S.d(v); dmax = max(dmax, S.d(v)); }
+        int np, m2p;
+        const int off = block_excl_scan(cnt, sh.red, &np);
+        const int eoff = block_excl_scan(dsum, sh.red, &m2p);
+        const int dm = block_max(dmax, sh.red);
+        int *nid = Q.aux;
+        int id = off, eo = eoff;
+        for (int v = beg; v < end; v++) {
+            if (live(v)) {
+                nid[v] = id;
+                Q.orig[id] = v;
+                Q.rp2[id] = eo;
+                id++;
+                eo += S.d(v);
+            } else {
+                nid[v] = -1;
             }
         }
         __syncthreads();
-        for (int v = threadIdx.x; v < n; v += blockDim.x)
-            if (Q.aux[v] == 4) Q.aux[v] = 1;
-    }
-    __syncthreads();
-    int c = 0;
-    for (int v = threadIdx.x; v < n; v += blockDim.x) {
-        bool in = Q.st[v] == 1 || Q.aux[v] == 2 || Q.aux[v] == 0;
-        Q.cover_flags[v] = in ? 1 : 0;
-        if (Q.aux[v] == 2 || Q.aux[v] == 0) c++;
-    }
-    int tot = block_sum(c, sh.red);
-    for (int v = threadIdx.x; v < n; v += blockDim.x) Q.aux[v] = 0;
-    __syncthreads();
-    return tot;
-}
-
-// Induce the subgraph on the live vertices with non-zero degree, relabelled
-// in increasing original id (so rows stay sorted).
-__device__ void root_induce(QueryDesc &Q, RootShared &sh)
-{
-    const int n = Q.n;
-    const int T = blockDim.x;
-    const int chunk = (n + T - 1) / T;
-    const int beg = min(n, threadIdx.x * chunk), end = min(n, beg + chunk);
-    int cnt = 0, dsum = 0, dmax = 0;
-    for (int v = beg; v < end; v++) {
-        if (Q.st[v] == 0 && Q.deg[v] > 0) { cnt++; dsum += Q.deg[v]; dmax = max(dmax, Q.deg[v]); }
-    }
-    int np, m2p;
-    int off = block_excl_scan(cnt, sh.red, &np);
-    int eoff = block_excl_scan(dsum, sh.red, &m2p);
-    int dm = block_max(dmax, sh.red);
-    int id = off, eo = eoff;
-    for (int v = beg; v < end; v++) {
-        if (Q.st[v] == 0 && Q.deg[v] > 0) {
-            Q.aux[v] = id;       // new id
-            Q.orig[id] = v;
-            Q.rp2[id] = eo;
-            id++;
-            eo += Q.deg[v];
-        } else {
-            Q.aux[v] = -1;
+        if (threadIdx.x == 0) {
+            Q.rp2[np] = m2p;
+            Q.np = np;
+            Q.m2p = m2p;
+            Q.maxdeg = dm;
         }
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        Q.rp2[np] = m2p;
-        Q.np = np;
-        Q.m2p = m2p;
-        Q.maxdeg = dm;
-    }
-    for (int i = threadIdx.x; i < np; i += T) {
-        int v = Q.orig[i];
-        int o = Q.rp2[i];
-        for (int e = Q.rp[v]; e < Q.rp[v + 1]; e++) {
-            int x = Q.col[e];
-            int nx = Q.aux[x];
-            if (nx >= 0) Q.col2[o++] = nx;
+        for (int i = threadIdx.x; i < np; i += T) {
+            const int v = Q.orig[i];
+            int o = Q.rp2[i];
+            for (int e = __ldg(rp + v); e < __ldg(rp + v + 1); e++) {
+                const int nx = nid[__ldg(col + e)];
+                if (nx >= 0) Q.col2[o++] = nx;
+            }
         }
+        __syncthreads();
+        for (int v = threadIdx.x; v < n; v += T) nid[v] = 0;
+        __syncthreads();
     }
-    __syncthreads();
-    for (int v = threadIdx.x; v < n; v += T) Q.aux[v] = 0;
-    __syncthreads();
-}
 
-__global__ void __launch_bounds__(kRootThreads) root_kernel(QueryDesc *qs)
+    __device__ void run()
+    {
+        for (int v = threadIdx.x; v < n; v += blockDim.x) {
+            S.set_d(v, __ldg(rp + v + 1) - __ldg(rp + v));
+            S.set_s(v, 0);
+            Q.aux[v] = 0;
+            Q.flag[v] = 0;
+            Q.cover_flags[v] = 0;
+        }
+        if (threadIdx.x == 0) {
+            sh.forced = 0;
+            sh.delta = INT_MAX;
+            Q.np = 0; Q.m2p = 0; Q.maxdeg = 0; Q.answered = 0; Q.greedy = -1;
+            Q.improved = 0; Q.result = -1; Q.yes = 0; Q.cover_len = 0;
+            Q.rounds = 0;
+            for (int i = 0; i < 4; i++) Q.root_cycles[i] = 0;
+        }
+        __syncthreads();
+
+        // phase 1: degree-one and degree-two-triangle rules (need no bound)
+        long long t0 = clock64();
+        reduce_rounds(false, INT_MAX);
+        long long t1 = clock64();
+        if (threadIdx.x == 0) Q.root_cycles[0] = t1 - t0;
+        if (live_edges2() == 0) {
+            // the rules alone produced a cover; they are exact, so it is minimum
+            S.publish(Q, n);
+            for (int v = threadIdx.x; v < n; v += blockDim.x) Q.cover_flags[v] = S.s(v) == 1;
+            if (threadIdx.x == 0) {
+                Q.forced = sh.forced;
+                Q.answered = 1;
+                Q.bound = sh.forced;
+                if (Q.k < 0) { Q.result = sh.forced; Q.yes = 1; }
+                else { Q.yes = sh.forced <= Q.k; Q.result = Q.yes ? sh.forced : -1; }
+            }
+            return;
+        }
+
+        // initial upper bound (Algorithm 1: "an approximate minimum ... such
+        // as a greedy one")
+        const int greedy_size = sh.forced + greedy();
+        t0 = clock64();
+        if (threadIdx.x == 0) { Q.greedy = greedy_size; Q.root_cycles[1] = t0 - t1; }
+        if (Q.k >= 0 && greedy_size <= Q.k) {
+            S.publish(Q, n);
+            if (threadIdx.x == 0) {
+                Q.forced = sh.forced; Q.answered = 1; Q.bound = greedy_size; Q.yes = 1; Q.result = greedy_size;
+            }
+            return;
+        }
+        // look only for covers smaller than `bound`
+        const int bound = Q.k >= 0 ? Q.k + 1 : greedy_size;
+
+        // phase 2: all three rules; high-degree budget b = bound - |F| - 1
+        const bool feasible = reduce_rounds(true, bound);
+        t1 = clock64();
+        if (threadIdx.x == 0) Q.root_cycles[2] = t1 - t0;
+        const int e2 = live_edges2();
+        S.publish(Q, n);
+        if (!feasible || sh.forced >= bound) {
+            // no cover smaller than the bound exists
+            if (threadIdx.x == 0) {
+                Q.forced = sh.forced; Q.answered = 1; Q.bound = bound;
+                if (Q.k < 0) { Q.result = greedy_size; Q.yes = 1; }   // the greedy flags hold it
+                else { Q.yes = 0; Q.result = -1; }
+            }
+            return;
+        }
+        if (e2 == 0) {
+            __syncthreads();
+            for (int v = threadIdx.x; v < n; v += blockDim.x) Q.cover_flags[v] = S.s(v) == 1;
+            if (threadIdx.x == 0) {
+                Q.forced = sh.forced; Q.answered = 1; Q.bound = bound;
+                Q.result = sh.forced; Q.yes = 1;
+            }
+            return;
+        }
+        induce();
+        if (threadIdx.x == 0) { Q.forced = sh.forced; Q.bound = bound; Q.root_cycles[3] = clock64() - t1; }
+    }
+};
+
+template <class Store>
+__global__ void __launch_bounds__(kRootThreads, 1) root_kernel(QueryDesc *qs)
 {
+    extern __shared__ __align__(16) char root_smem[];
     __shared__ RootShared sh;
     QueryDesc &Q = qs[blockIdx.x];
     if (Q.status != VC_OK) return;
-    const int n = Q.n;
-    for (int v = threadIdx.x; v < n; v += blockDim.x) {
-        Q.deg[v] = Q.rp[v + 1] - Q.rp[v];
-        Q.st[v] = 0;
-        Q.aux[v] = 0;
-        Q.flag[v] = 0;
-        Q.cover_flags[v] = 0;
-    }
-    if (threadIdx.x == 0) {
-        sh.forced = 0;
-        sh.delta = INT_MAX;
-        Q.np = 0; Q.m2p = 0; Q.maxdeg = 0; Q.answered = 0; Q.greedy = -1;
-        Q.improved = 0; Q.result = -1; Q.yes = 0; Q.cover_len = 0;
-    }
+    Root<Store> r(Q, sh, root_smem);
     __syncthreads();
-
-    // phase 1: degree-one and degree-two-triangle rules (need no bound)
-    root_reduce_rounds(Q, sh, false, INT_MAX);
-    int e2 = 0;
-    for (int v = threadIdx.x; v < n; v += blockDim.x)
-        if (Q.st[v] == 0) e2 += Q.deg[v];
-    e2 = block_sum(e2, sh.red);
-    if (e2 == 0) {
-        // the rules alone produced a cover; they are exact, so it is minimum
-        for (int v = threadIdx.x; v < n; v += blockDim.x) Q.cover_flags[v] = Q.st[v] == 1;
-        if (threadIdx.x == 0) {
-            Q.forced = sh.forced;
-            Q.answered = 1;
-            Q.bound = sh.forced;
-            if (Q.k < 0) { Q.result = sh.forced; Q.yes = 1; }
-            else { Q.yes = sh.forced <= Q.k; Q.result = Q.yes ? sh.forced : -1; }
-        }
-        return;
-    }
-
-    // initial upper bound (Algorithm 1: "an approximate minimum ... such as a greedy one")
-    int g = root_greedy(Q, sh);
-    const int greedy = sh.forced + g;
-    if (threadIdx.x == 0) Q.greedy = greedy;
-    if (Q.k >= 0 && greedy <= Q.k) {
-        if (threadIdx.x == 0) {
-            Q.forced = sh.forced; Q.answered = 1; Q.bound = greedy; Q.yes = 1; Q.result = greedy;
-        }
-        return;
-    }
-    // look only for covers smaller than `bound`
-    const int bound = Q.k >= 0 ? Q.k + 1 : greedy;
-
-    // phase 2: all three rules; high-degree budget b = bound - |F| - 1
-    bool feasible = root_reduce_rounds(Q, sh, true, bound);
-    e2 = 0;
-    for (int v = threadIdx.x; v < n; v += blockDim.x)
-        if (Q.st[v] == 0) e2 += Q.deg[v];
-    e2 = block_sum(e2, sh.red);
-    if (!feasible || sh.forced >= bound) {
-        // no cover smaller than the bound exists
-        if (threadIdx.x == 0) {
-            Q.forced = sh.forced; Q.answered = 1; Q.bound = bound;
-            if (Q.k < 0) { Q.result = greedy; Q.yes = 1; }   // greedy flags already hold it
-            else { Q.yes = 0; Q.result = -1; }
-        }
-        return;
-    }
-    if (e2 == 0) {
-        for (int v = threadIdx.x; v < n; v += blockDim.x) Q.cover_flags[v] = Q.st[v] == 1;
-        if (threadIdx.x == 0) {
-            Q.forced = sh.forced; Q.answered = 1; Q.bound = bound;
-            Q.result = sh.forced; Q.yes = 1;
-        }
-        return;
-    }
-    root_induce(Q, sh);
-    if (threadIdx.x == 0) { Q.forced = sh.forced; Q.bound = bound; }
+    r.run();
 }
 
 // ------------------------------------------------------------ final answer
@@ -515,9 +698,11 @@ __global__ void __launch_bounds__(kRootThreads) finalize_kernel(QueryDesc *qs, c
 
 namespace vcg {
 
+constexpr size_t kRootSmemMax = 200 * 1024;
+
 cudaError_t validate_run(int n, int m2, const int *rp, const int *col, int *d_err, cudaStream_t s)
 {
-    cudaError_t e = cudaMemsetAsync(d_err, 0, 2 * sizeof(int), s);
+    cudaError_t e = cudaMemsetAsync(d_err, 0, 3 * sizeof(int), s);
     if (e != cudaSuccess) return e;
     const int threads = 256;
     const int blocks = (n + 1 + threads - 1) / threads < 4096 ? (n + 1 + threads - 1) / threads : 4096;
@@ -526,15 +711,27 @@ cudaError_t validate_run(int n, int m2, const int *rp, const int *col, int *d_er
     if (e != cudaSuccess) return e;
     if (n > 0) {
         validate_col_kernel<<<blocks > 0 ? blocks : 1, threads, 0, s>>>(n, rp, col, d_err);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        max_degree_kernel<<<blocks > 0 ? blocks : 1, threads, 0, s>>>(n, rp, d_err);
         e = cudaGetLastError();
     }
     return e;
 }
 
-cudaError_t root_run(QueryDesc *d_q, int nq, cudaStream_t s)
+size_t root_smem_bytes(int max_n) { return SmemStore::smem_bytes(max_n); }
+
+cudaError_t root_run(QueryDesc *d_q, int nq, int max_n, int max_deg, cudaStream_t s)
 {
     if (nq <= 0) return cudaSuccess;
-    root_kernel<<<nq, kRootThreads, 0, s>>>(d_q);
+    const size_t smem = SmemStore::smem_bytes(max_n);
+    if (max_deg <= 65535 && smem <= kRootSmemMax) {
+        cudaError_t e = cudaFuncSetAttribute(root_kernel<SmemStore>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return e;
+        root_kernel<SmemStore><<<nq, kRootThreads, smem, s>>>(d_q);
+    } else {
+        root_kernel<GlobalStore><<<nq, kRootThreads, 0, s>>>(d_q);
+    }
     return cudaGetLastError();
 }
 

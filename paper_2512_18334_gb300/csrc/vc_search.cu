@@ -59,31 +59,51 @@ __host__ __device__ inline int worker_smem_bytes(int ncap, int wcap)
 template <class X>
 __device__ __forceinline__ X vld(const X &x) { return *(volatile const X *)&x; }
 
-__device__ int reg_alloc(const SearchParams &P)
+// Registry entries come from a per-worker free list first, then from a
+// global stack of free chunks (kChunk entries linked through `next`, chunks
+// linked through pad[0]), then from a global bump counter.  Freed entries go
+// to the freeing worker's list; when it reaches 2 * kChunk, kChunk of them go
+// back to the global stack as one chunk (one CAS per chunk, not per entry).
+// Only team leaders call these.
+constexpr int kChunk = 32;
+
+__device__ __forceinline__ unsigned long long cas_release_u64(unsigned long long *p, unsigned long long cmp,
+                                                              unsigned long long val)
 {
-    unsigned long long *head = &P.ctl[kRegHead];
-    for (int it = 0; it < (1 << 20); it++) {
-        unsigned long long h = atomicAdd(head, 0ull);
-        int idx = (int)(h & 0xffffffffull);
-        if (idx < 0) return -1;
-        int nx = *(volatile int *)&P.reg[idx].next;
-        unsigned long long nh = ((h >> 32) + 1) << 32 | (unsigned)nx;
-        if (atomicCAS(head, h, nh) == h) return idx;
-    }
-    return -1;
+    unsigned long long old;
+    asm volatile("atom.release.gpu.global.cas.b64 %0, [%1], %2, %3;"
+                 : "=l"(old) : "l"(p), "l"(cmp), "l"(val) : "memory");
+    return old;
 }
 
-__device__ void reg_free(const SearchParams &P, int idx)
+// Pop one chunk; returns its first entry or -1.
+__device__ int reg_chunk_pop(const SearchParams &P)
 {
-    unsigned long long *head = &P.ctl[kRegHead];
-    for (int it = 0; it < (1 << 20); it++) {
-        unsigned long long h = atomicAdd(head, 0ull);
-        *(volatile int *)&P.reg[idx].next = (int)(h & 0xffffffffull);
-        __threadfence();
-        unsigned long long nh = ((h >> 32) + 1) << 32 | (unsigned)idx;
-        if (atomicCAS(head, h, nh) == h) return;
+    unsigned long long *head = &ctlw(P.ctl, kRegHead);
+    for (int it = 0; it < 64; it++) {
+        const unsigned long long h = ld_acquire_u64(head);
+        const int idx = (int)(h & 0xffffffffull);
+        if (idx < 0) return -1;
+        const int nx = *(volatile int *)&P.reg[idx].pad[0];
+        const unsigned long long nh = ((h >> 32) + 1) << 32 | (unsigned)nx;
+        if (atomicCAS(head, h, nh) == h) return idx;
+        __nanosleep(16 + (it << 4));
     }
-    set_error(P.ctl, VC_ETIMEOUT);
+    return -1;   // contended: the caller falls back to the bump counter
+}
+
+// Push a chunk whose first entry is idx (its entries already linked).
+__device__ void reg_chunk_push(const SearchParams &P, int idx)
+{
+    unsigned long long *head = &ctlw(P.ctl, kRegHead);
+    for (int it = 0; it < (1 << 22); it++) {
+        const unsigned long long h = ld_acquire_u64(head);
+        *(volatile int *)&P.reg[idx].pad[0] = (int)(h & 0xffffffffull);
+        const unsigned long long nh = ((h >> 32) + 1) << 32 | (unsigned)idx;
+        if (cas_release_u64(head, h, nh) == h) return;
+        __nanosleep(16 + ((it & 63) << 4));
+    }
+    set_error(P.ctl, VC_ETIMEOUT, 1);
 }
 
 __device__ bool reg_lock(const SearchParams &P, int e)
@@ -97,7 +117,7 @@ __device__ bool reg_lock(const SearchParams &P, int e)
         if (aborted(P.ctl)) return false;
         __nanosleep(64);
     }
-    set_error(P.ctl, VC_ETIMEOUT);
+    set_error(P.ctl, VC_ETIMEOUT, 2);
     return false;
 }
 
@@ -116,7 +136,7 @@ __device__ inline uint32_t *reg_words(const SearchParams &P, int e)
 // cover <= k).  Counted once.
 __device__ void query_done(const SearchParams &P, int q)
 {
-    if (atomicExch(&P.queries[q].done, 1) == 0) atomicAdd(&P.ctl[kRemaining], (unsigned long long)-1ll);
+    if (atomicExch(&P.queries[q].done, 1) == 0) atomicAdd(&ctlw(P.ctl, kRemaining), (unsigned long long)-1ll);
 }
 
 __device__ inline bool query_is_done(const SearchParams &P, int q)
@@ -148,6 +168,9 @@ struct Worker {
     // private stack
     char *stack;
     int top;
+
+    // private registry free list (leader only)
+    int lf_head, lf_count;
     long long nodes_local, last_flush;
     int max_top;
 
@@ -167,6 +190,8 @@ struct Worker {
         last_flush = 0;
         max_top = 0;
         cntbuf = 0;
+        lf_head = -1;
+        lf_count = 0;
         if (tm.leader()) { sc[0] = 0; sc[1] = 0; }
         tm.sync();
     }
@@ -427,16 +452,18 @@ struct Worker {
         int ok = 0;
         long long t = -1;
         if (tm.leader()) {
-            long long old = (long long)atomicAdd(&P.ctl[kWlCount], 1ull);
-            if (old >= P.wl_cap) {
-                atomicAdd(&P.ctl[kWlCount], (unsigned long long)-1ll);
-            } else {
-                ok = 1;
-                t = (long long)atomicAdd(&P.ctl[kWlTail], 1ull);
+            unsigned long long *cnt = &ctlw(P.ctl, kWlCount);
+            if ((long long)*(volatile unsigned long long *)cnt < P.wl_cap) {
+                const long long old = (long long)atomicAdd(cnt, 1ull);
+                if (old < P.wl_cap) ok = 1;
+                else atomicAdd(cnt, (unsigned long long)-1ll);
+            }
+            if (ok) {
+                t = (long long)atomicAdd(&ctlw(P.ctl, kWlTail), 1ull);
                 const unsigned slot = (unsigned)t & (P.wl_cap - 1);
                 int it = 0;
                 while (ld_acquire_u32(&P.wl_seq[slot]) != (unsigned)t) {
-                    if (++it > (1 << 24) || aborted(P.ctl)) { set_error(P.ctl, VC_ETIMEOUT); ok = 0; break; }
+                    if (++it > (1 << 24) || aborted(P.ctl)) { set_error(P.ctl, VC_ETIMEOUT, 3); ok = 0; break; }
                     __nanosleep(32);
                 }
             }
@@ -458,7 +485,7 @@ struct Worker {
         if (tm.leader()) {
             const unsigned slot = (unsigned)t & (P.wl_cap - 1);
             st_release_u32(&P.wl_seq[slot], (unsigned)t + 1u);
-            atomicAdd(&P.ctl[kOffloaded], 1ull);
+            atomicAdd(&ctlw(P.ctl, kOffloaded), 1ull);
         }
     }
 
@@ -467,21 +494,25 @@ struct Worker {
         return P.wl_slots + (size_t)((unsigned)t & (P.wl_cap - 1)) * P.slot_bytes;
     }
 
-    // Try to take a node from the worklist into shared memory.
+    // Try to take a node from the worklist into shared memory.  The item
+    // counter is only decremented while it is positive (read, then CAS), so
+    // idle workers polling an empty worklist never write to it.
     __device__ bool wl_pop()
     {
         int ok = 0;
         if (tm.leader()) {
-            long long old = (long long)atomicAdd(&P.ctl[kWlCount], (unsigned long long)-1ll);
-            if (old <= 0) {
-                atomicAdd(&P.ctl[kWlCount], 1ull);
-            } else {
-                const long long t = (long long)atomicAdd(&P.ctl[kWlHead], 1ull);
+            unsigned long long *cnt = &ctlw(P.ctl, kWlCount);
+            for (int it = 0; it < 32; it++) {
+                const unsigned long long c = *(volatile unsigned long long *)cnt;
+                if ((long long)c <= 0) break;
+                if (atomicCAS(cnt, c, c - 1) == c) { ok = 1; break; }
+            }
+            if (ok) {
+                const long long t = (long long)atomicAdd(&ctlw(P.ctl, kWlHead), 1ull);
                 const unsigned slot = (unsigned)t & (P.wl_cap - 1);
                 int it = 0;
-                ok = 1;
                 while (ld_acquire_u32(&P.wl_seq[slot]) != (unsigned)t + 1u) {
-                    if (++it > (1 << 24) || aborted(P.ctl)) { set_error(P.ctl, VC_ETIMEOUT); ok = 0; break; }
+                    if (++it > (1 << 24) || aborted(P.ctl)) { set_error(P.ctl, VC_ETIMEOUT, 4); ok = 0; break; }
                     __nanosleep(32);
                 }
                 sc[5] = (int)(t & 0x7fffffff);
@@ -510,7 +541,7 @@ struct Worker {
     {
         int to_wl = 0;
         if (P.load_balance && tm.leader()) {
-            const long long cnt = (long long)*(volatile unsigned long long *)&P.ctl[kWlCount];
+            const long long cnt = (long long)*(volatile unsigned long long *)&ctlw(P.ctl, kWlCount);
             to_wl = cnt < P.wl_low;
         }
         to_wl = tm.bcast(to_wl);   // uniform decision: the team must take one path
@@ -530,7 +561,7 @@ struct Worker {
                 tm.sync();
                 return true;
             }
-            if (tm.leader()) set_error(P.ctl, VC_ECAPACITY);
+            if (tm.leader()) set_error(P.ctl, VC_ECAPACITY, 5);
             tm.sync();
             return false;
         }
@@ -541,6 +572,39 @@ struct Worker {
     }
 
     // ------------------------------------------------------------ registry ops
+
+    __device__ int reg_alloc()
+    {
+        if (lf_head < 0) {
+            const int c = reg_chunk_pop(P);
+            if (c >= 0) { lf_head = c; lf_count = kChunk; }
+        }
+        if (lf_head >= 0) {
+            const int e = lf_head;
+            lf_head = *(volatile int *)&P.reg[e].next;
+            lf_count--;
+            return e;
+        }
+        const int e = (int)atomicAdd(&ctlw(P.ctl, kRegBump), 1ull);
+        return e < P.reg_cap ? e : -1;
+    }
+
+    __device__ void reg_free(int e)
+    {
+        *(volatile int *)&P.reg[e].next = lf_head;
+        lf_head = e;
+        lf_count++;
+        if (lf_count >= 2 * kChunk) {
+            // detach the first kChunk entries as one chunk
+            int last = lf_head;
+            for (int i = 1; i < kChunk; i++) last = *(volatile int *)&P.reg[last].next;
+            const int chunk = lf_head;
+            lf_head = *(volatile int *)&P.reg[last].next;
+            *(volatile int *)&P.reg[last].next = -1;
+            lf_count -= kChunk;
+            reg_chunk_push(P, chunk);
+        }
+    }
 
     // A leaf with cover size S in context `comp`: Best = min(Best, S) and the
     // witness bitmap follows (under the entry's lock).
@@ -581,7 +645,7 @@ struct Worker {
     {
         for (int guard = 0;; guard++) {
             if (guard > (1 << 22)) {      // the registry chain is acyclic; never expected
-                if (tm.leader()) set_error(P.ctl, VC_ETIMEOUT);
+                if (tm.leader()) set_error(P.ctl, VC_ETIMEOUT, 6);
                 tm.sync();
                 return;
             }
@@ -611,7 +675,7 @@ struct Worker {
             int r2 = 0;
             if (tm.leader()) {
                 atomicAdd(&P.reg[par].val, bestc);
-                reg_free(P, c);
+                reg_free(c);
                 r2 = atom_add_acq_rel(&P.reg[par].live, -1) - 1;
             }
             r2 = tm.bcast(r2);
@@ -645,7 +709,7 @@ struct Worker {
                 }
             }
             tm.sync();
-            if (tm.leader()) reg_free(P, par);
+            if (tm.leader()) reg_free(par);
             tm.sync();
             c = anc;
         }
@@ -800,7 +864,7 @@ struct Worker {
         lb_sum = tm.sum(lb_sum);
         nontriv = tm.sum(nontriv);
         if (S + s_triv + lb_sum >= B) {       // even the lower bounds reach Best
-            if (tm.leader()) atomicAdd(&P.ctl[kPruned], 1ull);
+            if (tm.leader()) atomicAdd(&ctlw(P.ctl, kPruned), 1ull);
             return kComplete;
         }
         if (s_triv > 0) {
@@ -833,11 +897,11 @@ struct Worker {
             }
             ntriv = tm.sum(ntriv);
             S += s_triv;
-            if (tm.leader()) atomicAdd(&P.ctl[kTrivial], (unsigned long long)ntriv);
+            if (tm.leader()) atomicAdd(&ctlw(P.ctl, kTrivial), (unsigned long long)ntriv);
             tm.sync();
         }
         if (nontriv == 0) {                    // all edges covered: a leaf
-            if (tm.leader()) atomicAdd(&P.ctl[kLeaves], 1ull);
+            if (tm.leader()) atomicAdd(&ctlw(P.ctl, kLeaves), 1ull);
             improve();
             return kComplete;
         }
@@ -851,8 +915,8 @@ struct Worker {
         // included), LiveComps = number of components, witness = S
         int pidx = -1;
         if (tm.leader()) {
-            pidx = reg_alloc(P);
-            if (pidx < 0) set_error(P.ctl, VC_ECAPACITY);
+            pidx = reg_alloc();
+            if (pidx < 0) set_error(P.ctl, VC_ECAPACITY, 7);
         }
         pidx = tm.bcast(pidx);
         if (pidx < 0) return kError;
@@ -895,8 +959,8 @@ struct Worker {
                 const int clo_c = lo + r, chi_c = lo + __ldcg(chiv + r);
                 int cidx = -1;
                 if (tm.leader()) {
-                    cidx = reg_alloc(P);
-                    if (cidx < 0) set_error(P.ctl, VC_ECAPACITY);
+                    cidx = reg_alloc();
+                    if (cidx < 0) set_error(P.ctl, VC_ECAPACITY, 8);
                 }
                 cidx = tm.bcast(cidx);
                 if (cidx < 0) return kError;
@@ -932,9 +996,9 @@ struct Worker {
             }
         }
         if (tm.leader()) {
-            atomicAdd(&P.ctl[kCompBranches], 1ull);
+            atomicAdd(&ctlw(P.ctl, kCompBranches), 1ull);
             int b = min(nontriv, kHistBins) - 2;
-            if (b >= 0) atomicAdd(&P.ctl[kHist + b], 1ull);
+            if (b >= 0) atomicAdd(&ctlw(P.ctl, kHist + b), 1ull);
         }
         tm.sync();
         return kHandedOff;
@@ -953,18 +1017,18 @@ struct Worker {
             if (B == INT_MIN) return;   // aborted (decided by the leader for the whole team)
             Stats st = reduce(B);
             if (st.pruned) {
-                if (tm.leader()) atomicAdd(&P.ctl[kPruned], 1ull);
+                if (tm.leader()) atomicAdd(&ctlw(P.ctl, kPruned), 1ull);
                 complete(comp);
                 return;
             }
             const long long bud = (long long)B - S - 1;
             if (S >= B || st.e2 / 2 > bud * bud) {      // stopping condition
-                if (tm.leader()) atomicAdd(&P.ctl[kPruned], 1ull);
+                if (tm.leader()) atomicAdd(&ctlw(P.ctl, kPruned), 1ull);
                 complete(comp);
                 return;
             }
             if (st.e2 == 0) {                            // a new best cover
-                if (tm.leader()) atomicAdd(&P.ctl[kLeaves], 1ull);
+                if (tm.leader()) atomicAdd(&ctlw(P.ctl, kLeaves), 1ull);
                 improve();
                 complete(comp);
                 return;
@@ -985,7 +1049,7 @@ struct Worker {
             }
             // ---- branch on v_max (Algorithm 1 lines 9-11)
             if (vmax < lo || vmax > hi) {                         // cannot happen with edges left
-                if (tm.leader()) set_error(P.ctl, VC_ECAPACITY);
+                if (tm.leader()) set_error(P.ctl, VC_ECAPACITY, 9);
                 tm.sync();
                 return;
             }
@@ -1004,9 +1068,9 @@ struct Worker {
     __device__ void flush_counters()
     {
         if (tm.leader()) {
-            atomicAdd(&P.ctl[kNodes], (unsigned long long)(nodes_local - last_flush));
-            atomicAdd(&P.ctl[kProgress], 1ull);
-            atomicMax(&P.ctl[kMaxStack], (unsigned long long)max_top);
+            atomicAdd(&ctlw(P.ctl, kNodes), (unsigned long long)(nodes_local - last_flush));
+            atomicAdd(&ctlw(P.ctl, kProgress), 1ull);
+            atomicMax(&ctlw(P.ctl, kMaxStack), (unsigned long long)max_top);
         }
         last_flush = nodes_local;
     }
@@ -1015,6 +1079,9 @@ struct Worker {
     {
         unsigned long long idle_since = 0, seen_progress = ~0ull;
         int backoff = 32;
+        // counters are flushed every 64 nodes, more often under a small node budget
+        long long flush_every = 64;
+        if (P.node_budget > 0) flush_every = max(1ll, min(64ll, P.node_budget / (16ll * P.workers)));
         for (;;) {
             int ab = tm.leader() ? (int)aborted(P.ctl) : 0;
             if (tm.bcast(ab)) break;
@@ -1032,11 +1099,11 @@ struct Worker {
                 int qd = tm.leader() ? (int)query_is_done(P, q) : 0;
                 if (tm.bcast(qd)) { tm.sync(); continue; }   // PVC answered meanwhile
                 process();
-                if (nodes_local - last_flush >= 64) {
+                if (nodes_local - last_flush >= flush_every) {
                     flush_counters();
                     if (P.node_budget > 0 &&
-                        (long long)*(volatile unsigned long long *)&P.ctl[kNodes] > P.node_budget) {
-                        if (tm.leader()) set_error(P.ctl, VC_EBUDGET);
+                        (long long)*(volatile unsigned long long *)&ctlw(P.ctl, kNodes) > P.node_budget) {
+                        if (tm.leader()) set_error(P.ctl, VC_EBUDGET, 10);
                     }
                 }
                 tm.sync();
@@ -1044,15 +1111,15 @@ struct Worker {
             }
             // idle
             int stop = 0;
-            if (tm.leader() && *(volatile unsigned long long *)&P.ctl[kRemaining] == 0ull) stop = 2;
+            if (tm.leader() && *(volatile unsigned long long *)&ctlw(P.ctl, kRemaining) == 0ull) stop = 2;
             if (tm.leader() && !stop) {
-                const unsigned long long prog = *(volatile unsigned long long *)&P.ctl[kProgress];
+                const unsigned long long prog = *(volatile unsigned long long *)&ctlw(P.ctl, kProgress);
                 const unsigned long long now = globaltimer();
                 if (prog != seen_progress || idle_since == 0) { seen_progress = prog; idle_since = now; }
-                else if ((long long)(now - idle_since) > P.idle_timeout_ns) { set_error(P.ctl, VC_ETIMEOUT); stop = 1; }
+                else if ((long long)(now - idle_since) > P.idle_timeout_ns) { set_error(P.ctl, VC_ETIMEOUT, 11); stop = 1; }
                 __nanosleep(backoff);
             }
-            backoff = min(backoff * 2, 2048);
+            backoff = min(backoff * 2, 4096);
             stop = tm.bcast(stop);
             if (stop) break;
         }
@@ -1091,14 +1158,12 @@ __global__ void search_init_kernel(SearchParams P, int first)
 {
     const int tid = blockIdx.x * blockDim.x + threadIdx.x;
     const int nth = gridDim.x * blockDim.x;
-    for (int e = first + tid; e < P.reg_cap; e += nth) {
-        P.reg[e].next = e + 1 < P.reg_cap ? e + 1 : -1;
-        P.reg[e].lock = 0;
-    }
     for (int s = tid; s < P.wl_cap; s += nth) P.wl_seq[s] = (unsigned)s;
-    if (tid == 0) {
-        for (int i = 0; i < kCtlWords; i++) P.ctl[i] = 0;
-        P.ctl[kRegHead] = first < P.reg_cap ? (unsigned)first : 0xffffffffu;
+    for (int i = tid; i < kCtlWords; i += nth) {
+        unsigned long long v = 0;
+        if (i == kRegHead * kCtlStride) v = 0xffffffffull;            // overflow list empty
+        if (i == kRegBump * kCtlStride) v = (unsigned long long)first;  // after the root entries
+        P.ctl[i] = v;
     }
 }
 
@@ -1144,9 +1209,9 @@ __global__ void search_roots_kernel(SearchParams P, const int *root_slot)
 
 __global__ void search_roots_publish(SearchParams P, int nroots)
 {
-    P.ctl[kWlTail] = (unsigned long long)nroots;
-    P.ctl[kWlCount] = (unsigned long long)nroots;
-    P.ctl[kRemaining] = (unsigned long long)nroots;
+    ctlw(P.ctl, kWlTail) = (unsigned long long)nroots;
+    ctlw(P.ctl, kWlCount) = (unsigned long long)nroots;
+    ctlw(P.ctl, kRemaining) = (unsigned long long)nroots;
 }
 
 }  // namespace vcg

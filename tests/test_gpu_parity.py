@@ -101,13 +101,17 @@ def test_edge_cases(vc):
     assert gpu_min(vc, k2s)[0] == 9
 
 
-@pytest.mark.parametrize("copies,copy_n,chain", [(8, 48, 4), (16, 48, 4), (32, 48, 6)])
-def test_component_heavy_small(vc, copies, copy_n, chain):
-    g = gg.component_heavy(1, copies=copies, copy_n=copy_n, p=0.12, chain=chain)
+# disjoint random graphs hung on a chain of articulation vertices: forces
+# nested branches on components; shapes small enough for the oracle
+@pytest.mark.parametrize("copies,copy_n,p,chain", [(3, 48, 0.12, 2), (4, 48, 0.12, 2), (8, 24, 0.2, 3),
+                                                   (12, 24, 0.2, 3), (16, 20, 0.2, 4), (32, 16, 0.25, 6)])
+def test_component_heavy_small(vc, copies, copy_n, p, chain):
+    g = gg.component_heavy(1, copies=copies, copy_n=copy_n, p=p, chain=chain)
     want = oracle.mvc(g.n, g.row_ptr, g.col, node_budget=5_000_000)[0]
-    size, st = gpu_min(vc, g)
-    assert size == want
-    assert st["component_branches"] > 0
+    for team in (32, 256):
+        size, st = gpu_min(vc, g, team=team)
+        assert size == want, team
+        assert st["component_branches"] + st["trivial_components"] > 0
 
 
 def test_chung_lu_50k(vc):
@@ -214,7 +218,7 @@ def test_node_budget_reports_cleanly(vc):
 
 
 def test_registry_exhaustion_reports_cleanly(vc):
-    g = gg.component_heavy(2, copies=16, copy_n=48, p=0.12, chain=4)
+    g = gg.component_heavy(1, copies=8, copy_n=24, p=0.2, chain=3)
     dg = vc.Graph.from_csr(g.row_ptr, g.col)
     with pytest.raises(vc.VcError) as ei:
         vc.solve_min(dg, registry_capacity=1)
