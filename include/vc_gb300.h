@@ -140,6 +140,51 @@ int vc_solve_batch(int32_t count, vc_graph *const *graphs, const int32_t *ks,
                    int32_t *out_status, int32_t *const *covers, int32_t *cover_lens,
                    vc_stats *stats);
 
+/* Root reduction and induced-subgraph build WITHOUT ANY ALLOCATION.
+ *
+ * The paper has no counterpart: this entry point exists for callers that
+ * cannot call cudaMalloc -- for instance a process whose device memory is
+ * owned by another allocator (a framework's caching pool that reserved the
+ * GPU), or a latency-critical loop that must not call cudaMalloc / cudaFree,
+ * which can synchronise the whole device.  It runs the same root phase as
+ * vc_solve_min (degree-one and degree-two-triangle rules, greedy bound,
+ * high-degree rule, induced subgraph; Section 4.2) on one graph and stops
+ * there.
+ *
+ * Scratch: one file-scope device array of 2 MiB (vertex limit
+ * n <= 65536).  Every GPU that loads this library holds it until the
+ * process exits.  The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress) and sets a kernel attribute; make that
+ * first call before any stream capture.  All calls share the array and it
+ * keeps the last call's contents, so calls whose work overlaps on the GPU
+ * (on different streams, or from different host threads) race: serialise
+ * them.  Larger graphs are rejected with VC_ECAPACITY; nothing is allocated
+ * by this function or by the kernels it launches.
+ *
+ * All pointers are DEVICE pointers owned by the caller:
+ *   d_row_ptr int32[n + 1], d_col int32[m2]   the graph (m2 = row_ptr[n],
+ *                                              passed by value); checked on
+ *                                              the device like vc_load_csr
+ *   k                          < 0: minimum cover; >= 0: bound for "<= k"
+ *   d_forced                   int32[n]: vertices forced into the cover
+ *   d_induced_row_ptr          int32[n + 1], d_induced_col int32[m2],
+ *   d_induced_orig             int32[n]: the induced subgraph (sorted rows,
+ *                              vertices relabelled 0..n'-1 in increasing
+ *                              original id; orig[i] = original id)
+ *   d_info                     int32[8]: status (VC_OK / VC_EINVAL), forced
+ *                              count, n', 2|E'|, greedy cover size (-1 if not
+ *                              computed), answered (1: the root phase
+ *                              settled the answer), the answer when
+ *                              answered (minimum size; PVC: size or -1),
+ *                              max degree of the induced subgraph.
+ * Asynchronous on `cuda_stream`: d_info is valid once the stream reaches
+ * the end of the call.  Returns VC_OK, VC_EINVAL (bad arguments),
+ * VC_ECAPACITY (n > 65536) or VC_ECUDA (launch failure). */
+int vc_root_reduce_static(int32_t n, int32_t m2, const int32_t *d_row_ptr, const int32_t *d_col,
+                          int32_t k, int32_t *d_forced, int32_t *d_induced_row_ptr,
+                          int32_t *d_induced_col, int32_t *d_induced_orig, int32_t *d_info,
+                          void *cuda_stream);
+
 /* Release the handle and all device memory it owns.  NULL is a no-op. */
 void vc_free(vc_graph *g);
 

@@ -92,6 +92,7 @@ SIGNATURES = {
     "vc_solve_min": (ctypes.c_int, [_P, _P, _P, _P, _P, _P]),
     "vc_solve_k": (ctypes.c_int, [_P, _I, _P, _P, _P, _P, _P]),
     "vc_solve_batch": (ctypes.c_int, [_I, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
+    "vc_root_reduce_static": (ctypes.c_int, [_I, _I, _P, _P, _I, _P, _P, _P, _P, _P, _P]),
     "vc_free": (None, [_P]),
     "vc_strerror": (ctypes.c_char_p, [ctypes.c_int]),
 }

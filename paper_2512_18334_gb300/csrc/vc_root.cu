@@ -13,6 +13,7 @@
 // simultaneous application exact (no K2 or triangle gets every vertex).
 // Phase 1 uses only the first two rules (they need no bound), then a greedy
 // cover gives the bound, then phase 2 adds the high-degree rule.
+#include <algorithm>
 #include <climits>
 
 #include "vc_common.cuh"
@@ -744,3 +745,153 @@ cudaError_t finalize_run(QueryDesc *d_q, int nq, const RegEntry *reg, const uint
 }
 
 }  // namespace vcg
+
+// ------------------------------------------------------------ no-allocation variant
+//
+// vc_root_reduce_static(): the root reduction + induced subgraph above, for
+// callers that cannot allocate device memory.  Its scratch is one file-scope
+// device array, shared by every call in the process and kept between calls.
+
+#include <mutex>
+
+namespace vcg {
+
+constexpr int kStaticMaxN = 65536;
+constexpr size_t kStaticBytes = (size_t)2 << 20;   // 2 MiB, resident on every device that loads the library
+constexpr int kStaticMaxDevices = 64;
+
+static __device__ __align__(256) unsigned char vc_static_scratch[kStaticBytes];
+
+// Fixed layout inside the array, sized for kStaticMaxN vertices.
+struct StaticLayout {
+    static constexpr size_t kDesc = 0;                                    // QueryDesc
+    static constexpr size_t kErr = 512;                                   // 4 ints
+    static constexpr size_t kArr = 1024;                                  // int arrays
+    static constexpr size_t kIntArr = (size_t)kStaticMaxN * 4;
+    static constexpr size_t kDeg = kArr;
+    static constexpr size_t kAux = kDeg + kIntArr;
+    static constexpr size_t kFr0 = kAux + kIntArr;
+    static constexpr size_t kFr1 = kFr0 + kIntArr;
+    static constexpr size_t kFlag = kFr1 + kIntArr;
+    static constexpr size_t kHeavy = kFlag + kIntArr;
+    static constexpr size_t kSt = kHeavy + kIntArr;
+    static constexpr size_t kCover = kSt + kStaticMaxN;
+    static constexpr size_t kEnd = kCover + kStaticMaxN;
+};
+static_assert(StaticLayout::kEnd <= kStaticBytes, "static scratch too small");
+static_assert(sizeof(QueryDesc) <= StaticLayout::kErr, "descriptor does not fit");
+
+// One thread: clear the validation words (they must start at zero).
+__global__ void static_clear_kernel(char *base)
+{
+    int *err = (int *)(base + StaticLayout::kErr);
+    err[0] = 0; err[1] = 0; err[2] = 0; err[3] = 0;
+}
+
+// One thread: fill the descriptor from the arguments and the validation result.
+__global__ void static_setup_kernel(char *base, int n, int m2, const int *rp, const int *col, int k,
+                                    int *forced, int *irp, int *icol, int *iorig)
+{
+    QueryDesc *Q = (QueryDesc *)(base + StaticLayout::kDesc);
+    const int *err = (const int *)(base + StaticLayout::kErr);
+    QueryDesc q;
+    memset(&q, 0, sizeof(q));
+    q.n = n;
+    q.m2 = m2;
+    q.rp = rp;
+    q.col = col;
+    q.k = k;
+    q.maxdeg_in = err[2];
+    q.deg = (int *)(base + StaticLayout::kDeg);
+    q.aux = (int *)(base + StaticLayout::kAux);
+    q.fr0 = (int *)(base + StaticLayout::kFr0);
+    q.fr1 = (int *)(base + StaticLayout::kFr1);
+    q.flag = (int *)(base + StaticLayout::kFlag);
+    q.heavy = (int *)(base + StaticLayout::kHeavy);
+    q.forced_list = forced;
+    q.st = (uint8_t *)(base + StaticLayout::kSt);
+    q.cover_flags = (uint8_t *)(base + StaticLayout::kCover);
+    q.rp2 = irp;
+    q.col2 = icol;
+    q.orig = iorig;
+    q.status = (n > 0 && (err[0] != 0 || (long long)err[1] * 2 != m2)) ? VC_EINVAL : VC_OK;
+    q.greedy = -1;
+    *Q = q;
+}
+
+// One thread: copy the outcome to the caller's info array.
+__global__ void static_export_kernel(const char *base, int *info)
+{
+    const QueryDesc *Q = (const QueryDesc *)(base + StaticLayout::kDesc);
+    const bool ok = Q->status == VC_OK;
+    info[0] = Q->status;
+    info[1] = ok ? Q->forced : 0;
+    info[2] = ok ? Q->np : 0;
+    info[3] = ok ? Q->m2p : 0;
+    info[4] = ok ? Q->greedy : -1;
+    info[5] = ok ? Q->answered : 0;
+    info[6] = ok && Q->answered ? Q->result : -1;
+    info[7] = ok ? Q->maxdeg : 0;
+}
+
+// Per-device set-up: the device address of the scratch array (a host-side
+// use of the array's name is only a stand-in, not a device address).
+static std::mutex g_static_mu;
+static char *g_static_ptr[kStaticMaxDevices];
+
+static int static_setup(char **out)
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return VC_ECUDA;
+    if (dev < 0 || dev >= kStaticMaxDevices) return VC_ECAPACITY;
+    std::lock_guard<std::mutex> lk(g_static_mu);
+    if (!g_static_ptr[dev]) {
+        void *p = nullptr;
+        if (cudaGetSymbolAddress(&p, vc_static_scratch) != cudaSuccess || !p) return VC_ECUDA;
+        if (cudaFuncSetAttribute(root_kernel<SmemStore>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)kRootSmemMax) != cudaSuccess)
+            return VC_ECUDA;
+        g_static_ptr[dev] = (char *)p;
+    }
+    *out = g_static_ptr[dev];
+    return VC_OK;
+}
+
+}  // namespace vcg
+
+extern "C" int vc_root_reduce_static(int32_t n, int32_t m2, const int32_t *d_row_ptr, const int32_t *d_col,
+                                     int32_t k, int32_t *d_forced, int32_t *d_induced_row_ptr,
+                                     int32_t *d_induced_col, int32_t *d_induced_orig, int32_t *d_info,
+                                     void *cuda_stream)
+{
+    using namespace vcg;
+    if (n < 0 || m2 < 0 || (m2 & 1) || !d_info) return VC_EINVAL;
+    if (n > kStaticMaxN) return VC_ECAPACITY;
+    if (n > 0 && (!d_row_ptr || !d_forced || !d_induced_row_ptr || !d_induced_orig)) return VC_EINVAL;
+    if (m2 > 0 && (!d_col || !d_induced_col)) return VC_EINVAL;
+    char *base = nullptr;
+    int rc = static_setup(&base);
+    if (rc != VC_OK) return rc;
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    int *err = (int *)(base + StaticLayout::kErr);
+    static_clear_kernel<<<1, 1, 0, s>>>(base);
+    if (cudaGetLastError() != cudaSuccess) return VC_ECUDA;
+    if (n > 0) {
+        const int threads = 256;
+        const int blocks = std::min(4096, (n + 1 + threads - 1) / threads);
+        validate_rowptr_kernel<<<blocks, threads, 0, s>>>(n, m2, d_row_ptr, err);
+        validate_col_kernel<<<blocks, threads, 0, s>>>(n, d_row_ptr, d_col, err);
+        max_degree_kernel<<<blocks, threads, 0, s>>>(n, d_row_ptr, err);
+        if (cudaGetLastError() != cudaSuccess) return VC_ECUDA;
+    }
+    static_setup_kernel<<<1, 1, 0, s>>>(base, n, m2, d_row_ptr, d_col, k < 0 ? -1 : k, d_forced,
+                                        d_induced_row_ptr, d_induced_col, d_induced_orig);
+    QueryDesc *dq = (QueryDesc *)(base + StaticLayout::kDesc);
+    const size_t smem = SmemStore::smem_bytes(n);
+    if (smem <= kRootSmemMax)
+        root_kernel<SmemStore><<<1, kRootThreads, smem, s>>>(dq);
+    else
+        root_kernel<GlobalStore><<<1, kRootThreads, 0, s>>>(dq);
+    static_export_kernel<<<1, 1, 0, s>>>(base, d_info);
+    return cudaGetLastError() == cudaSuccess ? VC_OK : VC_ECUDA;
+}
