@@ -82,12 +82,14 @@ __global__ void max_degree_kernel(int n, const int *rp, int *err)
 // ------------------------------------------------------------ root kernel
 
 constexpr int kRootThreads = 1024;
-constexpr int kHeavyRow = 32;   // rows longer than this are scanned by a whole warp
+constexpr int kHeavyRow = 32;    // rows longer than this are scanned by a whole warp
+constexpr int kGiantRow = 512;   // rows longer than this are applied by the whole block
 
 struct RootShared {
     int cnt;        // marks in this round
     int fcnt;       // next-frontier size
     int hcnt;       // heavy-row list size
+    int gcnt;       // giant-row list size
     int forced;
     int delta;      // max live degree seen in the last full scan
     int red[33];
@@ -176,6 +178,19 @@ __device__ __forceinline__ unsigned mix32(unsigned x)
     x ^= x >> 15; x *= 0x846ca68bu;
     x ^= x >> 16;
     return x;
+}
+
+// Ask the memory system to bring [p, p + bytes) into L2 (bulk prefetch,
+// 16-byte granules); the block's threads split the range.
+__device__ __forceinline__ void prefetch_l2(const void *p, size_t bytes)
+{
+    const size_t start = ((size_t)p + 15) & ~(size_t)15;
+    const size_t end = ((size_t)p + bytes) & ~(size_t)15;
+    constexpr size_t kPiece = 16384;
+    for (size_t a = start + (size_t)threadIdx.x * kPiece; a < end; a += (size_t)blockDim.x * kPiece) {
+        const size_t len = end - a < kPiece ? end - a : kPiece;
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a), "r"((unsigned)len) : "memory");
+    }
 }
 
 // Where the per-vertex root state lives.
@@ -280,6 +295,23 @@ struct Root {
         agg_append(&sh.fcnt, next, x, S.try_flag(x));
     }
 
+    // Is w in u's (sorted) row?  Short rows: batched linear scan; else binary search.
+    __device__ bool row_has(int u, int w) const
+    {
+        const int a = __ldg(rp + u), b = __ldg(rp + u + 1);
+        if (b - a > 16) return bsearch_row(col + a, b - a, w);
+        for (int e0 = a; e0 < b; e0 += 8) {
+            int xs[8];
+#pragma unroll
+            for (int j = 0; j < 8; j++) xs[j] = e0 + j < b ? __ldg(col + e0 + j) : -1;
+            bool hit = false;
+#pragma unroll
+            for (int j = 0; j < 8; j++) hit |= xs[j] == w;
+            if (hit) return true;
+        }
+        return false;
+    }
+
     // The rule decision for v once its live neighbours u (and w) are known.
     __device__ void decide(int *next, int v, int d, int u, int w)
     {
@@ -289,7 +321,7 @@ struct Root {
             else mark(u);
         } else if (d == 2) {
             if (w < 0) return;
-            if (bsearch_row(col + __ldg(rp + u), __ldg(rp + u + 1) - __ldg(rp + u), w)) {
+            if (row_has(u, w)) {
                 int p = INT_MAX;
                 if (S.d(u) == 2 && u < v) p = u;
                 if (S.d(w) == 2 && w < v && w < p) p = w;
@@ -313,13 +345,20 @@ struct Root {
             agg_append(&sh.hcnt, heavy, v, true);
             return;
         }
+        // the first d live neighbours; eight independent loads in flight at a time
         int u = -1, w = -1;
-        for (int e = a; e < b; e++) {
-            const int x = __ldg(col + e);
-            if (live(x)) {
-                if (u < 0) { u = x; if (d == 1) break; }
-                else { w = x; break; }
+        for (int e0 = a; e0 < b; e0 += 8) {
+            int xs[8];
+#pragma unroll
+            for (int j = 0; j < 8; j++) xs[j] = e0 + j < b ? __ldg(col + e0 + j) : -1;
+#pragma unroll
+            for (int j = 0; j < 8; j++) {
+                const int x = xs[j];
+                if (x >= 0 && w < 0 && live(x)) {
+                    if (u < 0) u = x; else w = x;
+                }
             }
+            if (d == 1 ? u >= 0 : w >= 0) break;
         }
         decide(next, v, d, u, w);
     }
@@ -347,16 +386,30 @@ struct Root {
     }
 
     // Put u in the cover: lower the degrees of its live, unmarked neighbours.
+    __device__ __forceinline__ void apply_one(int *next, int x)
+    {
+        if (S.s(x) == 0 && S.d(x) > 0 && !S.marked(x)) {
+            S.dec(x);
+            push_frontier(next, x);
+        }
+    }
+
     __device__ void apply_row(int *next, int u, int lane, int stride)
     {
         const int a = __ldg(rp + u), b = __ldg(rp + u + 1);
-        for (int e = a + lane; e < b; e += stride) {
-            const int x = __ldg(col + e);
-            if (S.s(x) == 0 && S.d(x) > 0 && !S.marked(x)) {
-                S.dec(x);
-                push_frontier(next, x);
+        if (stride == 1) {
+            // one thread: eight independent loads in flight at a time
+            for (int e0 = a; e0 < b; e0 += 8) {
+                int xs[8];
+#pragma unroll
+                for (int j = 0; j < 8; j++) xs[j] = e0 + j < b ? __ldg(col + e0 + j) : -1;
+#pragma unroll
+                for (int j = 0; j < 8; j++)
+                    if (xs[j] >= 0) apply_one(next, xs[j]);
             }
+            return;
         }
+        for (int e = a + lane; e < b; e += stride) apply_one(next, __ldg(col + e));
     }
 
     // Synchronous rounds of the rules until nothing is marked.  hd: use the
@@ -409,16 +462,22 @@ struct Root {
             __syncthreads();
             if (threadIdx.x == 0) sh.hcnt = 0;
             __syncthreads();
-            // apply: lower the degrees of the marked vertices' live neighbours
+            // apply: lower the degrees of the marked vertices' live neighbours;
+            // short rows by one thread, long rows by a warp, giant rows (from
+            // the end of the same list) by the whole block
+            if (threadIdx.x == 0) sh.gcnt = 0;
+            __syncthreads();
             for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
                 const int u = Q.forced_list[base + i];
-                const bool hv = __ldg(rp + u + 1) - __ldg(rp + u) > kHeavyRow;
-                agg_append(&sh.hcnt, heavy, u, hv);
-                if (!hv) apply_row(next, u, 0, 1);
+                const int len = __ldg(rp + u + 1) - __ldg(rp + u);
+                agg_append(&sh.hcnt, heavy, u, len > kHeavyRow && len <= kGiantRow);
+                if (len > kGiantRow) heavy[n - 1 - atomicAdd(&sh.gcnt, 1)] = u;   // rare
+                if (len <= kHeavyRow) apply_row(next, u, 0, 1);
             }
             __syncthreads();
-            const int hc2 = sh.hcnt;
+            const int hc2 = sh.hcnt, gc = sh.gcnt;
             for (int i = warp; i < hc2; i += nwarps) apply_row(next, heavy[i], lane, 32);
+            for (int i = 0; i < gc; i++) apply_row(next, heavy[n - 1 - i], threadIdx.x, blockDim.x);
             __syncthreads();
             for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
                 const int u = Q.forced_list[base + i];
@@ -549,6 +608,8 @@ struct Root {
 
     __device__ void run()
     {
+        prefetch_l2(rp, (size_t)(n + 1) * 4);
+        prefetch_l2(col, (size_t)Q.m2 * 4);
         for (int v = threadIdx.x; v < n; v += blockDim.x) {
             S.set_d(v, __ldg(rp + v + 1) - __ldg(rp + v));
             S.set_s(v, 0);
@@ -641,6 +702,598 @@ __global__ void __launch_bounds__(kRootThreads, 1) root_kernel(QueryDesc *qs)
     r.run();
 }
 
+// ------------------------------------------------------------ cluster root kernel
+//
+// The same root phase for ONE large graph on a thread-block cluster of up to
+// 16 CTAs (one per SM).  Vertex v is owned by CTA v >> cs; its 16-bit degree,
+// state byte, mark bit and frontier bit live in that CTA's shared memory and
+// every CTA reaches them through distributed shared memory.  Each CTA examines
+// the vertices it owns; marks and frontier pushes go to the owner's lists.
+// Rounds are separated by cluster barriers; per-round totals are exchanged
+// through rank 0's shared memory.  Decisions taken from exchanged totals are
+// identical in every CTA, so all CTAs pass the same barriers.
+
+}  // namespace vcg
+#include <cooperative_groups.h>
+namespace vcg {
+namespace cgx = cooperative_groups;
+
+constexpr int kClusterMax = 16;
+constexpr int kClusterMinN = 8192;    // smaller graphs use one block
+
+struct ClusterShared {
+    int cnt;          // marks owned by this CTA in this round
+    int fcnt;         // frontier entries owned by this CTA
+    int hcnt, gcnt;   // heavy / giant row lists of this CTA
+    int red[33];
+    long long tot[4]; // exchanged totals (local copy)
+    int slot[2][kClusterMax][4];   // rank 0's copy is the exchange area (double-buffered)
+    unsigned long long rbase[kClusterMax];   // dynamic smem base of each rank
+    unsigned long long rsh[kClusterMax];     // ClusterShared of each rank
+};
+
+// per CTA: 16-bit degrees, then forced / mark / frontier bitmaps
+__host__ __device__ inline size_t cluster_smem_bytes(int chunk)
+{
+    return (size_t)chunk * 2 + 3 * ((size_t)chunk / 8);
+}
+
+struct ClusterRoot {
+    QueryDesc &Q;
+    ClusterShared &sh;
+    cgx::cluster_group cl;
+    int n, C, rank, cs, chunk;
+    int vbeg, vcnt;          // vertices owned here: [vbeg, vbeg + vcnt)
+    const int *rp, *col;
+    int ftot;                // cluster-wide forced count (same in every CTA)
+    int xround;              // exchange buffer selector
+
+    __device__ ClusterRoot(QueryDesc &q, ClusterShared &s, char *smem, int cs_)
+        : Q(q), sh(s), cl(cgx::this_cluster())
+    {
+        n = Q.n;
+        C = (int)cl.num_blocks();
+        rank = (int)cl.block_rank();
+        cs = cs_;
+        chunk = 1 << cs;
+        vbeg = rank << cs;
+        vcnt = max(0, min(chunk, n - vbeg));
+        rp = Q.rp;
+        col = Q.col;
+        ftot = 0;
+        xround = 0;
+        if (threadIdx.x < C) {
+            sh.rbase[threadIdx.x] = (unsigned long long)cl.map_shared_rank(smem, threadIdx.x);
+            sh.rsh[threadIdx.x] = (unsigned long long)cl.map_shared_rank(&sh, threadIdx.x);
+        }
+        uint32_t *bits = (uint32_t *)(smem + 2 * (size_t)chunk);
+        for (int i = threadIdx.x; i < 3 * (chunk / 32); i += blockDim.x) bits[i] = 0;
+    }
+
+    // ---- distributed state
+    __device__ __forceinline__ char *base(int r) const { return (char *)sh.rbase[r]; }
+    __device__ __forceinline__ uint16_t *degp(int r) const { return (uint16_t *)base(r); }
+    __device__ __forceinline__ uint32_t *forcedp(int r) const { return (uint32_t *)(base(r) + 2 * (size_t)chunk); }
+    __device__ __forceinline__ uint32_t *markp(int r) const
+    {
+        return (uint32_t *)(base(r) + 2 * (size_t)chunk + chunk / 8);
+    }
+    __device__ __forceinline__ uint32_t *flagp(int r) const
+    {
+        return (uint32_t *)(base(r) + 2 * (size_t)chunk + 2 * (chunk / 8));
+    }
+    __device__ __forceinline__ ClusterShared *shp(int r) const { return (ClusterShared *)sh.rsh[r]; }
+
+    __device__ __forceinline__ int d(int v) const { return ((volatile uint16_t *)degp(v >> cs))[v & (chunk - 1)]; }
+    __device__ __forceinline__ bool forced(int v) const
+    {
+        const int l = v & (chunk - 1);
+        return ((volatile uint32_t *)forcedp(v >> cs))[l >> 5] >> (l & 31) & 1u;
+    }
+    // a vertex is in the graph when it was not forced in an earlier round
+    // and has a neighbour left
+    __device__ __forceinline__ bool live(int x) const { return !forced(x) && d(x) > 0; }
+    __device__ __forceinline__ void set_bit(uint32_t *words, int v)
+    {
+        const int l = v & (chunk - 1);
+        atomicOr(&words[l >> 5], 1u << (l & 31));    // result unused: a fire-and-forget reduction
+    }
+    __device__ __forceinline__ void dec(int v)
+    {
+        const int l = v & (chunk - 1);
+        unsigned *w = (unsigned *)((char *)degp(v >> cs) + 2 * (l & ~1));
+        atomicSub(w, 1u << (16 * (l & 1)));          // result unused
+    }
+    __device__ __forceinline__ void mark(int u) { set_bit(markp(u >> cs), u); }
+    __device__ __forceinline__ void push_frontier(int x) { set_bit(flagp(x >> cs), x); }
+
+    __device__ bool row_has(int u, int w) const
+    {
+        const int a = __ldg(rp + u), b = __ldg(rp + u + 1);
+        if (b - a > 16) return bsearch_row(col + a, b - a, w);
+        for (int e0 = a; e0 < b; e0 += 8) {
+            int xs[8];
+#pragma unroll
+            for (int j = 0; j < 8; j++) xs[j] = e0 + j < b ? __ldg(col + e0 + j) : -1;
+            bool hit = false;
+#pragma unroll
+            for (int j = 0; j < 8; j++) hit |= xs[j] == w;
+            if (hit) return true;
+        }
+        return false;
+    }
+
+    __device__ void decide(int v, int dv, int u, int w)
+    {
+        if (dv == 1) {
+            if (u < 0) return;
+            if (d(u) == 1 && u < v) push_frontier(u);   // u's rule fires instead
+            else mark(u);
+        } else if (dv == 2) {
+            if (w < 0) return;
+            if (row_has(u, w)) {
+                int p = INT_MAX;
+                if (d(u) == 2 && u < v) p = u;
+                if (d(w) == 2 && w < v && w < p) p = w;
+                if (p != INT_MAX) push_frontier(p);
+                else { mark(u); mark(w); }
+            }
+        }
+    }
+
+    __device__ void examine(int *hv, int v, int bud)
+    {
+        if (forced(v)) return;
+        const int dv = d(v);
+        if (dv == 0) return;
+        if (dv > bud) mark(v);
+        if (dv > 2) return;
+        const int a = __ldg(rp + v), b = __ldg(rp + v + 1);
+        if (b - a > kHeavyRow) {
+            hv[atomicAdd(&sh.hcnt, 1)] = v;
+            return;
+        }
+        int u = -1, w = -1;
+        for (int e0 = a; e0 < b; e0 += 8) {
+            int xs[8];
+            bool lv[8];
+#pragma unroll
+            for (int j = 0; j < 8; j++) xs[j] = e0 + j < b ? __ldg(col + e0 + j) : -1;
+#pragma unroll
+            for (int j = 0; j < 8; j++) lv[j] = xs[j] >= 0 && live(xs[j]);
+#pragma unroll
+            for (int j = 0; j < 8; j++) {
+                if (lv[j] && w < 0) {
+                    if (u < 0) u = xs[j]; else w = xs[j];
+                }
+            }
+            if (dv == 1 ? u >= 0 : w >= 0) break;
+        }
+        decide(v, dv, u, w);
+    }
+
+    __device__ void warp_live_nbrs(int v, int need, int &u, int &w) const
+    {
+        const int lane = threadIdx.x & 31;
+        const int a = __ldg(rp + v), b = __ldg(rp + v + 1);
+        u = -1;
+        w = -1;
+        int found = 0;
+        for (int base0 = a; base0 < b && found < need; base0 += 32) {
+            const int e = base0 + lane;
+            const int x = e < b ? __ldg(col + e) : -1;
+            unsigned m = __ballot_sync(kFull, x >= 0 && live(x));
+            while (m && found < need) {
+                const int pos = __ffs(m) - 1;
+                const int val = __shfl_sync(kFull, x, pos);
+                if (found == 0) u = val; else w = val;
+                found++;
+                m &= m - 1;
+            }
+        }
+    }
+
+    // u is in the cover: every live neighbour loses one degree and joins the
+    // next frontier (forced bits already include this round's marks)
+    __device__ void apply_row(int u, int lane, int stride)
+    {
+        const int a = __ldg(rp + u), b = __ldg(rp + u + 1);
+        if (stride == 1) {
+            for (int e0 = a; e0 < b; e0 += 8) {
+                int xs[8];
+                bool lv[8];
+#pragma unroll
+                for (int j = 0; j < 8; j++) xs[j] = e0 + j < b ? __ldg(col + e0 + j) : -1;
+#pragma unroll
+                for (int j = 0; j < 8; j++) lv[j] = xs[j] >= 0 && live(xs[j]);
+#pragma unroll
+                for (int j = 0; j < 8; j++)
+                    if (lv[j]) { dec(xs[j]); push_frontier(xs[j]); }
+            }
+            return;
+        }
+        for (int e = a + lane; e < b; e += stride) {
+            const int x = __ldg(col + e);
+            if (live(x)) { dec(x); push_frontier(x); }
+        }
+    }
+
+    // Take the set bits of `words` (my chunk; fetched and cleared atomically,
+    // other CTAs may be setting bits meanwhile) into list[] as vertex ids;
+    // returns the count.  new_forced: keep only bits whose forced bit is clear
+    // and add them to the forced bitmap.  Each thread owns words tid + j*T,
+    // j < 4 (chunk <= 4 * 32 * blockDim).
+    __device__ int bits_to_list(uint32_t *words, int *list, bool new_forced)
+    {
+        uint32_t *fw = forcedp(rank);
+        const int nw = chunk >> 5;
+        uint32_t m[4];
+        int c = 0;
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            const int i = threadIdx.x + j * blockDim.x;
+            uint32_t x = 0;
+            if (i < nw) {
+                x = atomicExch(&words[i], 0u);
+                if (new_forced) { x &= ~fw[i]; fw[i] |= x; }
+            }
+            m[j] = x;
+            c += __popc(x);
+        }
+        int tot;
+        int off = block_excl_scan(c, sh.red, &tot);
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            const int i = threadIdx.x + j * blockDim.x;
+            uint32_t x = m[j];
+            while (x) {
+                const int b = __ffs(x) - 1;
+                list[off++] = vbeg + i * 32 + b;
+                x &= x - 1;
+            }
+        }
+        __syncthreads();
+        return tot;
+    }
+
+    // Every CTA contributes four numbers; every CTA gets the cluster totals
+    // (sum for 0..2, max for 3) in sh.tot.  One cluster barrier (the slots
+    // are double-buffered).
+    __device__ void exchange(long long a0, long long a1, long long a2, long long a3)
+    {
+        const int buf = xround & 1;
+        xround++;
+        if (threadIdx.x == 0) {
+            int *sl = shp(0)->slot[buf][rank];
+            sl[0] = (int)a0; sl[1] = (int)a1; sl[2] = (int)a2; sl[3] = (int)a3;
+        }
+        cl.sync();
+        if (threadIdx.x < 32) {
+            const int l = threadIdx.x;
+            long long v0 = 0, v1 = 0, v2 = 0, v3 = INT_MIN;
+            if (l < C) {
+                const volatile int *sl = shp(0)->slot[buf][l];
+                v0 = sl[0]; v1 = sl[1]; v2 = sl[2]; v3 = sl[3];
+            }
+            for (int o = 16; o > 0; o >>= 1) {
+                v0 += __shfl_xor_sync(kFull, v0, o);
+                v1 += __shfl_xor_sync(kFull, v1, o);
+                v2 += __shfl_xor_sync(kFull, v2, o);
+                v3 = max(v3, (long long)__shfl_xor_sync(kFull, v3, o));
+            }
+            if (l == 0) { sh.tot[0] = v0; sh.tot[1] = v1; sh.tot[2] = v2; sh.tot[3] = v3; }
+        }
+        __syncthreads();
+    }
+
+    // Prefix over ranks of two per-CTA values (exclusive) and their totals.
+    __device__ void exchange_prefix(int mine, int mine2, int &off, int &tot, int &off2, int &tot2)
+    {
+        const int buf = xround & 1;
+        xround++;
+        if (threadIdx.x == 0) {
+            int *sl = shp(0)->slot[buf][rank];
+            sl[0] = mine; sl[1] = mine2;
+        }
+        cl.sync();
+        if (threadIdx.x == 0) {
+            int o = 0, t = 0, o2 = 0, t2 = 0;
+            for (int r = 0; r < C; r++) {
+                const int x = ((volatile int *)shp(0)->slot[buf][r])[0];
+                const int y = ((volatile int *)shp(0)->slot[buf][r])[1];
+                if (r < rank) { o += x; o2 += y; }
+                t += x;
+                t2 += y;
+            }
+            sh.red[0] = o; sh.red[1] = t; sh.red[2] = o2; sh.red[3] = t2;
+        }
+        __syncthreads();
+        off = sh.red[0]; tot = sh.red[1]; off2 = sh.red[2]; tot2 = sh.red[3];
+        __syncthreads();
+    }
+
+    // Synchronous rounds, three cluster barriers each:
+    //   B1  last round's decrements and frontier bits have landed
+    //   B2  this round's marks and partner bits have landed (inside exchange)
+    //   B3  totals known, forced bits include this round's marks
+    __device__ bool reduce_rounds(bool hd, int bound)
+    {
+        int *fl = Q.fr0 + vbeg;        // my frontier list
+        int *ml = Q.heavy + vbeg;      // my marks of this round
+        int *hv = Q.aux + vbeg;        // heavy rows (front) / giant rows (back)
+        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+        bool first = true;
+        long long delta = INT_MAX;
+        for (;;) {
+            const int bud = hd ? bound - ftot - 1 : INT_MAX;
+            if (hd && bud < 0) return false;
+            const bool full = first || (hd && delta > bud);
+            first = false;
+            cl.sync();                                                    // B1
+            if (threadIdx.x == 0) { sh.hcnt = 0; sh.gcnt = 0; }
+            const int fsize = bits_to_list(flagp(rank), fl, false);       // my frontier
+            int dmax = 0;
+            if (full) {
+                for (int i = threadIdx.x; i < vcnt; i += blockDim.x) {
+                    const int v = vbeg + i;
+                    if (!forced(v)) dmax = max(dmax, d(v));
+                }
+                for (int i = threadIdx.x; i < vcnt; i += blockDim.x) examine(hv, vbeg + i, bud);
+            } else {
+                for (int i = threadIdx.x; i < fsize; i += blockDim.x) examine(hv, fl[i], bud);
+            }
+            __syncthreads();
+            const int hc = sh.hcnt;
+            for (int i = warp; i < hc; i += nwarps) {
+                const int v = hv[i];
+                const int dv = d(v);
+                int u, w;
+                warp_live_nbrs(v, dv, u, w);
+                if (lane == 0) decide(v, dv, u, w);
+            }
+            const int dm = full ? block_max(dmax, sh.red) : 0;
+            cl.sync();                                                    // B2
+            // this round's marks that I own: list them, fold them into forced
+            const int cnt = bits_to_list(markp(rank), ml, true);
+            int pend = 0;
+            {
+                const uint32_t *fw = flagp(rank);
+                for (int i = threadIdx.x; i < chunk / 32; i += blockDim.x) pend += __popc(fw[i]);
+                pend = block_sum(pend, sh.red);
+            }
+            exchange(cnt, pend, 0, dm);                                   // B3
+            const long long tcnt = sh.tot[0], tpend = sh.tot[1];
+            if (full) delta = sh.tot[3];
+            if (rank == 0 && threadIdx.x == 0) Q.rounds++;
+            if (tcnt == 0 && tpend == 0) return true;
+            // append my marks to the forced list
+            __shared__ int fbase;
+            if (threadIdx.x == 0) fbase = cnt ? atomicAdd(&Q.forced, cnt) : 0;
+            if (threadIdx.x == 0) { sh.hcnt = 0; sh.gcnt = 0; }
+            __syncthreads();
+            for (int i = threadIdx.x; i < cnt; i += blockDim.x) Q.forced_list[fbase + i] = ml[i];
+            // apply: short rows by one thread, long by a warp, giant by the block
+            for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
+                const int u = ml[i];
+                const int len = __ldg(rp + u + 1) - __ldg(rp + u);
+                if (len > kGiantRow) hv[vcnt - 1 - atomicAdd(&sh.gcnt, 1)] = u;
+                else if (len > kHeavyRow) hv[atomicAdd(&sh.hcnt, 1)] = u;
+                else apply_row(u, 0, 1);
+            }
+            __syncthreads();
+            const int hc2 = sh.hcnt, gc = sh.gcnt;
+            for (int i = warp; i < hc2; i += nwarps) apply_row(hv[i], lane, 32);
+            for (int i = 0; i < gc; i++) apply_row(hv[vcnt - 1 - i], threadIdx.x, blockDim.x);
+            ftot += (int)tcnt;
+            __syncthreads();
+        }
+    }
+
+    __device__ long long live_edges2()
+    {
+        cl.sync();   // every decrement of the last round has landed
+        int e2 = 0;
+        for (int i = threadIdx.x; i < vcnt; i += blockDim.x)
+            if (!forced(vbeg + i)) e2 += d(vbeg + i);
+        e2 = block_sum(e2, sh.red);
+        exchange(e2, 0, 0, 0);
+        return sh.tot[0];
+    }
+
+    __device__ int greedy()
+    {
+        int *aux = Q.aux, *join = Q.fr0;
+        for (int i = threadIdx.x; i < vcnt; i += blockDim.x) aux[vbeg + i] = live(vbeg + i) ? 0 : 3;
+        cl.sync();
+        for (;;) {
+            int any = 0;
+            for (int i = threadIdx.x; i < vcnt; i += blockDim.x) {
+                const int v = vbeg + i;
+                if (__ldcg(aux + v) != 0) continue;
+                const unsigned long long pv = ((unsigned long long)d(v) << 32) | mix32((unsigned)v);
+                bool j = true;
+                for (int e = __ldg(rp + v); e < __ldg(rp + v + 1) && j; e++) {
+                    const int x = __ldg(col + e);
+                    const int ax = ((volatile int *)aux)[x];
+                    if (ax == 1) j = false;
+                    else if (ax == 0) {
+                        const unsigned long long px = ((unsigned long long)d(x) << 32) | mix32((unsigned)x);
+                        if (px < pv || (px == pv && x < v)) j = false;
+                    }
+                }
+                join[v] = j;
+            }
+            cl.sync();
+            for (int i = threadIdx.x; i < vcnt; i += blockDim.x) {
+                const int v = vbeg + i;
+                if (__ldcg(aux + v) == 0 && join[v]) { aux[v] = 4; any = 1; }
+            }
+            any = block_sum(any, sh.red);
+            exchange(any, 0, 0, 0);
+            if (sh.tot[0] == 0) break;
+            for (int i = threadIdx.x; i < vcnt; i += blockDim.x) {
+                const int v = vbeg + i;
+                if (__ldcg(aux + v) != 4) continue;
+                for (int e = __ldg(rp + v); e < __ldg(rp + v + 1); e++) atomicCAS(&aux[__ldg(col + e)], 0, 2);
+            }
+            cl.sync();
+            for (int i = threadIdx.x; i < vcnt; i += blockDim.x)
+                if (__ldcg(aux + vbeg + i) == 4) aux[vbeg + i] = 1;
+            cl.sync();
+        }
+        int c = 0;
+        for (int i = threadIdx.x; i < vcnt; i += blockDim.x) {
+            const int v = vbeg + i;
+            const int av = __ldcg(aux + v);
+            const bool g = av == 2 || av == 0;
+            Q.cover_flags[v] = (forced(v) || g) ? 1 : 0;
+            c += g;
+        }
+        c = block_sum(c, sh.red);
+        exchange(c, 0, 0, 0);
+        const int tot = (int)sh.tot[0];
+        for (int i = threadIdx.x; i < vcnt; i += blockDim.x) aux[vbeg + i] = 0;
+        cl.sync();
+        return tot;
+    }
+
+    __device__ void induce()
+    {
+        const int T = blockDim.x;
+        const int per = (vcnt + T - 1) / T;
+        const int beg = vbeg + min(vcnt, (int)threadIdx.x * per), end = vbeg + min(vcnt, ((int)threadIdx.x + 1) * per);
+        int cnt = 0, dsum = 0, dmax = 0;
+        for (int v = beg; v < end; v++)
+            if (live(v)) { cnt++; dsum += d(v); dmax = max(dmax, d(v)); }
+        int lnp, lm2;
+        const int loff = block_excl_scan(cnt, sh.red, &lnp);
+        const int leoff = block_excl_scan(dsum, sh.red, &lm2);
+        const int ldm = block_max(dmax, sh.red);
+        int coff, np, ceoff, m2p;
+        exchange_prefix(lnp, lm2, coff, np, ceoff, m2p);
+        exchange(0, 0, 0, ldm);
+        const int dm = (int)sh.tot[3];
+        int *nid = Q.aux;
+        int id = coff + loff, eo = ceoff + leoff;
+        for (int v = beg; v < end; v++) {
+            if (live(v)) {
+                nid[v] = id;
+                Q.orig[id] = v;
+                Q.rp2[id] = eo;
+                id++;
+                eo += d(v);
+            } else {
+                nid[v] = -1;
+            }
+        }
+        if (rank == 0 && threadIdx.x == 0) {
+            Q.rp2[np] = m2p;
+            Q.np = np;
+            Q.m2p = m2p;
+            Q.maxdeg = dm;
+        }
+        cl.sync();
+        for (int i = coff + threadIdx.x; i < coff + lnp; i += T) {
+            const int v = Q.orig[i];
+            int o = Q.rp2[i];
+            for (int e = __ldg(rp + v); e < __ldg(rp + v + 1); e++) {
+                const int nx = ((volatile int *)nid)[__ldg(col + e)];
+                if (nx >= 0) Q.col2[o++] = nx;
+            }
+        }
+        cl.sync();
+        for (int i = threadIdx.x; i < vcnt; i += T) nid[vbeg + i] = 0;
+        cl.sync();
+    }
+
+    __device__ void publish()
+    {
+        for (int i = threadIdx.x; i < vcnt; i += blockDim.x) Q.st[vbeg + i] = forced(vbeg + i) ? 1 : 0;
+    }
+
+    __device__ void run()
+    {
+        if (rank == 0) {
+            prefetch_l2(rp, (size_t)(n + 1) * 4);
+            prefetch_l2(col, (size_t)Q.m2 * 4);
+        }
+        for (int i = threadIdx.x; i < vcnt; i += blockDim.x) {
+            const int v = vbeg + i;
+            degp(rank)[i] = (uint16_t)(__ldg(rp + v + 1) - __ldg(rp + v));
+            Q.aux[v] = 0;
+            Q.cover_flags[v] = 0;
+        }
+        if (rank == 0 && threadIdx.x == 0) {
+            Q.forced = 0;
+            Q.np = 0; Q.m2p = 0; Q.maxdeg = 0; Q.answered = 0; Q.greedy = -1;
+            Q.improved = 0; Q.result = -1; Q.yes = 0; Q.cover_len = 0;
+            Q.rounds = 0;
+            for (int i = 0; i < 4; i++) Q.root_cycles[i] = 0;
+        }
+        cl.sync();
+        long long t0 = clock64();
+        reduce_rounds(false, INT_MAX);
+        long long t1 = clock64();
+        if (rank == 0 && threadIdx.x == 0) Q.root_cycles[0] = t1 - t0;
+        if (live_edges2() == 0) {
+            publish();
+            for (int i = threadIdx.x; i < vcnt; i += blockDim.x) Q.cover_flags[vbeg + i] = forced(vbeg + i);
+            if (rank == 0 && threadIdx.x == 0) {
+                Q.answered = 1;
+                Q.bound = ftot;
+                if (Q.k < 0) { Q.result = ftot; Q.yes = 1; }
+                else { Q.yes = ftot <= Q.k; Q.result = Q.yes ? ftot : -1; }
+            }
+            return;
+        }
+        const int greedy_size = ftot + greedy();
+        t0 = clock64();
+        if (rank == 0 && threadIdx.x == 0) { Q.greedy = greedy_size; Q.root_cycles[1] = t0 - t1; }
+        if (Q.k >= 0 && greedy_size <= Q.k) {
+            publish();
+            if (rank == 0 && threadIdx.x == 0) {
+                Q.answered = 1; Q.bound = greedy_size; Q.yes = 1; Q.result = greedy_size;
+            }
+            return;
+        }
+        const int bound = Q.k >= 0 ? Q.k + 1 : greedy_size;
+        const bool feasible = reduce_rounds(true, bound);
+        t1 = clock64();
+        if (rank == 0 && threadIdx.x == 0) Q.root_cycles[2] = t1 - t0;
+        const long long e2 = live_edges2();
+        publish();
+        if (!feasible || ftot >= bound) {
+            if (rank == 0 && threadIdx.x == 0) {
+                Q.answered = 1; Q.bound = bound;
+                if (Q.k < 0) { Q.result = greedy_size; Q.yes = 1; }
+                else { Q.yes = 0; Q.result = -1; }
+            }
+            return;
+        }
+        if (e2 == 0) {
+            for (int i = threadIdx.x; i < vcnt; i += blockDim.x) Q.cover_flags[vbeg + i] = forced(vbeg + i);
+            if (rank == 0 && threadIdx.x == 0) {
+                Q.answered = 1; Q.bound = bound; Q.result = ftot; Q.yes = 1;
+            }
+            return;
+        }
+        induce();
+        if (rank == 0 && threadIdx.x == 0) { Q.bound = bound; Q.root_cycles[3] = clock64() - t1; }
+    }
+};
+
+__global__ void __launch_bounds__(kRootThreads, 1) root_cluster_kernel(QueryDesc *qs, int cs)
+{
+    extern __shared__ __align__(16) char root_smem[];
+    __shared__ ClusterShared sh;
+    QueryDesc &Q = qs[0];
+    if (Q.status != VC_OK) return;   // uniform across the cluster
+    ClusterRoot r(Q, sh, root_smem, cs);
+    cgx::this_cluster().sync();      // remote addresses and zeroed bitmaps everywhere
+    r.run();
+    cgx::this_cluster().sync();      // nobody leaves while others may touch its shared memory
+}
+
 // ------------------------------------------------------------ final answer
 
 // Assemble each query's cover in original ids: the root-forced vertices plus
@@ -721,13 +1374,76 @@ cudaError_t validate_run(int n, int m2, const int *rp, const int *col, int *d_er
 
 size_t root_smem_bytes(int max_n) { return SmemStore::smem_bytes(max_n); }
 
+// log2 of the vertices per CTA for the cluster kernel, or -1 when one block
+// per query is used
+int root_cluster_shift(int nq, int max_n, int max_deg)
+{
+    if (nq != 1 || max_n < kClusterMinN || max_deg > 65535) return -1;
+    int cs = 10;
+    while (((long long)kClusterMax << cs) < max_n) cs++;
+    if (cluster_smem_bytes(1 << cs) > kRootSmemMax || (1 << cs) > 4 * 32 * kRootThreads) return -1;
+    return cs;
+}
+
 cudaError_t root_run(QueryDesc *d_q, int nq, int max_n, int max_deg, cudaStream_t s)
 {
     if (nq <= 0) return cudaSuccess;
+    int cs = root_cluster_shift(nq, max_n, max_deg);
+    if (cs >= 0) {
+        cudaError_t e = cudaFuncSetAttribute(root_cluster_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        if (e != cudaSuccess) return e;
+        e = cudaFuncSetAttribute(root_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)kRootSmemMax);
+        if (e != cudaSuccess) return e;
+        int C = (int)((max_n + (1 << cs) - 1) >> cs);
+        // a cluster wider than 8 is not guaranteed: shrink until one fits
+        for (;;) {
+            cudaLaunchConfig_t probe = {};
+            probe.gridDim = dim3(C, 1, 1);
+            probe.blockDim = dim3(kRootThreads, 1, 1);
+            probe.dynamicSmemBytes = cluster_smem_bytes(1 << cs);
+            cudaLaunchAttribute pa[1];
+            pa[0].id = cudaLaunchAttributeClusterDimension;
+            pa[0].val.clusterDim.x = C;
+            pa[0].val.clusterDim.y = 1;
+            pa[0].val.clusterDim.z = 1;
+            probe.attrs = pa;
+            probe.numAttrs = 1;
+            int clusters = 0;
+            if (cudaOccupancyMaxActiveClusters(&clusters, root_cluster_kernel, &probe) == cudaSuccess && clusters > 0)
+                break;
+            cudaGetLastError();
+            if (C <= 1 || cluster_smem_bytes(2 << cs) > kRootSmemMax || (2 << cs) > 4 * 32 * kRootThreads) {
+                cs = -1;
+                break;
+            }
+            cs++;
+            C = (int)((max_n + (1 << cs) - 1) >> cs);
+        }
+    }
+    if (cs >= 0) {
+        const int C = (int)((max_n + (1 << cs) - 1) >> cs);
+        const size_t smem = cluster_smem_bytes(1 << cs);
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(C, 1, 1);
+        cfg.blockDim = dim3(kRootThreads, 1, 1);
+        cfg.dynamicSmemBytes = smem;
+        cfg.stream = s;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = C;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        return cudaLaunchKernelEx(&cfg, root_cluster_kernel, d_q, cs);
+    }
     const size_t smem = SmemStore::smem_bytes(max_n);
     if (max_deg <= 65535 && smem <= kRootSmemMax) {
+        // the attribute is a ceiling shared by every launch of the kernel:
+        // always set the maximum, never a smaller per-launch size
         cudaError_t e = cudaFuncSetAttribute(root_kernel<SmemStore>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
+                                             (int)kRootSmemMax);
         if (e != cudaSuccess) return e;
         root_kernel<SmemStore><<<nq, kRootThreads, smem, s>>>(d_q);
     } else {

@@ -114,6 +114,18 @@ def test_component_heavy_small(vc, copies, copy_n, p, chain):
         assert st["component_branches"] + st["trivial_components"] > 0
 
 
+def test_large_graph_with_core(vc):
+    # n >= 8192: the root phase runs on a thread-block cluster; the core left
+    # after the unbounded rules exercises the greedy bound, the bounded rules
+    # and the induced-subgraph build
+    parts = [gg.gnm(40, 90, s) for s in range(300)]
+    g = gg.disjoint_union(parts)
+    want = sum(oracle.mvc(p.n, p.row_ptr, p.col)[0] for p in parts)
+    size, st = gpu_min(vc, g)
+    assert size == want
+    assert st["n_induced"] > 0
+
+
 def test_chung_lu_50k(vc):
     g = gg.chung_lu(50_000, 2.5, 6.0, 2000.0, 0)
     want = oracle.mvc(g.n, g.row_ptr, g.col)[0]

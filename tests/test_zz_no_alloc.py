@@ -67,6 +67,7 @@ CASES = [
     ("hub_components", lambda: gg.component_heavy(1, copies=8, copy_n=24, p=0.2, chain=3)),
     ("forest", lambda: gg.random_forest(3000, 4, 2)),
     ("chung_lu_50k", lambda: gg.chung_lu(50_000, 2.5, 6.0, 2000.0, 1000)),
+    ("many_cores_12k", lambda: gg.disjoint_union([gg.gnm(40, 90, s) for s in range(300)])),
 ]
 
 
