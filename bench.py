@@ -164,6 +164,87 @@ def root_algorithmic_bytes(g, st) -> int:
     return csr + outs
 
 
+def extra_workloads(vc, torch, stream, peak):
+    """Context numbers beside the headline: plain vs batched launches of small
+    graphs, the search kernel on a component-heavy graph, and a mixed batch
+    under a per-query node budget.  Each part runs for a few seconds."""
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+
+    def timed(fn):
+        ev0.record(stream)
+        r = fn()
+        ev1.record(stream)
+        ev1.synchronize()
+        return r, ev0.elapsed_time(ev1)
+
+    out = {}
+    # G(n=80, m=200): one launch per graph vs one batched launch
+    gs = [gg.gnm(80, 200, s) for s in range(256)]
+    dgs = [vc.Graph.from_csr(g.row_ptr, g.col, stream=stream) for g in gs]
+    for d in dgs[:8]:
+        vc.solve_min(d)
+    lat, nodes = [], 0
+    for d in dgs:
+        (size, _, st), ms = timed(lambda: vc.solve_min(d))
+        lat.append(ms)
+        nodes += st["nodes"]
+    vc.solve_batch(dgs[:16])
+    (sizes, _, status, _, bst), bms = timed(lambda: vc.solve_batch(dgs))
+    out["gnm_80_200"] = {
+        "graphs": len(dgs), "plain_graphs_per_s": round(len(dgs) / (sum(lat) / 1e3), 1),
+        "plain_p50_ms": round(float(np.percentile(lat, 50)), 4), "plain_p99_ms": round(float(np.percentile(lat, 99)), 4),
+        "plain_nodes_per_s": round(nodes / (sum(lat) / 1e3), 1),
+        "batched_graphs_per_s": round(len(dgs) / (bms / 1e3), 1), "batched_ms": round(bms, 3),
+        "batched_nodes_per_s": round(bst["nodes"] / (bms / 1e3), 1)}
+    for d in dgs:
+        d.close()
+
+    # component-heavy: 8 copies of G(48, 0.12) on a 2-vertex chain
+    g = gg.component_heavy(1, copies=8, copy_n=48, p=0.12, chain=2)
+    d = vc.Graph.from_csr(g.row_ptr, g.col, stream=stream)
+    vc.solve_min(d)
+    (size, _, st), ms = timed(lambda: vc.solve_min(d))
+    d.close()
+    gbs = st["search_bytes"] / (st["ms_search"] / 1e3) / 1e9 if st["ms_search"] > 0 else 0.0
+    out["component_heavy_8x48"] = {
+        "n": g.n, "answer": size, "nodes": st["nodes"], "ms_total": round(ms, 3),
+        "ms_search_kernel": round(st["ms_search"], 3),
+        "nodes_per_s": round(st["nodes"] / (st["ms_search"] / 1e3), 1),
+        "component_branches": st["component_branches"], "workers": st["workers"], "team": st["team"],
+        "search_roofline": {"bound": "hbm", "kernel": "search_kernel", "achieved": round(gbs, 3),
+                            "peak": peak, "unit": "GB/s", "frac": round(gbs / peak, 6),
+                            "algorithmic_bytes": st["search_bytes"],
+                            "bytes_per_node": round(st["search_bytes"] / max(1, st["nodes"]), 1)}}
+
+    # mixed batch (n in [40, 400]; half G(n,p), half Chung-Lu), per-query budget
+    mix = gg.batch_pvc_mix(512, 7, n_lo=40, n_hi=400)
+    dms = [vc.Graph.from_csr(h.row_ptr, h.col, stream=stream) for h in mix]
+    budget = 500_000
+    # first pass: which queries finish within the budget (the rest are dropped)
+    _, _, status, _, _ = vc.solve_batch(dms, node_budget=budget, raise_on_error=False)
+    solved = [i for i in range(len(dms)) if status[i] == 0]
+    keep = [dms[i] for i in solved]
+    vc.solve_batch(keep[:32], raise_on_error=False)
+    (sizes, _, st2, _, bst), bms = timed(lambda: vc.solve_batch(keep, node_budget=budget, raise_on_error=False))
+    plain = []
+    for i in solved:
+        try:
+            (_, _, _), ms = timed(lambda: vc.solve_min(dms[i], node_budget=budget))
+        except vc.VcError:
+            continue   # the search order differs between launches; rarely over budget alone
+        plain.append(ms)
+    out["mixed_batch_512"] = {
+        "queries": len(dms), "solved": len(solved), "dropped_over_budget": int((status == vc.VC_EBUDGET).sum()),
+        "node_budget_per_query": budget, "batched_ms": round(bms, 3),
+        "batched_graphs_per_s": round(int((st2 == 0).sum()) / (bms / 1e3), 1),
+        "plain_graphs_per_s": round(len(plain) / (sum(plain) / 1e3), 1) if plain else None,
+        "batched_nodes_per_s": round(bst["nodes"] / (bms / 1e3), 1)}
+    for d in dms:
+        d.close()
+    return out
+
+
 def ours_main(args, rank, world, local_rank):
     import torch
     import paper_2512_18334_gb300 as vc
@@ -263,6 +344,10 @@ def ours_main(args, rank, world, local_rank):
         cpu = {"value": round(v, 6), "unit": "graphs/s", "cores": 1, "kind": "oracle",
                "sample": "2 solves of the same workload graph (seed 1000), single thread"}
 
+    also = None
+    if rank == 0 and not args.no_extra:
+        also = extra_workloads(vc, torch, stream, peak)
+
     if rank == 0:
         line = {
             "metric": METRIC, "value": round(value, 3), "unit": "graphs/s", "n_gpus": world,
@@ -283,6 +368,7 @@ def ours_main(args, rank, world, local_rank):
             "cpu_baseline": cpu,
             "clocks": clk,
             "gpu_launches": launches,
+            "also": also,
         }
         print(json.dumps(line), flush=True)
     dg.close()
@@ -297,6 +383,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extra", action="store_true", help="skip the context workloads")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     rank, world, local_rank = dist_env()

@@ -61,7 +61,8 @@ typedef struct vc_options {
                                  root is shared, workers keep what they create      */
     int32_t idle_timeout_ms;  /* abort with VC_ETIMEOUT after this long without
                                  any worker making progress; 0 = 60000              */
-    int64_t node_budget;      /* 0 = unlimited; else stop with VC_EBUDGET           */
+    int64_t node_budget;      /* 0 = unlimited; else a query that needs more search-tree
+                                 nodes stops with VC_EBUDGET (per query in a batch) */
 } vc_options;
 
 /* What a solve did.  All counters are totals over the launch. */
@@ -90,6 +91,8 @@ typedef struct vc_stats {
     double ms_total;            /* whole call, host wall clock                      */
     int64_t root_cycles[4];     /* SM cycles in the root phase: rules without a
                                    bound, greedy bound, rules with the bound, induce */
+    int64_t search_bytes;       /* algorithmic bytes the search moved: node slots
+                                   read and written, CSR rows read, witness bitmaps */
 } vc_stats;
 
 /* Fill *opt with the defaults. */

@@ -67,6 +67,7 @@ class Stats(ctypes.Structure):
         ("ms_search", ctypes.c_double),
         ("ms_total", ctypes.c_double),
         ("root_cycles", ctypes.c_int64 * 4),
+        ("search_bytes", ctypes.c_int64),
     ]
 
     def to_dict(self) -> dict:

@@ -347,6 +347,7 @@ int solve_queries(vc_graph *g0, const std::vector<QueryRef> &qs, const vc_option
         QueryOut &o = out[i];
         const QueryDesc &Q = hq[i];
         o.status = Q.status != VC_OK ? Q.status : (root_slot[i] >= 0 && kstatus ? kstatus : VC_OK);
+        if (o.status != VC_OK) { o.size = -1; o.yes = 0; }
         o.size = Q.result;
         o.yes = Q.yes;
         o.cover_len = (o.status == VC_OK) ? Q.cover_len : 0;
@@ -355,6 +356,7 @@ int solve_queries(vc_graph *g0, const std::vector<QueryRef> &qs, const vc_option
     if (stats) {
         memset(stats, 0, sizeof(*stats));
         stats->nodes = (int64_t)ctlw(hctl_local, kNodes);
+        stats->search_bytes = (int64_t)ctlw(hctl_local, kBytes);
         stats->component_branches = (int64_t)ctlw(hctl_local, kCompBranches);
         stats->leaves = (int64_t)ctlw(hctl_local, kLeaves);
         stats->pruned = (int64_t)ctlw(hctl_local, kPruned);

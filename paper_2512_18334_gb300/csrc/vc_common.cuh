@@ -74,6 +74,8 @@ struct QueryDesc {
     int rounds;          // root-phase rule rounds (diagnostics)
     int pad2;
     long long root_cycles[4];  // clock64 cycles: phase 1, greedy, phase 2, induce
+    long long nodes;     // search-tree nodes spent on this query
+    long long budget;    // node budget of this query (0: none)
     int *cover_list;     // ascending original ids (device, >= n)
 };
 
@@ -166,6 +168,7 @@ enum Ctl : int {
     kErrWhere = 15,   // where the first error was raised (diagnostics)
     kRegBump = 16,    // next never-used registry entry
     kHist = 17,       // kHistBins entries
+    kBytes = 33,      // algorithmic bytes moved by the search (slots, CSR rows, bitmaps)
     kCtlEntries = 34
 };
 constexpr int kCtlStride = 16;

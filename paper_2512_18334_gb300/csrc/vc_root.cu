@@ -46,25 +46,32 @@ __global__ void validate_rowptr_kernel(int n, int m2, const int *rp, int *err)
     }
 }
 
-__global__ void validate_col_kernel(int n, const int *rp, const int *col, int *err)
+// One entry per thread (edge-parallel, so a hub's long row is spread over
+// many threads): entry e of row v must be in range, not v itself, larger
+// than the entry before it in the row, and (when above the diagonal) mirrored
+// in row col[e].  Needs valid row pointers (checked first).
+__global__ void validate_col_kernel(int n, int m2, const int *rp, const int *col, int *err)
 {
     if (*(volatile int *)err) return;   // row pointers are bad: rows cannot be read safely
     int up = 0;
-    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
-        int a = rp[v], b = rp[v + 1];
-        int prev = -1;
-        bool bad = false;
-        for (int e = a; e < b && !bad; e++) {
-            int u = col[e];
-            if (u < 0 || u >= n || u == v || u <= prev) { bad = true; break; }
-            prev = u;
-            if (u > v) {
-                up++;
-                if (!bsearch_row(col + rp[u], rp[u + 1] - rp[u], v)) bad = true;
-            }
+    bool bad = false;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < m2; e += gridDim.x * blockDim.x) {
+        // the row holding e: the largest v with rp[v] <= e
+        int lo = 0, hi = n - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (__ldg(rp + mid) <= e) lo = mid; else hi = mid - 1;
         }
-        if (bad) atomicOr(err, 1);
+        const int v = lo;
+        const int u = __ldg(col + e);
+        if (u < 0 || u >= n || u == v) { bad = true; continue; }
+        if (e > __ldg(rp + v) && __ldg(col + e - 1) >= u) { bad = true; continue; }
+        if (u > v) {
+            up++;
+            if (!bsearch_row(col + __ldg(rp + u), __ldg(rp + u + 1) - __ldg(rp + u), v)) bad = true;
+        }
     }
+    if (bad) atomicOr(err, 1);
     up = __reduce_add_sync(kFull, up);
     if ((threadIdx.x & 31) == 0 && up) atomicAdd(err + 1, up);
 }
@@ -1364,7 +1371,8 @@ cudaError_t validate_run(int n, int m2, const int *rp, const int *col, int *d_er
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     if (n > 0) {
-        validate_col_kernel<<<blocks > 0 ? blocks : 1, threads, 0, s>>>(n, rp, col, d_err);
+        const int eblocks = std::max(1, std::min(4096, (m2 + threads - 1) / threads));
+        validate_col_kernel<<<eblocks, threads, 0, s>>>(n, m2, rp, col, d_err);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         max_degree_kernel<<<blocks > 0 ? blocks : 1, threads, 0, s>>>(n, rp, d_err);
         e = cudaGetLastError();
@@ -1596,7 +1604,8 @@ extern "C" int vc_root_reduce_static(int32_t n, int32_t m2, const int32_t *d_row
         const int threads = 256;
         const int blocks = std::min(4096, (n + 1 + threads - 1) / threads);
         validate_rowptr_kernel<<<blocks, threads, 0, s>>>(n, m2, d_row_ptr, err);
-        validate_col_kernel<<<blocks, threads, 0, s>>>(n, d_row_ptr, d_col, err);
+        const int eblocks = std::max(1, std::min(4096, (m2 + threads - 1) / threads));
+        validate_col_kernel<<<eblocks, threads, 0, s>>>(n, m2, d_row_ptr, d_col, err);
         max_degree_kernel<<<blocks, threads, 0, s>>>(n, d_row_ptr, err);
         if (cudaGetLastError() != cudaSuccess) return VC_ECUDA;
     }

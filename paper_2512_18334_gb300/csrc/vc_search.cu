@@ -172,6 +172,9 @@ struct Worker {
     // private registry free list (leader only)
     int lf_head, lf_count;
     long long nodes_local, last_flush;
+    long long qnodes;        // nodes of query qcur not yet added to its counter
+    int qcur;
+    long long bytes_local;   // this thread's share of the algorithmic bytes
     int max_top;
 
     __device__ Worker(const SearchParams &p, Team<WT> t, int w, char *smem) : P(p), tm(t), wid(w)
@@ -187,6 +190,9 @@ struct Worker {
         stack = P.stack_slots + (size_t)wid * P.stack_depth * P.slot_bytes;
         top = 0;
         nodes_local = 0;
+        bytes_local = 0;
+        qnodes = 0;
+        qcur = -1;
         last_flush = 0;
         max_top = 0;
         cntbuf = 0;
@@ -260,6 +266,7 @@ struct Worker {
         for (int i = tm.rank; i < c; i += tm.size()) {
             const int u = lab[i];
             cov_set(u);
+            bytes_local += 8 + 4ll * (rp[u + 1] - rp[u]);
             for (int e = rp[u]; e < rp[u + 1]; e++) {
                 const int x = __ldg(col + e);
                 if (dg(x) > 0 && !marked(x)) dec(x);
@@ -318,19 +325,23 @@ struct Worker {
                 nhi = max(nhi, v);
                 if (dv == 1) {
                     int u = -1;
-                    for (int e = rp[v]; e < rp[v + 1]; e++) {
+                    int e = rp[v];
+                    for (; e < rp[v + 1]; e++) {
                         int x = __ldg(col + e);
                         if (dg(x) > 0) { u = x; break; }
                     }
+                    bytes_local += 8 + 4ll * (e - rp[v] + 1);
                     if (u >= 0 && !(dg(u) == 1 && u < v)) mark_vertex(u);
                 } else if (dv == 2) {
                     int u = -1, w = -1;
-                    for (int e = rp[v]; e < rp[v + 1]; e++) {
+                    int e = rp[v];
+                    for (; e < rp[v + 1]; e++) {
                         int x = __ldg(col + e);
                         if (dg(x) > 0) {
                             if (u < 0) u = x; else { w = x; break; }
                         }
                     }
+                    bytes_local += 16 + 4ll * (e - rp[v] + 1) + 4ll * (32 - __clz(max(1, rp[u + 1] - rp[u])));
                     if (w >= 0 && adjacent(u, w)) {
                         if (!((dg(u) == 2 && u < v) || (dg(w) == 2 && w < v))) {
                             mark_vertex(u);
@@ -384,6 +395,9 @@ struct Worker {
             h->depth = depth + 1;
         }
         uint4 *dst = (uint4 *)(slot + sizeof(NodeHdr));
+        if (tm.leader())
+            bytes_local += (long long)sizeof(NodeHdr) + 16ll * nvec +
+                           (kind == 0 ? 4ll * ((chi >> 5) - (clo >> 5) + 1) : 0);
         if (kind == 0) {
             const uint4 *src = (const uint4 *)(d + (slo - wlo));
             for (int i = tm.rank; i < nvec; i += tm.size()) dst[i] = src[i];
@@ -428,6 +442,7 @@ struct Worker {
         const int w0 = clo >> 5, nw = (chi >> 5) - w0 + 1;
         const uint32_t *csrc = (const uint32_t *)(slot + sizeof(NodeHdr) + deg_region_bytes<T>(P.ncap));
         for (int i = tm.rank; i < nw; i += tm.size()) cov[i] = cov_empty ? 0u : __ldcg(csrc + i);
+        if (tm.leader()) bytes_local += (long long)sizeof(NodeHdr) + 16ll * nvec + (cov_empty ? 0 : 4ll * nw);
         const QueryDesc &Q = P.queries[q];
         rp = Q.rp2;
         col = Q.col2;
@@ -438,6 +453,7 @@ struct Worker {
             for (int e = rp[op] + tm.rank; e < rp[op + 1]; e += tm.size()) {
                 const int x = __ldg(col + e);
                 if (dg(x) > 0) mark_vertex(x);
+                bytes_local += 4;
             }
             const int c = take_count();
             apply_marks(c);
@@ -626,6 +642,7 @@ struct Worker {
         uint32_t *w = reg_words(P, comp);
         const int nw = (chi >> 5) - (clo >> 5) + 1;
         for (int i = tm.rank; i < nw; i += tm.size()) w[i] = cov[i];
+        if (tm.leader()) bytes_local += 4ll * nw + sizeof(RegEntry);
         __threadfence();
         tm.sync();
         if (tm.leader()) {
@@ -669,6 +686,7 @@ struct Worker {
                 const int cnw = vld(C.nw);
                 uint32_t *dst = reg_words(P, par) + (vld(C.wlo) - vld(Pe.wlo));
                 for (int i = tm.rank; i < cnw; i += tm.size()) atomicOr(&dst[i], __ldcg(src + i));
+                if (tm.leader()) bytes_local += 8ll * cnw;
                 __threadfence();
             }
             tm.sync();
@@ -698,6 +716,7 @@ struct Worker {
                 const int pnw = vld(Pe.nw);
                 uint32_t *dst = reg_words(P, anc) + (vld(Pe.wlo) - vld(A.wlo));
                 for (int i = tm.rank; i < pnw; i += tm.size()) dst[i] = __ldcg(src + i);
+                if (tm.leader()) bytes_local += 8ll * pnw;
                 __threadfence();
                 tm.sync();
                 if (tm.leader()) {
@@ -753,6 +772,7 @@ struct Worker {
         for (int i = tm.rank; i < W; i += tm.size()) {
             const int v = lo + i;
             if (d[v - wlo] == 0) continue;
+            bytes_local += 8 + 4ll * (rp[v + 1] - rp[v]);
             for (int e = rp[v]; e < rp[v + 1]; e++) {
                 const int u = __ldg(col + e);
                 if (u > v && u <= hi && d[u - wlo] > 0) uf_unite(i, u - lo);
@@ -1011,6 +1031,7 @@ struct Worker {
     {
         for (;;) {
             nodes_local++;
+            qnodes++;
             int B = 0;
             if (tm.leader()) B = aborted(P.ctl) ? INT_MIN : ld_relaxed(&P.reg[comp].val);
             B = tm.bcast(B);
@@ -1065,9 +1086,28 @@ struct Worker {
 
     // ------------------------------------------------------------ main loop
 
+    // Add this worker's nodes of the current query to its counter; a query
+    // over its budget stops with VC_EBUDGET (the others continue).
+    __device__ void flush_query_nodes()
+    {
+        if (tm.leader() && qnodes > 0 && qcur >= 0) {
+            QueryDesc &Q = P.queries[qcur];
+            const long long tot = (long long)atomicAdd((unsigned long long *)&Q.nodes, (unsigned long long)qnodes) + qnodes;
+            if (Q.budget > 0 && tot > Q.budget) {
+                atomicCAS(&Q.status, VC_OK, VC_EBUDGET);
+                query_done(P, qcur);
+            }
+        }
+        qnodes = 0;
+    }
+
     __device__ void flush_counters()
     {
+        flush_query_nodes();
+        const long long b = tm.lsum(bytes_local);
+        bytes_local = 0;
         if (tm.leader()) {
+            atomicAdd(&ctlw(P.ctl, kBytes), (unsigned long long)b);
             atomicAdd(&ctlw(P.ctl, kNodes), (unsigned long long)(nodes_local - last_flush));
             atomicAdd(&ctlw(P.ctl, kProgress), 1ull);
             atomicMax(&ctlw(P.ctl, kMaxStack), (unsigned long long)max_top);
@@ -1081,7 +1121,7 @@ struct Worker {
         int backoff = 32;
         // counters are flushed every 64 nodes, more often under a small node budget
         long long flush_every = 64;
-        if (P.node_budget > 0) flush_every = max(1ll, min(64ll, P.node_budget / (16ll * P.workers)));
+        if (P.node_budget > 0) flush_every = max(1ll, min(64ll, P.node_budget / 64));
         for (;;) {
             int ab = tm.leader() ? (int)aborted(P.ctl) : 0;
             if (tm.bcast(ab)) break;
@@ -1096,16 +1136,14 @@ struct Worker {
             if (got) {
                 backoff = 32;
                 idle_since = 0;
+                if (q != qcur) {
+                    flush_query_nodes();
+                    qcur = q;
+                }
                 int qd = tm.leader() ? (int)query_is_done(P, q) : 0;
                 if (tm.bcast(qd)) { tm.sync(); continue; }   // PVC answered meanwhile
                 process();
-                if (nodes_local - last_flush >= flush_every) {
-                    flush_counters();
-                    if (P.node_budget > 0 &&
-                        (long long)*(volatile unsigned long long *)&ctlw(P.ctl, kNodes) > P.node_budget) {
-                        if (tm.leader()) set_error(P.ctl, VC_EBUDGET, 10);
-                    }
-                }
+                if (nodes_local - last_flush >= flush_every) flush_counters();
                 tm.sync();
                 continue;
             }
@@ -1191,6 +1229,8 @@ __global__ void search_roots_kernel(SearchParams P, const int *root_slot)
         R.next = -1;
         Q.root_entry = qi;
         Q.done = 0;
+        Q.nodes = 0;
+        Q.budget = P.node_budget;
     }
     char *s = P.wl_slots + (size_t)slot * P.slot_bytes;
     NodeHdr *h = (NodeHdr *)s;
