@@ -36,13 +36,44 @@ import numpy as np  # noqa: E402
 import graphgen as gg  # noqa: E402
 
 METRIC = "graphs/sec & search-tree nodes/sec at exact MVC; p99 latency; batched vs plain"
-WORKLOAD = dict(workload="chung_lu_50k", n=50_000, gamma=2.5, avg_deg=6.0, max_deg=2000.0)
+WORKLOADS = {
+    # the headline: plain exact MVC of one Chung-Lu power-law graph
+    "chung_lu_50k": dict(workload="chung_lu_50k", n=50_000, gamma=2.5, avg_deg=6.0, max_deg=2000.0),
+    # search-dominated: 8 copies of G(48, 0.12) hung on a 2-vertex chain
+    "component_heavy_8x48": dict(workload="component_heavy_8x48", copies=8, copy_n=48, p=0.12, chain=2),
+}
+WORKLOAD = WORKLOADS["chung_lu_50k"]
 L2_FLUSH_BYTES = 256 << 20
 
 
 def make_graph(rank: int):
     w = WORKLOAD
-    return gg.chung_lu(w["n"], w["gamma"], w["avg_deg"], w["max_deg"], 1000 + rank)
+    if w["workload"] == "chung_lu_50k":
+        return gg.chung_lu(w["n"], w["gamma"], w["avg_deg"], w["max_deg"], 1000 + rank)
+    return gg.component_heavy(1 + rank, copies=w["copies"], copy_n=w["copy_n"], p=w["p"], chain=w["chain"])
+
+
+def solve_options():
+    """Search capacities: the defaults, or modest fixed ones for the
+    search-dominated workload (keeps its device footprint small)."""
+    if WORKLOAD["workload"] == "component_heavy_8x48":
+        return dict(stack_depth=128, registry_capacity=1 << 18)
+    return {}
+
+
+def kernel_traffic(kernel: str):
+    """DRAM bytes per launch from the committed ncu summary, when it was taken
+    on the current source of that kernel (else None)."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        rec = json.load(open(path))[WORKLOAD["workload"]]
+    except Exception:
+        return None
+    if rec.get("kernel") != kernel:
+        return None
+    src = open(os.path.join(ROOT, rec["source"]), "rb").read()
+    return rec["traffic"] if hashlib.sha256(src).hexdigest() == rec["sha256"] else None
 
 
 def dist_env():
@@ -139,13 +170,13 @@ def reference_main(args, rank, world):
     if rank != 0:
         return
     value, ms, size = cpu_oracle_run(args.steps, args.warmup)
-    sample = (f"full {WORKLOAD['workload']} graph (seed 1000), {args.steps} timed solves after "
+    sample = (f"full {WORKLOAD['workload']} graph, {args.steps} timed solves after "
               f"{args.warmup} warm-up, single thread")
     line = {
         "impl": "reference", "metric": METRIC, "value": round(value, 6), "unit": "graphs/s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 3),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
-        "data": "synthetic", "config": dict(WORKLOAD, seed=1000, answer=size),
+        "data": "synthetic", "config": dict(WORKLOAD, answer=size),
         "cpu_baseline": {"value": round(value, 6), "unit": "graphs/s", "cores": 1, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": round(value, 6), "unit": "graphs/s", "h2d_bytes_per_step": 0,
@@ -189,6 +220,7 @@ def extra_workloads(vc, torch, stream, peak):
         (size, _, st), ms = timed(lambda: vc.solve_min(d))
         lat.append(ms)
         nodes += st["nodes"]
+        search_bytes += st["search_bytes"]
     vc.solve_batch(dgs[:16])
     (sizes, _, status, _, bst), bms = timed(lambda: vc.solve_batch(dgs))
     out["gnm_80_200"] = {
@@ -268,7 +300,7 @@ def ours_main(args, rank, world, local_rank):
 
     # ---- warm-up (also checks the answer against the library's own verify path)
     for _ in range(max(args.warmup, 3)):
-        size, cover, st = vc.solve_min(dg)
+        size, cover, st = vc.solve_min(dg, **solve_options())
     flags = np.zeros(g.n, np.uint8)
     flags[cover] = 1
     src = np.repeat(np.arange(g.n), np.diff(g.row_ptr))
@@ -280,11 +312,11 @@ def ours_main(args, rank, world, local_rank):
     barrier()
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
-    step_ms, root_ms, search_ms, nodes, launches = [], [], [], 0, 0
+    step_ms, root_ms, search_ms, nodes, launches, search_bytes = [], [], [], 0, 0, 0
     for _ in range(args.steps):
         flush.fill_(0)
         ev0.record(stream)
-        size_k, _, st = vc.solve_min(dg, want_cover=True)
+        size_k, _, st = vc.solve_min(dg, want_cover=True, **solve_options())
         ev1.record(stream)
         ev1.synchronize()
         step_ms.append(ev0.elapsed_time(ev1))
@@ -312,7 +344,7 @@ def ours_main(args, rank, world, local_rank):
         flush.fill_(0)
         ev0.record(stream)
         h = vc.Graph.from_csr(rp_h.numpy(), col_h.numpy(), stream=stream)
-        s2, cov2, _ = vc.solve_min(h)
+        s2, cov2, _ = vc.solve_min(h, **solve_options())
         h.close()
         ev1.record(stream)
         ev1.synchronize()
@@ -326,23 +358,33 @@ def ours_main(args, rank, world, local_rank):
         e2e_total = float(t.item())
     e2e_value = world * args.steps / (e2e_total / 1e3)
 
-    # ---- roofline of the dominant kernel (root reduction), timed by the
-    # library with CUDA events on the launching stream
+    # ---- roofline of the dominant kernel, timed by the library with CUDA
+    # events on the launching stream
     peak, peak_kind = load_peaks()
     mean_root_ms = statistics.mean(root_ms)
-    achieved = root_algorithmic_bytes(g, st) / (mean_root_ms / 1e3) / 1e9
-    roofline = {"bound": "hbm", "kernel": "root_kernel", "achieved": round(achieved, 3),
+    mean_search_ms = statistics.mean(search_ms)
+    if mean_search_ms > mean_root_ms:
+        kname = "search_kernel"
+        algo = search_bytes / args.steps
+        achieved = algo / (mean_search_ms / 1e3) / 1e9
+        ms_launch = mean_search_ms
+    else:
+        kname = "root_cluster_kernel" if g.n >= 8192 else "root_kernel"
+        algo = root_algorithmic_bytes(g, st)
+        achieved = algo / (mean_root_ms / 1e3) / 1e9
+        ms_launch = mean_root_ms
+    roofline = {"bound": "hbm", "kernel": kname, "achieved": round(achieved, 3),
                 "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
-                "frac": round(achieved / peak, 6), "traffic": None,
-                "algorithmic_bytes": root_algorithmic_bytes(g, st), "ms_per_launch": round(mean_root_ms, 4)}
+                "frac": round(achieved / peak, 6), "traffic": kernel_traffic(kname),
+                "algorithmic_bytes": int(algo), "ms_per_launch": round(ms_launch, 4)}
 
     # ---- CPU baseline: the oracle on a bounded sample (rank 0, N = 1 only)
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and WORKLOAD["workload"] == "chung_lu_50k":
         v, ms, osize = cpu_oracle_run(steps=2, warmup=0)
         assert osize == size, (osize, size)
         cpu = {"value": round(v, 6), "unit": "graphs/s", "cores": 1, "kind": "oracle",
-               "sample": "2 solves of the same workload graph (seed 1000), single thread"}
+               "sample": "2 solves of the same workload graph, single thread"}
 
     also = None
     if rank == 0 and not args.no_extra:
@@ -354,7 +396,8 @@ def ours_main(args, rank, world, local_rank):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(total_ms / args.steps, 4),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
             "data": "synthetic", "impl": "ours",
-            "config": dict(WORKLOAD, seed=1000 + rank, answer=size, n_induced=st["n_induced"],
+            "config": dict(WORKLOAD, seed=(1000 if WORKLOAD["workload"] == "chung_lu_50k" else 1) + rank,
+                           answer=size, n_induced=st["n_induced"],
                            forced=st["forced"], l2="256 MiB write before every timed step",
                            parallelism=f"replicas x{world}"),
             "p99_ms": round(p99, 4),
@@ -384,8 +427,11 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the context workloads")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="chung_lu_50k")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
+    global WORKLOAD
+    WORKLOAD = WORKLOADS[args.workload]
     rank, world, local_rank = dist_env()
     if args.impl == "reference":
         reference_main(args, rank, world)
