@@ -111,7 +111,12 @@ struct RegEntry {
     int32_t q;       // query id
     int32_t next;    // free-list link
     int32_t kind;    // 0 component, 1 parent
-    int32_t pad[6];
+    // parameterized queries (Section 3.5) keep every improvement flowing up:
+    int32_t cur;     // component: size of the cover its bitmap holds
+    int32_t sib;     // component: next child of the same parent (-1 ends)
+    int32_t first;   // parent: first child
+    int32_t tot;     // parent: |S_P| + sum of its children's cur
+    int32_t pad[2];
 };
 static_assert(sizeof(RegEntry) == 64, "registry entry must stay 64 bytes");
 

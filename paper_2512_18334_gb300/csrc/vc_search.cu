@@ -645,14 +645,92 @@ struct Worker {
         if (tm.leader()) bytes_local += 4ll * nw + sizeof(RegEntry);
         __threadfence();
         tm.sync();
+        int oldcur = 0;
         if (tm.leader()) {
             RegEntry &E = P.reg[comp];
+            oldcur = vld(E.cur);
             E.has_w = 1;
+            E.cur = S;
             atomicExch(&E.val, S);
             reg_unlock(P, comp);
             if (vld(E.link) < 0 && P.queries[q].k >= 0) query_done(P, q);   // PVC: a cover <= k exists
         }
+        oldcur = tm.bcast(oldcur);
+        if (pvc()) pvc_propagate(comp, oldcur, S);
+    }
+
+    __device__ __forceinline__ bool pvc() const { return P.queries[q].k >= 0; }
+
+    // Entry a's witness := the parent entry's own cover S_P (its bitmap) plus
+    // every child's current cover.  Caller holds a's lock; children are
+    // locked while read when they may still improve.
+    __device__ void assemble(int a, int par, bool lock_children)
+    {
+        const RegEntry &A = P.reg[a];
+        const RegEntry &Pe = P.reg[par];
+        const int aw = vld(A.wlo);
+        uint32_t *dst = reg_words(P, a);
+        const uint32_t *sp = reg_words(P, par);
+        const int pnw = vld(Pe.nw), pw = vld(Pe.wlo);
+        for (int i = tm.rank; i < pnw; i += tm.size()) dst[pw - aw + i] = __ldcg(sp + i);
+        __threadfence();
         tm.sync();
+        int ch = vld(Pe.first);
+        for (int guard = 0; ch >= 0 && guard < (1 << 20); guard++) {
+            int ok = 1;
+            if (lock_children && tm.leader()) ok = reg_lock(P, ch);
+            ok = tm.bcast(ok);
+            if (!ok) return;   // aborted
+            const RegEntry &C = P.reg[ch];
+            const int cw = vld(C.wlo), cnw = vld(C.nw);
+            const uint32_t *src = reg_words(P, ch);
+            for (int i = tm.rank; i < cnw; i += tm.size()) dst[cw - aw + i] |= __ldcg(src + i);
+            if (tm.leader()) bytes_local += 8ll * cnw;
+            __threadfence();
+            tm.sync();
+            if (lock_children && tm.leader()) reg_unlock(P, ch);
+            ch = vld(C.sib);
+        }
+    }
+
+    // Section 3.5: in a parameterized query every improvement of a component
+    // entry (its cover shrank from oldcur to newcur) is pushed up the chain
+    // at once, so the root can reach k before the components are finished.
+    __device__ void pvc_propagate(int c, int oldcur, int newcur)
+    {
+        for (int guard = 0; guard < (1 << 20); guard++) {
+            const int par = vld(P.reg[c].link);
+            if (par < 0 || newcur >= oldcur) return;
+            int t = 0, a = -1, go = 0;
+            if (tm.leader()) {
+                t = atomicAdd(&P.reg[par].tot, newcur - oldcur) + (newcur - oldcur);
+                a = vld(P.reg[par].link);
+                if (t < ld_relaxed(&P.reg[a].val) && reg_lock(P, a)) {
+                    if (t < vld(P.reg[a].val)) go = 1;
+                    else reg_unlock(P, a);
+                }
+                sc[8] = t; sc[9] = a; sc[10] = go;
+            }
+            tm.sync();
+            t = sc[8]; a = sc[9]; go = sc[10];
+            tm.sync();
+            if (!go) return;
+            assemble(a, par, true);
+            int olda = 0;
+            if (tm.leader()) {
+                RegEntry &A = P.reg[a];
+                olda = vld(A.cur);
+                A.has_w = 1;
+                A.cur = t;
+                atomicExch(&A.val, t);
+                reg_unlock(P, a);
+                if (vld(A.link) < 0) query_done(P, q);   // the query's root reached k
+            }
+            olda = tm.bcast(olda);
+            c = a;
+            oldcur = olda;
+            newcur = t;
+        }
     }
 
     // One node of context c completed (Section 3.3).  The last descendant of
@@ -681,6 +759,10 @@ struct Worker {
             const int bestc = vld(C.val);
             const int hw = vld(C.has_w);
             const RegEntry &Pe = P.reg[par];
+            if (pvc()) {
+                if (complete_pvc_child(c, par, bestc)) { c = vld(Pe.link); continue; }
+                return;
+            }
             if (hw) {
                 const uint32_t *src = reg_words(P, c);
                 const int cnw = vld(C.nw);
@@ -732,6 +814,61 @@ struct Worker {
             tm.sync();
             c = anc;
         }
+    }
+
+    // A child c of parent entry `par` finished in a parameterized query:
+    // add its Best to Sum; when it was the last child, update the ancestor
+    // from S_P + the children's covers (Algorithm 2 line 20), push that up
+    // (Section 3.5), free the children and the parent, and return true so the
+    // caller continues with the ancestor's LiveNodes.
+    __device__ bool complete_pvc_child(int c, int par, int bestc)
+    {
+        int r2 = 0;
+        if (tm.leader()) {
+            atomicAdd(&P.reg[par].val, bestc);
+            r2 = atom_add_acq_rel(&P.reg[par].live, -1) - 1;
+        }
+        r2 = tm.bcast(r2);
+        if (r2 != 0) return false;
+        const RegEntry &Pe = P.reg[par];
+        const int anc = vld(Pe.link);
+        const int sum = vld(Pe.val);
+        int go = 0;
+        if (tm.leader()) {
+            RegEntry &A = P.reg[anc];
+            if (sum < ld_relaxed(&A.val) && reg_lock(P, anc)) {
+                if (sum < vld(A.val)) go = 1;
+                else reg_unlock(P, anc);
+            }
+        }
+        go = tm.bcast(go);
+        if (go) {
+            assemble(anc, par, false);
+            int olda = 0;
+            if (tm.leader()) {
+                RegEntry &A = P.reg[anc];
+                olda = vld(A.cur);
+                A.has_w = 1;
+                A.cur = sum;
+                atomicExch(&A.val, sum);
+                reg_unlock(P, anc);
+                if (vld(A.link) < 0) query_done(P, q);
+            }
+            olda = tm.bcast(olda);
+            pvc_propagate(anc, olda, sum);
+        }
+        tm.sync();
+        if (tm.leader()) {
+            int ch = vld(Pe.first);
+            for (int guard = 0; ch >= 0 && guard < (1 << 20); guard++) {
+                const int nx = vld(P.reg[ch].sib);
+                reg_free(ch);
+                ch = nx;
+            }
+            reg_free(par);
+        }
+        tm.sync();
+        return true;
     }
 
     // ------------------------------------------------------------ components
@@ -952,68 +1089,82 @@ struct Worker {
                 E.nw = (chi >> 5) - (clo >> 5) + 1;
                 E.q = q;
                 E.kind = 1;
+                E.first = -1;
+                E.tot = S;      // + each child's cur, added as the children are registered
             }
             uint32_t *w = reg_words(P, pidx);
             const int nw = (chi >> 5) - (clo >> 5) + 1;
             for (int i = tm.rank; i < nw; i += tm.size()) w[i] = cov[i];
         }
         // child entries {Best_i, LiveNodes = 1, ParentIdx}, one per
-        // non-trivial component in index order; each child node is written by
-        // the whole team (sequential over components, parallel within one)
-        for (int base = 0; base < W; base += tm.size()) {
-            const int i = base + tm.rank;
-            bool isroot = false;
-            if (i < W && lab[i] == i) isroot = true;
-            // rank the roots of this stripe
-            int tot;
-            int pos = tm.excl_scan(isroot ? 1 : 0, &tot);
-            for (int j = 0; j < tot; j++) {
-                // the thread holding the j-th root broadcasts it
-                int mine = (isroot && pos == j) ? i : -1;
-                int r = tm.max(mine);
-                const int sz = __ldcg(csize + r), mx = __ldcg(cmax + r);
-                const int m = __ldcg(csum + r) / 2;
-                const int lb = (m + mx - 1) / mx;
-                int bi = B - S - (lb_sum - lb);
-                if (bi > sz - 1) bi = sz - 1;
-                const int clo_c = lo + r, chi_c = lo + __ldcg(chiv + r);
-                int cidx = -1;
-                if (tm.leader()) {
-                    cidx = reg_alloc();
-                    if (cidx < 0) set_error(P.ctl, VC_ECAPACITY, 8);
-                }
-                cidx = tm.bcast(cidx);
-                if (cidx < 0) return kError;
-                RegEntry &C = P.reg[cidx];
-                const int has = bi == sz - 1;
-                const int cw0 = clo_c >> 5, cnw = (chi_c >> 5) - cw0 + 1;
-                if (tm.leader()) {
-                    C.val = bi;
-                    C.live = 1;
-                    C.link = pidx;
-                    C.lock = 0;
-                    C.has_w = has;
-                    C.wlo = cw0;
-                    C.nw = cnw;
-                    C.q = q;
-                    C.kind = 0;
-                }
-                if (has) {
-                    // every vertex of the component but its highest one
-                    uint32_t *w = reg_words(P, cidx);
-                    for (int x = tm.rank; x < cnw; x += tm.size()) {
-                        uint32_t bits = 0;
-                        for (int b = 0; b < 32; b++) {
-                            const int v = (cw0 + x) * 32 + b;
-                            if (v >= lo + r && v < chi_c && lab[v - lo] == r) bits |= 1u << b;
+        // non-trivial component in index order.  Pass 1 registers and links
+        // every child (the parent's child list and running total are final
+        // before any child becomes visible); pass 2 writes each child node
+        // with the whole team (sequential over components, parallel within).
+        // cmin[r] holds the child's entry index between the passes.
+        for (int pass = 0; pass < 2; pass++) {
+            for (int base = 0; base < W; base += tm.size()) {
+                const int i = base + tm.rank;
+                const bool isroot = i < W && lab[i] == i;
+                int tot;
+                const int pos = tm.excl_scan(isroot ? 1 : 0, &tot);
+                for (int j = 0; j < tot; j++) {
+                    // the thread holding the j-th root of this stripe broadcasts it
+                    const int r = tm.max((isroot && pos == j) ? i : -1);
+                    const int clo_c = lo + r, chi_c = lo + __ldcg(chiv + r);
+                    if (pass == 1) {
+                        if (!push_child(1, -1, r, clo_c, chi_c, __ldcg(cmin + r), 0, chi_c)) return kError;
+                        continue;
+                    }
+                    const int sz = __ldcg(csize + r), mx = __ldcg(cmax + r);
+                    const int m = __ldcg(csum + r) / 2;
+                    const int lb = (m + mx - 1) / mx;
+                    int bi = B - S - (lb_sum - lb);
+                    if (bi > sz - 1) bi = sz - 1;
+                    int cidx = -1;
+                    if (tm.leader()) {
+                        cidx = reg_alloc();
+                        if (cidx < 0) set_error(P.ctl, VC_ECAPACITY, 8);
+                    }
+                    cidx = tm.bcast(cidx);
+                    if (cidx < 0) return kError;
+                    RegEntry &C = P.reg[cidx];
+                    RegEntry &E = P.reg[pidx];
+                    // a parameterized query needs every child's achievable cover
+                    const int has = bi == sz - 1 || pvc();
+                    const int cw0 = clo_c >> 5, cnw = (chi_c >> 5) - cw0 + 1;
+                    if (tm.leader()) {
+                        C.val = bi;
+                        C.live = 1;
+                        C.link = pidx;
+                        C.lock = 0;
+                        C.has_w = bi == sz - 1;
+                        C.cur = sz - 1;
+                        C.sib = E.first;
+                        E.first = cidx;
+                        E.tot += sz - 1;
+                        C.wlo = cw0;
+                        C.nw = cnw;
+                        C.q = q;
+                        C.kind = 0;
+                        cmin[r] = cidx;
+                    }
+                    if (has) {
+                        // every vertex of the component but its highest one
+                        uint32_t *w = reg_words(P, cidx);
+                        for (int x = tm.rank; x < cnw; x += tm.size()) {
+                            uint32_t bits = 0;
+                            for (int bb = 0; bb < 32; bb++) {
+                                const int v = (cw0 + x) * 32 + bb;
+                                if (v >= lo + r && v < chi_c && lab[v - lo] == r) bits |= 1u << bb;
+                            }
+                            w[x] = bits;
                         }
-                        w[x] = bits;
                     }
                 }
-                __threadfence();
-                tm.sync();
-                if (!push_child(1, -1, r, clo_c, chi_c, cidx, 0, chi_c)) return kError;
             }
+            __threadfence();
+            tm.sync();
         }
         if (tm.leader()) {
             atomicAdd(&ctlw(P.ctl, kCompBranches), 1ull);

@@ -158,6 +158,25 @@ def test_pvc_at_opt_and_opt_minus_one(vc):
         dg.close()
 
 
+@pytest.mark.parametrize("copies,copy_n,p,chain", [(4, 48, 0.12, 2), (8, 24, 0.2, 3), (16, 20, 0.2, 4),
+                                                   (32, 16, 0.25, 6)])
+def test_pvc_component_heavy(vc, copies, copy_n, p, chain):
+    # improvements inside components are pushed to the root (Section 3.5):
+    # the answer and the witness must stay exact
+    g = gg.component_heavy(2, copies=copies, copy_n=copy_n, p=p, chain=chain)
+    opt = oracle.mvc(g.n, g.row_ptr, g.col, node_budget=5_000_000)[0]
+    dg = vc.Graph.from_csr(g.row_ptr, g.col)
+    for team in (32, 256):
+        yes, cover, st = vc.solve_k(dg, opt, team=team)
+        assert yes and len(cover) <= opt
+        check_cover(g, cover, len(cover))
+        assert not vc.solve_k(dg, opt - 1, team=team)[0]
+        yes2, cover2, _ = vc.solve_k(dg, opt + 2, team=team)
+        assert yes2 and len(cover2) <= opt + 2
+        check_cover(g, cover2, len(cover2))
+    dg.close()
+
+
 def test_pvc_k_zero(vc):
     g = gg.from_edges(5, [], [])
     dg = vc.Graph.from_csr(g.row_ptr, g.col)
