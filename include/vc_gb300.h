@@ -191,6 +191,10 @@ int vc_root_reduce_static(int32_t n, int32_t m2, const int32_t *d_row_ptr, const
 /* Release the handle and all device memory it owns.  NULL is a no-op. */
 void vc_free(vc_graph *g);
 
+/* Name of the CUDA error behind the last VC_ECUDA / VC_ENOMEM returned on
+ * this host thread ("no error" if none). */
+const char *vc_last_cuda_error(void);
+
 /* Static string naming a status code. */
 const char *vc_strerror(int status);
 

@@ -96,6 +96,7 @@ SIGNATURES = {
     "vc_root_reduce_static": (ctypes.c_int, [_I, _I, _P, _P, _I, _P, _P, _P, _P, _P, _P]),
     "vc_free": (None, [_P]),
     "vc_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+    "vc_last_cuda_error": (ctypes.c_char_p, []),
 }
 
 
@@ -126,4 +127,7 @@ def strerror(status: int) -> str:
 
 def check(status: int, stats=None) -> None:
     if status != VC_OK:
-        raise VcError(int(status), strerror(status), stats.to_dict() if stats is not None else None)
+        msg = strerror(status)
+        if status in (VC_ECUDA, VC_ENOMEM):
+            msg += ": " + lib().vc_last_cuda_error().decode()
+        raise VcError(int(status), msg, stats.to_dict() if stats is not None else None)

@@ -250,7 +250,19 @@ int solve_queries(vc_graph *g0, const std::vector<QueryRef> &qs, const vc_option
         if (dtype < need) dtype = need;
         const int ncap = (max_np + 16 + 15) / 16 * 16;
         const int wcap = max_np / 32 + 2;
-        if ((rc = search_plan(dtype, opt.team, ncap, wcap, g0->sms, &pl)) != VC_OK) {
+        // one searched query with a small induced graph: stage its CSR in
+        // shared memory (up to 48 KB, and only when it still leaves room)
+        int csr_bytes = 0, csr_query = 0;
+        if (nroots == 1) {
+            int qi = 0;
+            while (root_slot[qi] < 0) qi++;
+            csr_query = qi;
+            const long long b = 4ll * (hq[qi].np + 1 + hq[qi].m2p);
+            if (b <= 48 * 1024) csr_bytes = (int)((b + 15) / 16 * 16);
+        }
+        rc = search_plan(dtype, opt.team, ncap, wcap, g0->sms, csr_bytes, &pl);
+        if (rc == VC_ECAPACITY && csr_bytes > 0) rc = search_plan(dtype, opt.team, ncap, wcap, g0->sms, 0, &pl);
+        if (rc != VC_OK) {
             if (rc == VC_ECUDA) last_cuda_error() = cudaGetLastError();
             return rc;
         }
@@ -308,6 +320,8 @@ int solve_queries(vc_graph *g0, const std::vector<QueryRef> &qs, const vc_option
         P.idle_timeout_ns = (long long)opt.idle_timeout_ms * 1000000ll;
         P.use_components = opt.use_components;
         P.load_balance = opt.load_balance;
+        P.csr_smem = pl.csr_bytes;
+        P.csr_query = csr_query;
         VC_CK(search_run(pl, P, ws.root_slot.as<int>(), nq, nroots, s, ws.ev[2], ws.ev[3]));
         VC_CK(finalize_run(dq, nq, P.reg, P.reg_words, wcap, s));
         VC_CK(cudaMemcpyAsync(ws.hctl.p, P.ctl, kCtlWords * 8, cudaMemcpyDeviceToHost, s));
@@ -527,6 +541,11 @@ void vc_free(vc_graph *g)
     g->err.release();
     g->ws.release();
     delete g;
+}
+
+const char *vc_last_cuda_error(void)
+{
+    return cudaGetErrorString(last_cuda_error());
 }
 
 const char *vc_strerror(int status)

@@ -149,6 +149,9 @@ struct SearchParams {
     long long idle_timeout_ns;
     int use_components;
     int load_balance;
+    int csr_smem;             // >0: the (single) query's induced CSR is staged in shared
+                              // memory (this many bytes at the start of each block's region)
+    int csr_query;            // the query whose CSR is staged
 };
 
 // Control block: one unsigned long long per entry, each entry on its own

@@ -24,11 +24,13 @@ struct SearchPlan {
     int workers;        // workers = blocks * (warp_team ? threads / 32 : 1)
     size_t smem;        // dynamic shared memory per block
     int slot_bytes;     // bytes per node slot
+    int csr_bytes;      // shared memory reserved for a staged CSR (0: none)
 };
 
 // Choose the worker shape for induced graphs of up to ncap vertices.
 // Returns VC_OK or VC_ECAPACITY (does not fit in shared memory).
-int search_plan(int dtype, int team_req, int ncap, int wcap, int sms, SearchPlan *out);
+// csr_bytes > 0 reserves that much shared memory per block for a staged CSR.
+int search_plan(int dtype, int team_req, int ncap, int wcap, int sms, int csr_bytes, SearchPlan *out);
 
 // Initialise the registry / worklist, place each root node (root_slot[q] >= 0
 // for searched queries) and run the persistent kernel.

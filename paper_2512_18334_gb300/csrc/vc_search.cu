@@ -26,6 +26,27 @@
 
 namespace vcg {
 
+// ---------------------------------------------------------------- checks
+//
+// Built with -DVC_CHECKS, every shared-memory, slot, registry and stack index
+// below is verified first; a bad one is skipped and recorded (status
+// VC_ECAPACITY, site code 100 + n in the control block) instead of executed.
+#ifdef VC_CHECKS
+#define VC_GUARD(cond, site)                                            \
+    if (!(cond)) {                                                      \
+        set_error(P.ctl, VC_ECAPACITY, 100 + (site));                   \
+        return;                                                         \
+    }
+#define VC_GUARD_R(cond, site, r)                                       \
+    if (!(cond)) {                                                      \
+        set_error(P.ctl, VC_ECAPACITY, 100 + (site));                   \
+        return r;                                                       \
+    }
+#else
+#define VC_GUARD(cond, site)
+#define VC_GUARD_R(cond, site, r)
+#endif
+
 // ---------------------------------------------------------------- sizes
 
 template <typename T>
@@ -159,6 +180,8 @@ struct Worker {
     uint32_t *cov;    // cover bitmap of the context window
     int *sc;          // scalars
 
+    const int *csr_s;   // staged CSR in shared memory (single-query launches) or null
+
     // node state (uniform across the team)
     int q, np;
     const int *rp, *col;
@@ -177,7 +200,8 @@ struct Worker {
     long long bytes_local;   // this thread's share of the algorithmic bytes
     int max_top;
 
-    __device__ Worker(const SearchParams &p, Team<WT> t, int w, char *smem) : P(p), tm(t), wid(w)
+    __device__ Worker(const SearchParams &p, Team<WT> t, int w, char *smem, const int *csr)
+        : P(p), tm(t), wid(w), csr_s(csr)
     {
         const int ncap = P.ncap, wcap = P.wcap;
         char *s = smem;
@@ -216,6 +240,7 @@ struct Worker {
 
     __device__ __forceinline__ void dec(int u)
     {
+        VC_GUARD(u >= wlo && u <= whi && u - wlo < P.ncap, 1)
         const int off = u - wlo;
         if constexpr (sizeof(T) == 1) {
             unsigned *w = (unsigned *)((char *)d + (off & ~3));
@@ -231,17 +256,20 @@ struct Worker {
     // queue u for the cover in this round (deduplicated); list in lab[]
     __device__ __forceinline__ void mark_vertex(int u)
     {
+        VC_GUARD(u >= wlo && u <= whi && u - wlo < P.ncap, 2)
         const int off = u - wlo;
         unsigned *w = (unsigned *)(mark + (off & ~3));
         unsigned bit = 1u << (8 * (off & 3));
         if (!(atomicOr(w, bit) & bit)) {
             int pos = atomicAdd(&sc[cntbuf], 1);
+            VC_GUARD(pos >= 0 && pos < P.ncap, 3)
             lab[pos] = u;
         }
     }
 
     __device__ __forceinline__ void cov_set(int v)
     {
+        VC_GUARD(v >= clo && v <= chi && (v >> 5) - (clo >> 5) < P.wcap, 4)
         atomicOr(&cov[(v >> 5) - (clo >> 5)], 1u << (v & 31));
     }
 
@@ -251,7 +279,7 @@ struct Worker {
         int l = 0, h = rp[a + 1] - rp[a] - 1;
         while (l <= h) {
             int mid = (l + h) >> 1;
-            int x = __ldg(row + mid);
+            int x = row[mid];
             if (x == b) return true;
             if (x < b) l = mid + 1; else h = mid - 1;
         }
@@ -268,13 +296,14 @@ struct Worker {
             cov_set(u);
             bytes_local += 8 + 4ll * (rp[u + 1] - rp[u]);
             for (int e = rp[u]; e < rp[u + 1]; e++) {
-                const int x = __ldg(col + e);
+                const int x = col[e];
                 if (dg(x) > 0 && !marked(x)) dec(x);
             }
         }
         tm.sync();
         for (int i = tm.rank; i < c; i += tm.size()) {
             const int u = lab[i];
+            VC_GUARD(u >= wlo && u <= whi && u - wlo < P.ncap, 5)
             d[u - wlo] = 0;
             mark[u - wlo] = 0;
         }
@@ -307,6 +336,13 @@ struct Worker {
     __device__ Stats reduce(int B)
     {
         Stats st;
+#ifdef VC_CHECKS
+        if (!(lo >= wlo && hi <= whi && whi - wlo < P.ncap && chi - clo >= 0 && (chi >> 5) - (clo >> 5) < P.wcap)) {
+            if (tm.leader()) set_error(P.ctl, VC_ECAPACITY, 106);
+            st.pruned = 1;
+            return st;
+        }
+#endif
         for (;;) {
             const int bud = B - S - 1;
             if (bud < 0) { st.pruned = 1; return st; }
@@ -327,7 +363,7 @@ struct Worker {
                     int u = -1;
                     int e = rp[v];
                     for (; e < rp[v + 1]; e++) {
-                        int x = __ldg(col + e);
+                        int x = col[e];
                         if (dg(x) > 0) { u = x; break; }
                     }
                     bytes_local += 8 + 4ll * (e - rp[v] + 1);
@@ -336,7 +372,7 @@ struct Worker {
                     int u = -1, w = -1;
                     int e = rp[v];
                     for (; e < rp[v + 1]; e++) {
-                        int x = __ldg(col + e);
+                        int x = col[e];
                         if (dg(x) > 0) {
                             if (u < 0) u = x; else { w = x; break; }
                         }
@@ -369,7 +405,13 @@ struct Worker {
 
     // ------------------------------------------------------------ slots
 
-    __device__ char *stack_slot(int i) const { return stack + (size_t)i * P.slot_bytes; }
+    __device__ char *stack_slot(int i) const
+    {
+#ifdef VC_CHECKS
+        if (i < 0 || i >= P.stack_depth) { set_error(P.ctl, VC_ECAPACITY, 107); i = 0; }
+#endif
+        return stack + (size_t)i * P.slot_bytes;
+    }
 
     // Write the current node (or a component child) into a slot.
     //   kind 0: the current array with a pending op (right child G - N(op))
@@ -431,6 +473,13 @@ struct Worker {
         clo = __ldcg(&h->clo); chi = __ldcg(&h->chi); q = __ldcg(&h->q); depth = __ldcg(&h->depth);
         const int op = __ldcg(&h->op), cov_empty = __ldcg(&h->cov_empty);
         lo = wlo; hi = whi;
+#ifdef VC_CHECKS
+        if (!(wlo >= 0 && whi >= wlo && align_up(whi + 1, V) - wlo <= P.ncap && clo <= chi &&
+              (chi >> 5) - (clo >> 5) < P.wcap && comp >= 0 && comp < P.reg_cap && q >= 0 && q < P.nq)) {
+            if (tm.leader()) set_error(P.ctl, VC_ECAPACITY, 108);
+            whi = wlo = lo = hi = 0; clo = chi = 0; comp = 0; q = 0;
+        }
+#endif
         const int nvec = (align_up(whi + 1, V) - wlo) / V;
         const uint4 *src = (const uint4 *)(slot + sizeof(NodeHdr));
         uint4 *dst = (uint4 *)d;
@@ -444,14 +493,19 @@ struct Worker {
         for (int i = tm.rank; i < nw; i += tm.size()) cov[i] = cov_empty ? 0u : __ldcg(csrc + i);
         if (tm.leader()) bytes_local += (long long)sizeof(NodeHdr) + 16ll * nvec + (cov_empty ? 0 : 4ll * nw);
         const QueryDesc &Q = P.queries[q];
-        rp = Q.rp2;
-        col = Q.col2;
+        if (csr_s && q == P.csr_query) {
+            rp = csr_s;
+            col = csr_s + Q.np + 1;
+        } else {
+            rp = Q.rp2;
+            col = Q.col2;
+        }
         np = Q.np;
         tm.sync();
         if (op >= 0) {
             // right child of a vertex branch: G - N(op), S + N(op)
             for (int e = rp[op] + tm.rank; e < rp[op + 1]; e += tm.size()) {
-                const int x = __ldg(col + e);
+                const int x = col[e];
                 if (dg(x) > 0) mark_vertex(x);
                 bytes_local += 4;
             }
@@ -911,7 +965,7 @@ struct Worker {
             if (d[v - wlo] == 0) continue;
             bytes_local += 8 + 4ll * (rp[v + 1] - rp[v]);
             for (int e = rp[v]; e < rp[v + 1]; e++) {
-                const int u = __ldg(col + e);
+                const int u = col[e];
                 if (u > v && u <= hi && d[u - wlo] > 0) uf_unite(i, u - lo);
             }
         }
@@ -936,7 +990,7 @@ struct Worker {
             if ((k & 1) == 0) cov_set(cur);
             int next = -1;
             for (int e = rp[cur]; e < rp[cur + 1]; e++) {
-                const int x = __ldg(col + e);
+                const int x = col[e];
                 if (x != prev && dg(x) > 0) { next = x; break; }
             }
             prev = cur;
@@ -1321,7 +1375,21 @@ struct Worker {
 template <typename T, int WT>
 __global__ void search_kernel(const __grid_constant__ SearchParams P)
 {
-    extern __shared__ __align__(16) char smem[];
+    extern __shared__ __align__(16) char smem_all[];
+    // single-query launches keep the induced CSR (row pointers, then
+    // columns) in shared memory: every row read of the search hits it
+    const int *csr = nullptr;
+    char *smem = smem_all;
+    if (P.csr_smem > 0) {
+        const QueryDesc &Q = P.queries[P.csr_query];
+        int *dst = (int *)smem_all;
+        const int nrp = Q.np + 1, ncol = Q.m2p;
+        for (int i = threadIdx.x; i < nrp; i += blockDim.x) dst[i] = __ldg(Q.rp2 + i);
+        for (int i = threadIdx.x; i < ncol; i += blockDim.x) dst[nrp + i] = __ldg(Q.col2 + i);
+        __syncthreads();
+        csr = dst;
+        smem = smem_all + P.csr_smem;
+    }
     if constexpr (WT == 1) {
         const int warp = threadIdx.x >> 5;
         const int wpb = blockDim.x >> 5;
@@ -1329,14 +1397,14 @@ __global__ void search_kernel(const __grid_constant__ SearchParams P)
         Team<1> t;
         t.rank = threadIdx.x & 31;
         char *mine = smem + (size_t)warp * align_up(worker_smem_bytes<T>(P.ncap, P.wcap), 16);
-        Worker<T, 1> w(P, t, wid, mine);
+        Worker<T, 1> w(P, t, wid, mine, csr);
         w.run();
     } else {
         Team<0> t;
         t.rank = threadIdx.x;
         t.nthreads = blockDim.x;
         t.red = nullptr;
-        Worker<T, 0> w(P, t, blockIdx.x, smem);
+        Worker<T, 0> w(P, t, blockIdx.x, smem, csr);
         w.run();
     }
 }
@@ -1423,10 +1491,10 @@ static cudaError_t plan_one(int threads, size_t smem, int *blocks_per_sm)
 }
 
 template <typename T>
-static int plan_t(int team_req, int ncap, int wcap, int sms, SearchPlan *pl)
+static int plan_t(int team_req, int ncap, int wcap, int sms, int csr_bytes, SearchPlan *pl)
 {
     const int wsm = align_up(worker_smem_bytes<T>(ncap, wcap), 16);
-    const int kMaxSmem = 227 * 1024;
+    const int kMaxSmem = 227 * 1024 - csr_bytes;
     pl->dtype = sizeof(T);
     pl->slot_bytes = slot_bytes_for<T>(ncap, wcap);
     bool warp = team_req == 32 || (team_req == 0 && wsm <= 12 * 1024);
@@ -1437,14 +1505,14 @@ static int plan_t(int team_req, int ncap, int wcap, int sms, SearchPlan *pl)
         if (wpb < 1) return VC_ECAPACITY;
         pl->warp_team = 1;
         pl->threads = 32 * wpb;
-        pl->smem = (size_t)wpb * wsm;
+        pl->smem = (size_t)wpb * wsm + csr_bytes;
         if (plan_one<T, 1>(pl->threads, pl->smem, &bps) != cudaSuccess) return VC_ECUDA;
     } else {
         if (wsm > kMaxSmem) return VC_ECAPACITY;
         int th = team_req >= 64 ? team_req : (ncap > 4096 ? 512 : 256);
         pl->warp_team = 0;
         pl->threads = th;
-        pl->smem = (size_t)wsm;
+        pl->smem = (size_t)wsm + csr_bytes;
         if (plan_one<T, 0>(pl->threads, pl->smem, &bps) != cudaSuccess) return VC_ECUDA;
     }
     if (bps < 1) return VC_ECAPACITY;
@@ -1453,12 +1521,13 @@ static int plan_t(int team_req, int ncap, int wcap, int sms, SearchPlan *pl)
     return VC_OK;
 }
 
-int search_plan(int dtype, int team_req, int ncap, int wcap, int sms, SearchPlan *out)
+int search_plan(int dtype, int team_req, int ncap, int wcap, int sms, int csr_bytes, SearchPlan *out)
 {
+    out->csr_bytes = csr_bytes;
     switch (dtype) {
-    case 1: return plan_t<uint8_t>(team_req, ncap, wcap, sms, out);
-    case 2: return plan_t<uint16_t>(team_req, ncap, wcap, sms, out);
-    default: return plan_t<uint32_t>(team_req, ncap, wcap, sms, out);
+    case 1: return plan_t<uint8_t>(team_req, ncap, wcap, sms, csr_bytes, out);
+    case 2: return plan_t<uint16_t>(team_req, ncap, wcap, sms, csr_bytes, out);
+    default: return plan_t<uint32_t>(team_req, ncap, wcap, sms, csr_bytes, out);
     }
 }
 
