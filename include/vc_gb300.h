@@ -191,6 +191,132 @@ int vc_root_reduce_static(int32_t n, int32_t m2, const int32_t *d_row_ptr, const
 /* Release the handle and all device memory it owns.  NULL is a no-op. */
 void vc_free(vc_graph *g);
 
+/* ------------------------------------------------------------------ serving
+ *
+ * A request server with continuous batching (a build extension: the paper
+ * solves one graph per launch).  Requests -- a graph and a mode (minimum
+ * cover, or "is there a cover of size <= k?") -- are queued on the host by
+ * vc_server_submit().  Each vc_server_step():
+ *   1. admits queued requests in submission order while a query slot is free
+ *      and the device arena has room for the request's resident arrays
+ *      (induced subgraph, id map, cover arrays: about 4 n + 4 * 2|E| + 14 n
+ *      bytes): admission by device memory.  The admitted graphs are copied
+ *      to the device in one transfer, validated like vc_load_csr,
+ *      root-reduced (Section 4.2), and their root nodes are pushed into the
+ *      shared worklist, which still holds the nodes of the requests admitted
+ *      earlier;
+ *   2. runs the persistent search (Sections 2.3, 3) for one time slice over
+ *      every request in flight, old and new together.  At the end of the
+ *      slice each worker stores the node it holds and exits; node slots,
+ *      worklist, registry and private stacks stay resident in device memory
+ *      and the next slice resumes from them;
+ *   3. retires the requests that finished: answers and covers are finalised
+ *      on the device and written to mapped host memory, and their slots and
+ *      arena space are freed.
+ * The answer of a request does not depend on what else is in flight; it is
+ * the answer vc_solve_min / vc_solve_k give for the same graph.  The
+ * resident search accepts induced subgraphs of up to max_induced vertices
+ * (after the root reduction); a larger one finishes with VC_ECAPACITY.
+ *
+ * Threading: a server is not thread-safe; one host thread drives it.
+ */
+typedef struct vc_server vc_server;
+
+typedef struct vc_server_config {
+    int32_t max_inflight;      /* query slots resident on the device (default 1024) */
+    int32_t max_induced;       /* vertex capacity of a search node (default 2048) */
+    int32_t dtype_bytes;       /* degree entry size 1, 2 or 4 (0: 2) */
+    int32_t team;              /* as vc_options.team (0: 128-thread block workers) */
+    int32_t stack_depth;       /* private stack slots per worker (0: auto) */
+    int32_t worklist_capacity; /* shared worklist slots (0: auto) */
+    int32_t registry_capacity; /* registry entries (0: auto) */
+    int32_t quantum_us;        /* search time slice per step (default 2000) */
+    int32_t use_components;    /* default 1 */
+    int32_t load_balance;      /* default 1 */
+    int32_t idle_timeout_ms;   /* default 60000 */
+    int32_t reserved;
+    int64_t arena_bytes;       /* device memory for admitted requests (default 2 GiB) */
+    int64_t node_budget;       /* per request (0: none); VC_EBUDGET when exceeded */
+    int64_t cover_buffer;      /* int32 entries of the mapped cover buffer (default 16M) */
+} vc_server_config;
+
+typedef struct vc_server_result {
+    int64_t tag;               /* the caller's tag from vc_server_submit */
+    int32_t status;            /* VC_OK, or the status that ended the request */
+    int32_t size;              /* MVC: minimum size; PVC: size of the cover found, or -1 */
+    int32_t yes;               /* PVC answer (1 for MVC) */
+    int32_t n;                 /* vertices of the request's graph */
+    int32_t n_induced;         /* vertices left after the root reduction */
+    int32_t cover_len;         /* entries of the cover (0 when status != VC_OK or PVC no) */
+    int64_t cover_off;         /* offset of the cover in vc_server_poll's cover_buf */
+    int64_t nodes;             /* search-tree nodes spent on the request */
+    double t_submit_ms;        /* server clock: milliseconds since vc_server_create */
+    double t_admit_ms;
+    double t_done_ms;
+} vc_server_result;
+
+typedef struct vc_server_stats {
+    int64_t steps;             /* vc_server_step calls */
+    int64_t slices;            /* search kernel launches */
+    int64_t submitted, admitted, completed;
+    int64_t nodes;             /* search-tree nodes, all requests */
+    int64_t search_bytes;      /* algorithmic bytes moved by the search */
+    int64_t h2d_bytes;         /* graphs copied to the device */
+    int64_t d2h_bytes;         /* records and covers written to host memory */
+    int64_t resets;            /* times the resident search state was emptied */
+    double ms_admit;           /* device time: validation, root phase, placement */
+    double ms_search;          /* device time of the search slices */
+    double ms_retire;          /* device time of finalisation */
+    int32_t workers, team, dtype_bytes, max_induced;
+    int32_t slot_bytes, max_stack;
+    int64_t device_bytes;      /* device memory held by the server */
+} vc_server_stats;
+
+/* Fill *cfg with the defaults. */
+int vc_server_config_default(vc_server_config *cfg);
+
+/* Create a server on the current device; every launch runs on `cuda_stream`
+ * (a cudaStream_t, NULL = legacy default stream).  Allocates the resident
+ * search state (node slots, worklist, registry), the arena and the mapped
+ * host buffers up front.  VC_EINVAL (bad config), VC_ECAPACITY (max_induced
+ * does not fit a worker in shared memory), VC_ENOMEM, VC_ECUDA. */
+int vc_server_create(const vc_server_config *cfg, void *cuda_stream, vc_server **out);
+
+/* Queue a request.  row_ptr / col are HOST arrays in the CSR form above;
+ * they are copied, so the caller may reuse them on return.  k < 0: minimum
+ * cover; k >= 0: is there a cover of size <= k.  The graph is validated on
+ * the device at admission (a malformed one finishes with VC_EINVAL).
+ * Returns VC_EINVAL (n < 0, null arrays, row_ptr[n] odd or negative) or
+ * VC_ECAPACITY (the request alone is larger than the arena). */
+int vc_server_submit(vc_server *s, int32_t n, const int32_t *row_ptr, const int32_t *col, int32_t k,
+                     int64_t tag);
+
+/* One scheduling iteration (admit, one search slice, retire); blocks until
+ * the device finished it.  *completed (nullable) receives the number of
+ * requests retired by this step.  A device-side failure (a bounded wait
+ * expired, stack / worklist / registry full) ends every request in flight
+ * with that status and empties the resident state; the server stays usable
+ * and the step returns VC_OK.  VC_ECUDA / VC_ENOMEM are returned as such. */
+int vc_server_step(vc_server *s, int32_t *completed);
+
+/* Counts of queued (not yet admitted), in-flight and retired-but-not-polled
+ * requests (each pointer nullable). */
+int vc_server_counts(const vc_server *s, int32_t *queued, int32_t *inflight, int32_t *ready);
+
+/* Take up to max_results retired requests in completion order.  Their
+ * covers are packed into cover_buf (host, capacity cover_cap int32
+ * entries; nullable when cover_cap is 0) at each result's cover_off; a
+ * result whose cover does not fit stays for the next poll.  *count receives
+ * the number taken. */
+int vc_server_poll(vc_server *s, int32_t max_results, vc_server_result *out, int32_t *count,
+                   int32_t *cover_buf, int64_t cover_cap);
+
+/* Cumulative statistics. */
+int vc_server_get_stats(const vc_server *s, vc_server_stats *st);
+
+/* Release the server and all its memory.  NULL is a no-op. */
+void vc_server_free(vc_server *s);
+
 /* Name of the CUDA error behind the last VC_ECUDA / VC_ENOMEM returned on
  * this host thread ("no error" if none). */
 const char *vc_last_cuda_error(void);

@@ -9,6 +9,10 @@ importing this package never falls back to anything else.
     g = vc.Graph.from_csr(row_ptr, col)          # host numpy arrays
     size, cover, stats = vc.solve_min(g)
     yes, cover, stats = vc.solve_k(g, k)
+
+    srv = vc.Server(max_induced=2048)                 # resident search, continuous batching
+    srv.submit(row_ptr, col, tag=7)
+    results = srv.drain()                             # steps until every request retired
 """
 from __future__ import annotations
 
@@ -19,10 +23,10 @@ import numpy as np
 
 from . import _lib as _L
 from ._lib import (VC_OK, VC_EINVAL, VC_ENOMEM, VC_ECAPACITY, VC_ETIMEOUT, VC_ECUDA, VC_EBUDGET,
-                   VcError, Options, Stats, lib_path)
+                   VcError, Options, Stats, ServerConfig, ServerResult, ServerStats, lib_path)
 
 __all__ = [
-    "Graph", "solve_min", "solve_k", "solve_batch", "options", "VcError", "lib_path",
+    "Graph", "solve_min", "solve_k", "solve_batch", "options", "Server", "VcError", "lib_path",
     "VC_OK", "VC_EINVAL", "VC_ENOMEM", "VC_ECAPACITY", "VC_ETIMEOUT", "VC_ECUDA", "VC_EBUDGET",
 ]
 
@@ -155,3 +159,98 @@ def solve_batch(graphs, ks=None, opts: Options | None = None, want_covers: bool 
         _L.check(rc, st)
     covers = [b[:l].copy() for b, l in zip(bufs, lens)] if want_covers else None
     return sizes, yes.astype(bool), status, covers, st.to_dict()
+
+
+class Server:
+    """Request server with continuous batching (vc_server_*): requests are
+    admitted by device memory, root-reduced and searched in time slices
+    together with the requests already in flight; the search state stays
+    resident on the device between steps."""
+
+    def __init__(self, stream=None, **cfg):
+        c = ServerConfig()
+        _L.check(_L.lib().vc_server_config_default(ctypes.byref(c)))
+        for k, v in cfg.items():
+            if not hasattr(c, k):
+                raise TypeError(f"unknown server option {k}")
+            setattr(c, k, v)
+        self.config = c
+        self._h = ctypes.c_void_p()
+        _L.check(_L.lib().vc_server_create(ctypes.byref(c), _stream_handle(stream), ctypes.byref(self._h)))
+        self._covers = np.zeros(1 << 20, np.int32)
+        self._next_tag = 0
+
+    def submit(self, row_ptr, col, k: int = -1, tag: int | None = None) -> int:
+        """Queue one graph (host CSR arrays, copied); returns its tag."""
+        rp = np.ascontiguousarray(row_ptr, dtype=np.int32)
+        cl = np.ascontiguousarray(col, dtype=np.int32)
+        if tag is None:
+            tag = self._next_tag
+        self._next_tag = max(self._next_tag, int(tag) + 1)
+        _L.check(_L.lib().vc_server_submit(self._h, int(rp.size - 1), rp.ctypes.data_as(ctypes.c_void_p),
+                                           cl.ctypes.data_as(ctypes.c_void_p) if cl.size else None,
+                                           int(k), int(tag)))
+        return int(tag)
+
+    def step(self) -> int:
+        """One scheduling iteration; returns the number of requests retired."""
+        done = ctypes.c_int32(0)
+        _L.check(_L.lib().vc_server_step(self._h, ctypes.byref(done)))
+        return done.value
+
+    def counts(self):
+        """(queued, in flight, retired but not polled)."""
+        q, f, r = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        _L.check(_L.lib().vc_server_counts(self._h, ctypes.byref(q), ctypes.byref(f), ctypes.byref(r)))
+        return q.value, f.value, r.value
+
+    def poll(self, max_results: int = 4096) -> list:
+        """Retired requests in completion order, as dicts with the cover."""
+        out = []
+        while True:
+            res = (ServerResult * max_results)()
+            cnt = ctypes.c_int32(0)
+            _L.check(_L.lib().vc_server_poll(self._h, max_results, res, ctypes.byref(cnt),
+                                             self._covers.ctypes.data_as(ctypes.c_void_p),
+                                             int(self._covers.size)))
+            for i in range(cnt.value):
+                r = res[i]
+                d = {name: getattr(r, name) for name, _ in ServerResult._fields_}
+                off, ln = r.cover_off, r.cover_len
+                d["cover"] = self._covers[off:off + ln].copy() if ln > 0 else np.zeros(0, np.int32)
+                out.append(d)
+            if cnt.value == 0:
+                if self.counts()[2] > 0:            # the next cover is larger than the buffer
+                    self._covers = np.zeros(self._covers.size * 2, np.int32)
+                    continue
+                return out
+            if cnt.value < max_results and self.counts()[2] == 0:
+                return out
+
+    def drain(self, max_steps: int = 1 << 30) -> list:
+        """Step until nothing is queued or in flight; returns every result."""
+        out = []
+        for _ in range(max_steps):
+            q, f, _r = self.counts()
+            if q == 0 and f == 0:
+                break
+            self.step()
+            out.extend(self.poll())
+        out.extend(self.poll())
+        return out
+
+    def stats(self) -> dict:
+        st = ServerStats()
+        _L.check(_L.lib().vc_server_get_stats(self._h, ctypes.byref(st)))
+        return st.to_dict()
+
+    def close(self):
+        if self._h is not None and self._h.value:
+            _L.lib().vc_server_free(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -83,6 +83,71 @@ class Stats(ctypes.Structure):
         return d
 
 
+class ServerConfig(ctypes.Structure):
+    _fields_ = [
+        ("max_inflight", ctypes.c_int32),
+        ("max_induced", ctypes.c_int32),
+        ("dtype_bytes", ctypes.c_int32),
+        ("team", ctypes.c_int32),
+        ("stack_depth", ctypes.c_int32),
+        ("worklist_capacity", ctypes.c_int32),
+        ("registry_capacity", ctypes.c_int32),
+        ("quantum_us", ctypes.c_int32),
+        ("use_components", ctypes.c_int32),
+        ("load_balance", ctypes.c_int32),
+        ("idle_timeout_ms", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
+        ("arena_bytes", ctypes.c_int64),
+        ("node_budget", ctypes.c_int64),
+        ("cover_buffer", ctypes.c_int64),
+    ]
+
+
+class ServerResult(ctypes.Structure):
+    _fields_ = [
+        ("tag", ctypes.c_int64),
+        ("status", ctypes.c_int32),
+        ("size", ctypes.c_int32),
+        ("yes", ctypes.c_int32),
+        ("n", ctypes.c_int32),
+        ("n_induced", ctypes.c_int32),
+        ("cover_len", ctypes.c_int32),
+        ("cover_off", ctypes.c_int64),
+        ("nodes", ctypes.c_int64),
+        ("t_submit_ms", ctypes.c_double),
+        ("t_admit_ms", ctypes.c_double),
+        ("t_done_ms", ctypes.c_double),
+    ]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [
+        ("steps", ctypes.c_int64),
+        ("slices", ctypes.c_int64),
+        ("submitted", ctypes.c_int64),
+        ("admitted", ctypes.c_int64),
+        ("completed", ctypes.c_int64),
+        ("nodes", ctypes.c_int64),
+        ("search_bytes", ctypes.c_int64),
+        ("h2d_bytes", ctypes.c_int64),
+        ("d2h_bytes", ctypes.c_int64),
+        ("resets", ctypes.c_int64),
+        ("ms_admit", ctypes.c_double),
+        ("ms_search", ctypes.c_double),
+        ("ms_retire", ctypes.c_double),
+        ("workers", ctypes.c_int32),
+        ("team", ctypes.c_int32),
+        ("dtype_bytes", ctypes.c_int32),
+        ("max_induced", ctypes.c_int32),
+        ("slot_bytes", ctypes.c_int32),
+        ("max_stack", ctypes.c_int32),
+        ("device_bytes", ctypes.c_int64),
+    ]
+
+    def to_dict(self) -> dict:
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
 # Every symbol the header declares, with its ctypes signature.
 _P = ctypes.c_void_p
 _I = ctypes.c_int32
@@ -97,6 +162,14 @@ SIGNATURES = {
     "vc_free": (None, [_P]),
     "vc_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "vc_last_cuda_error": (ctypes.c_char_p, []),
+    "vc_server_config_default": (ctypes.c_int, [_P]),
+    "vc_server_create": (ctypes.c_int, [_P, _P, _P]),
+    "vc_server_submit": (ctypes.c_int, [_P, _I, _P, _P, _I, ctypes.c_int64]),
+    "vc_server_step": (ctypes.c_int, [_P, _P]),
+    "vc_server_counts": (ctypes.c_int, [_P, _P, _P, _P]),
+    "vc_server_poll": (ctypes.c_int, [_P, _I, _P, _P, _P, ctypes.c_int64]),
+    "vc_server_get_stats": (ctypes.c_int, [_P, _P]),
+    "vc_server_free": (None, [_P]),
 }
 
 

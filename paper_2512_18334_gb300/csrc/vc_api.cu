@@ -29,56 +29,6 @@ namespace {
         }                                                            \
     } while (0)
 
-cudaError_t &last_cuda_error()
-{
-    static thread_local cudaError_t e = cudaSuccess;
-    return e;
-}
-
-// Growable device buffer.
-struct DevBuf {
-    void *p = nullptr;
-    size_t bytes = 0;
-    int ensure(size_t want)
-    {
-        if (want <= bytes) return VC_OK;
-        if (p) cudaFree(p);
-        p = nullptr;
-        bytes = 0;
-        if (cudaMalloc(&p, want) != cudaSuccess) return VC_ENOMEM;
-        bytes = want;
-        return VC_OK;
-    }
-    void release()
-    {
-        if (p) cudaFree(p);
-        p = nullptr;
-        bytes = 0;
-    }
-    template <class X>
-    X *as() const { return (X *)p; }
-};
-
-struct HostBuf {
-    void *p = nullptr;
-    size_t bytes = 0;
-    int ensure(size_t want)
-    {
-        if (want <= bytes) return VC_OK;
-        if (p) cudaFreeHost(p);
-        p = nullptr;
-        bytes = 0;
-        if (cudaMallocHost(&p, want) != cudaSuccess) return VC_ENOMEM;
-        bytes = want;
-        return VC_OK;
-    }
-    void release()
-    {
-        if (p) cudaFreeHost(p);
-        p = nullptr;
-        bytes = 0;
-    }
-};
 
 // Search workspace: node slots, worklist, registry, scratch, control block.
 struct Workspace {

@@ -72,11 +72,28 @@ struct QueryDesc {
     int cover_len;       // entries written to cover_list
     int done;            // set once when the query is finished during the search
     int rounds;          // root-phase rule rounds (diagnostics)
-    int pad2;
+    int gen;             // generation of the query slot (served requests): node
+                         // headers carry it; a node whose generation differs
+                         // belongs to an earlier request of the slot and is dropped
     long long root_cycles[4];  // clock64 cycles: phase 1, greedy, phase 2, induce
     long long nodes;     // search-tree nodes spent on this query
     long long budget;    // node budget of this query (0: none)
     int *cover_list;     // ascending original ids (device, >= n)
+};
+
+// One served request as seen after a time slice, written by the device into
+// mapped host memory.
+struct RetireRec {
+    int slot;
+    int state;             // 0: still searching; 1: finished (fields below valid)
+    int status;
+    int result;
+    int yes;
+    int cover_len;
+    long long cover_off;   // offset in the cover buffer, -1: buffer full (retry)
+    long long nodes;
+    int np;
+    int pad;
 };
 
 // ------------------------------------------------------------------ nodes
@@ -90,7 +107,8 @@ struct NodeHdr {            // 64 bytes; the payload after it stays 16-aligned
     int32_t q;              // query id
     int32_t cov_empty;      // 1: cover bitmap not stored (all zero)
     int32_t depth;          // search-tree depth (statistics only)
-    int32_t pad[6];
+    int32_t gen;            // generation of the query slot when the node was made
+    int32_t pad[5];
 };
 static_assert(sizeof(NodeHdr) == 64, "node header must stay 64 bytes");
 
@@ -152,6 +170,11 @@ struct SearchParams {
     int csr_smem;             // >0: the (single) query's induced CSR is staged in shared
                               // memory (this many bytes at the start of each block's region)
     int csr_query;            // the query whose CSR is staged
+    long long quantum_ns;     // >0: time slice; each worker stores its node and
+                              // exits once this long has passed since it started
+    int *stack_top;           // non-null: per-worker private stack depth, read at
+                              // start and written at exit (the stacks stay resident
+                              // between slices)
 };
 
 // Control block: one unsigned long long per entry, each entry on its own

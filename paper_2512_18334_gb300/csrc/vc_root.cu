@@ -1306,12 +1306,9 @@ __global__ void __launch_bounds__(kRootThreads, 1) root_cluster_kernel(QueryDesc
 // Assemble each query's cover in original ids: the root-forced vertices plus
 // the witness of the induced graph's registry entry when the search improved
 // on the bound; otherwise the root phase's cover (greedy or forced set).
-__global__ void __launch_bounds__(kRootThreads) finalize_kernel(QueryDesc *qs, const RegEntry *reg,
-                                                                 const uint32_t *reg_words, int wcap)
+// Called by every thread of the block.
+__device__ void finalize_query(QueryDesc &Q, const RegEntry *reg, const uint32_t *reg_words, int wcap, int *red)
 {
-    __shared__ int red[33];
-    QueryDesc &Q = qs[blockIdx.x];
-    if (Q.status != VC_OK) return;
     const int n = Q.n;
     if (!Q.answered) {
         const RegEntry &R = reg[Q.root_entry];
@@ -1349,6 +1346,97 @@ __global__ void __launch_bounds__(kRootThreads) finalize_kernel(QueryDesc *qs, c
         for (int v = beg; v < end; v++)
             if (Q.cover_flags[v]) Q.cover_list[off++] = v;
     if (threadIdx.x == 0) Q.cover_len = emit ? tot : 0;
+}
+
+__global__ void __launch_bounds__(kRootThreads) finalize_kernel(QueryDesc *qs, const RegEntry *reg,
+                                                                 const uint32_t *reg_words, int wcap)
+{
+    __shared__ int red[33];
+    QueryDesc &Q = qs[blockIdx.x];
+    if (Q.status != VC_OK) return;
+    finalize_query(Q, reg, reg_words, wcap, red);
+}
+
+// ------------------------------------------------------------ served requests
+
+// One block per staged request: the CSR checks of vc_load_csr (row pointers
+// non-decreasing from 0 to 2|E|; each entry in range, not a self-loop,
+// strictly ascending in its row and mirrored in the other row).  A failure
+// sets the request's status to VC_EINVAL.
+__global__ void __launch_bounds__(kRootThreads) serve_validate_kernel(QueryDesc *qs)
+{
+    QueryDesc &Q = qs[blockIdx.x];
+    const int n = Q.n, m2 = Q.m2;
+    const int *rp = Q.rp, *col = Q.col;
+    int bad = 0;
+    if (threadIdx.x == 0) bad = n < 0 || m2 < 0 || (n == 0 && m2 != 0) || (n > 0 && (rp[0] != 0 || rp[n] != m2));
+    for (int v = threadIdx.x; v < n && !bad; v += blockDim.x)
+        if (rp[v] > rp[v + 1]) bad = 1;
+    bad = __syncthreads_or(bad);
+    if (!bad) {
+        for (int e = threadIdx.x; e < m2 && !bad; e += blockDim.x) {
+            int lo = 0, hi = n - 1;                // the row of e: last v with rp[v] <= e
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (rp[mid] <= e) lo = mid; else hi = mid - 1;
+            }
+            const int v = lo, u = col[e];
+            if (u < 0 || u >= n || u == v || (e > rp[v] && col[e - 1] >= u)) { bad = 1; break; }
+            int a = rp[u], b = rp[u + 1] - 1;
+            bool found = false;
+            while (a <= b) {
+                const int mid = (a + b) >> 1, x = col[mid];
+                if (x == v) { found = true; break; }
+                if (x < v) a = mid + 1; else b = mid - 1;
+            }
+            if (!found) bad = 1;
+        }
+        bad = __syncthreads_or(bad);
+    }
+    if (bad && threadIdx.x == 0) Q.status = VC_EINVAL;
+}
+
+// One block per active slot (and at least one block): finished requests are
+// finalised and their covers appended to the mapped output buffer; block 0
+// copies the control block's entries out as well.
+__global__ void __launch_bounds__(kRootThreads) serve_retire_kernel(
+    QueryDesc *slots, const int *active, int nactive, const RegEntry *reg, const uint32_t *reg_words, int wcap,
+    RetireRec *rec, int *cover_out, long long cover_cap, unsigned long long *cover_ctr,
+    const unsigned long long *ctl, unsigned long long *ctl_out)
+{
+    __shared__ int red[33];
+    __shared__ long long s_off;
+    if (blockIdx.x == 0)
+        for (int i = threadIdx.x; i < kCtlEntries; i += blockDim.x) ctl_out[i] = ctl[i * kCtlStride];
+    if ((int)blockIdx.x >= nactive) return;
+    const int qi = active[blockIdx.x];
+    QueryDesc &Q = slots[qi];
+    RetireRec &R = rec[blockIdx.x];
+    if (!Q.done) {
+        if (threadIdx.x == 0) { R.slot = qi; R.state = 0; }
+        return;
+    }
+    const bool ok = Q.status == VC_OK;
+    if (ok) finalize_query(Q, reg, reg_words, wcap, red);
+    __syncthreads();
+    const int len = ok ? Q.cover_len : 0;
+    if (threadIdx.x == 0) s_off = len > 0 ? (long long)atomicAdd(cover_ctr, (unsigned long long)len) : 0;
+    __syncthreads();
+    const long long off = s_off;
+    const bool fits = off + len <= cover_cap;
+    if (fits)
+        for (int i = threadIdx.x; i < len; i += blockDim.x) cover_out[off + i] = Q.cover_list[i];
+    if (threadIdx.x == 0) {
+        R.slot = qi;
+        R.state = 1;
+        R.status = Q.status;
+        R.result = Q.result;
+        R.yes = Q.yes;
+        R.cover_len = len;
+        R.cover_off = fits ? off : -1;
+        R.nodes = Q.nodes;
+        R.np = Q.np;
+    }
 }
 
 }  // namespace vcg
@@ -1465,6 +1553,23 @@ cudaError_t finalize_run(QueryDesc *d_q, int nq, const RegEntry *reg, const uint
 {
     if (nq <= 0) return cudaSuccess;
     finalize_kernel<<<nq, kRootThreads, 0, s>>>(d_q, reg, reg_words, wcap);
+    return cudaGetLastError();
+}
+
+cudaError_t serve_validate_run(QueryDesc *d_staging, int na, cudaStream_t s)
+{
+    if (na <= 0) return cudaSuccess;
+    serve_validate_kernel<<<na, kRootThreads, 0, s>>>(d_staging);
+    return cudaGetLastError();
+}
+
+cudaError_t serve_retire_run(QueryDesc *d_slots, const int *active, int nactive, const RegEntry *reg,
+                             const uint32_t *reg_words, int wcap, RetireRec *rec, int *cover_out,
+                             long long cover_cap, unsigned long long *cover_ctr,
+                             const unsigned long long *ctl, unsigned long long *ctl_out, cudaStream_t s)
+{
+    serve_retire_kernel<<<nactive > 0 ? nactive : 1, kRootThreads, 0, s>>>(
+        d_slots, active, nactive, reg, reg_words, wcap, rec, cover_out, cover_cap, cover_ctr, ctl, ctl_out);
     return cudaGetLastError();
 }
 

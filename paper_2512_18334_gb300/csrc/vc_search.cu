@@ -57,6 +57,9 @@ struct Vec {
 __host__ __device__ inline int align_up(int x, int a) { return (x + a - 1) / a * a; }
 __host__ __device__ inline int align_down(int x, int a) { return x / a * a; }
 
+// Best value broadcast to the team when the time slice is over.
+constexpr int kPreempt = INT_MIN + 1;
+
 template <typename T>
 __host__ __device__ inline int deg_region_bytes(int ncap) { return align_up(ncap * (int)sizeof(T), 16); }
 
@@ -81,11 +84,13 @@ template <class X>
 __device__ __forceinline__ X vld(const X &x) { return *(volatile const X *)&x; }
 
 // Registry entries come from a per-worker free list first, then from a
-// global stack of free chunks (kChunk entries linked through `next`, chunks
-// linked through pad[0]), then from a global bump counter.  Freed entries go
-// to the freeing worker's list; when it reaches 2 * kChunk, kChunk of them go
-// back to the global stack as one chunk (one CAS per chunk, not per entry).
-// Only team leaders call these.
+// global stack of free chunks (entries linked through `next`, chunks linked
+// through pad[0] of their first entry, which also holds the chunk's size in
+// pad[1]), then from a global bump counter.  Freed entries go to the freeing
+// worker's list; when it reaches 2 * kChunk, kChunk of them go back to the
+// global stack as one chunk (one CAS per chunk, not per entry), and a worker
+// returns whatever its list holds when it exits (so that time slices of a
+// resident search lose nothing).  Only team leaders call these.
 constexpr int kChunk = 32;
 
 __device__ __forceinline__ unsigned long long cas_release_u64(unsigned long long *p, unsigned long long cmp,
@@ -113,10 +118,12 @@ __device__ int reg_chunk_pop(const SearchParams &P)
     return -1;   // contended: the caller falls back to the bump counter
 }
 
-// Push a chunk whose first entry is idx (its entries already linked).
-__device__ void reg_chunk_push(const SearchParams &P, int idx)
+// Push a chunk of cnt entries whose first entry is idx (already linked,
+// the last one's `next` is -1).
+__device__ void reg_chunk_push(const SearchParams &P, int idx, int cnt)
 {
     unsigned long long *head = &ctlw(P.ctl, kRegHead);
+    *(volatile int *)&P.reg[idx].pad[1] = cnt;
     for (int it = 0; it < (1 << 22); it++) {
         const unsigned long long h = ld_acquire_u64(head);
         *(volatile int *)&P.reg[idx].pad[0] = (int)(h & 0xffffffffull);
@@ -186,6 +193,7 @@ struct Worker {
     int q, np;
     const int *rp, *col;
     int S, comp, lo, hi, clo, chi, wlo, whi, depth;
+    int gen;          // generation of the node's query slot
     int cntbuf;       // double-buffer index of the mark counter
 
     // private stack
@@ -199,6 +207,8 @@ struct Worker {
     int qcur;
     long long bytes_local;   // this thread's share of the algorithmic bytes
     int max_top;
+    unsigned long long t_end;  // end of the time slice (leader; 0: none)
+    bool preempted;            // the slice ended: the node was stored, stop
 
     __device__ Worker(const SearchParams &p, Team<WT> t, int w, char *smem, const int *csr)
         : P(p), tm(t), wid(w), csr_s(csr)
@@ -212,7 +222,10 @@ struct Worker {
         sc = (int *)s;             s += 64;
         if constexpr (WT == 0) tm.red = (long long *)s;
         stack = P.stack_slots + (size_t)wid * P.stack_depth * P.slot_bytes;
-        top = 0;
+        top = P.stack_top ? P.stack_top[wid] : 0;
+        gen = 0;
+        t_end = 0;
+        preempted = false;
         nodes_local = 0;
         bytes_local = 0;
         qnodes = 0;
@@ -435,6 +448,7 @@ struct Worker {
             h->q = q;
             h->cov_empty = kind == 1;
             h->depth = depth + 1;
+            h->gen = gen;
         }
         uint4 *dst = (uint4 *)(slot + sizeof(NodeHdr));
         if (tm.leader())
@@ -471,6 +485,7 @@ struct Worker {
         // may have been written by another SM)
         S = __ldcg(&h->S); comp = __ldcg(&h->comp); wlo = __ldcg(&h->lo); whi = __ldcg(&h->hi);
         clo = __ldcg(&h->clo); chi = __ldcg(&h->chi); q = __ldcg(&h->q); depth = __ldcg(&h->depth);
+        gen = __ldcg(&h->gen);
         const int op = __ldcg(&h->op), cov_empty = __ldcg(&h->cov_empty);
         lo = wlo; hi = whi;
 #ifdef VC_CHECKS
@@ -647,7 +662,7 @@ struct Worker {
     {
         if (lf_head < 0) {
             const int c = reg_chunk_pop(P);
-            if (c >= 0) { lf_head = c; lf_count = kChunk; }
+            if (c >= 0) { lf_head = c; lf_count = *(volatile int *)&P.reg[c].pad[1]; }
         }
         if (lf_head >= 0) {
             const int e = lf_head;
@@ -672,7 +687,7 @@ struct Worker {
             lf_head = *(volatile int *)&P.reg[last].next;
             *(volatile int *)&P.reg[last].next = -1;
             lf_count -= kChunk;
-            reg_chunk_push(P, chunk);
+            reg_chunk_push(P, chunk, kChunk);
         }
     }
 
@@ -1234,13 +1249,24 @@ struct Worker {
     // Process the node now in shared memory and all its left descendants.
     __device__ void process()
     {
-        for (;;) {
-            nodes_local++;
-            qnodes++;
+        for (int iter = 0;; iter++) {
             int B = 0;
-            if (tm.leader()) B = aborted(P.ctl) ? INT_MIN : ld_relaxed(&P.reg[comp].val);
+            if (tm.leader()) {
+                if (aborted(P.ctl)) B = INT_MIN;
+                else if (iter > 0 && t_end && globaltimer() > t_end) B = kPreempt;
+                else B = ld_relaxed(&P.reg[comp].val);
+            }
             B = tm.bcast(B);
             if (B == INT_MIN) return;   // aborted (decided by the leader for the whole team)
+            if (B == kPreempt) {
+                // the slice is over: store this node (no pending operation) so
+                // that the next slice resumes it; it stays live in its context
+                push_child(0, -1, -1, clo, chi, comp, S, hi);
+                preempted = true;
+                return;
+            }
+            nodes_local++;
+            qnodes++;
             Stats st = reduce(B);
             if (st.pruned) {
                 if (tm.leader()) atomicAdd(&ctlw(P.ctl, kPruned), 1ull);
@@ -1322,13 +1348,15 @@ struct Worker {
 
     __device__ void run()
     {
+        if (P.quantum_ns > 0 && tm.leader()) t_end = globaltimer() + (unsigned long long)P.quantum_ns;
         unsigned long long idle_since = 0, seen_progress = ~0ull;
         int backoff = 32;
         // counters are flushed every 64 nodes, more often under a small node budget
         long long flush_every = 64;
         if (P.node_budget > 0) flush_every = max(1ll, min(64ll, P.node_budget / 64));
         for (;;) {
-            int ab = tm.leader() ? (int)aborted(P.ctl) : 0;
+            int ab = 0;
+            if (tm.leader()) ab = aborted(P.ctl) || (t_end && globaltimer() > t_end);
             if (tm.bcast(ab)) break;
             bool got = false;
             if (top > 0) {
@@ -1345,9 +1373,12 @@ struct Worker {
                     flush_query_nodes();
                     qcur = q;
                 }
-                int qd = tm.leader() ? (int)query_is_done(P, q) : 0;
-                if (tm.bcast(qd)) { tm.sync(); continue; }   // PVC answered meanwhile
+                // finished meanwhile (PVC answer, node budget), or a node of an
+                // earlier request of a recycled slot: drop it
+                int qd = tm.leader() ? (int)(query_is_done(P, q) || vld(P.queries[q].gen) != gen) : 0;
+                if (tm.bcast(qd)) { tm.sync(); continue; }
                 process();
+                if (preempted) break;
                 if (nodes_local - last_flush >= flush_every) flush_counters();
                 tm.sync();
                 continue;
@@ -1367,6 +1398,12 @@ struct Worker {
             if (stop) break;
         }
         flush_counters();
+        if (tm.leader()) {
+            if (lf_count > 0) reg_chunk_push(P, lf_head, lf_count);
+            lf_head = -1;
+            lf_count = 0;
+            if (P.stack_top) P.stack_top[wid] = top;
+        }
     }
 };
 
@@ -1455,7 +1492,7 @@ __global__ void search_roots_kernel(SearchParams P, const int *root_slot)
     NodeHdr *h = (NodeHdr *)s;
     if (threadIdx.x == 0) {
         h->S = 0; h->comp = qi; h->lo = 0; h->hi = np - 1; h->clo = 0; h->chi = np - 1;
-        h->op = -1; h->q = qi; h->cov_empty = 1; h->depth = 0;
+        h->op = -1; h->q = qi; h->cov_empty = 1; h->depth = 0; h->gen = Q.gen;
     }
     T *dd = (T *)(s + sizeof(NodeHdr));
     const int lim = align_up(np, V);
@@ -1471,6 +1508,81 @@ __global__ void search_roots_publish(SearchParams P, int nroots)
     ctlw(P.ctl, kWlTail) = (unsigned long long)nroots;
     ctlw(P.ctl, kWlCount) = (unsigned long long)nroots;
     ctlw(P.ctl, kRemaining) = (unsigned long long)nroots;
+}
+
+// Served requests (one block each): copy the root-reduced descriptor from the
+// staging array into its slot.  A request that still needs a search gets its
+// root registry entry (index = slot) and its root node in the shared
+// worklist, behind the nodes of the requests admitted earlier.  The search
+// kernel is not running meanwhile (the stream orders the launches), so the
+// worklist tickets are taken without contention.  A request whose induced
+// graph exceeds the resident node capacity or the degree type finishes with
+// VC_ECAPACITY; one settled by the root phase (or rejected) is done at once.
+template <typename T>
+__global__ void serve_place_kernel(SearchParams P, const QueryDesc *staging, const int *slot_idx, int max_np)
+{
+    __shared__ long long s_t;
+    __shared__ int s_ok;
+    constexpr int V = Vec<T>::kPer16;
+    const int qi = slot_idx[blockIdx.x];
+    QueryDesc &Q = P.queries[qi];
+    if (threadIdx.x == 0) {
+        Q = staging[blockIdx.x];
+        int ok = Q.status == VC_OK && !Q.answered && Q.np > 0;
+        const bool fits_t = sizeof(T) >= 4 || Q.maxdeg <= (int)((1u << (8 * sizeof(T))) - 1u);
+        if (ok && (Q.np > max_np || !fits_t)) {
+            Q.status = VC_ECAPACITY;
+            ok = 0;
+        }
+        Q.done = ok ? 0 : 1;
+        Q.nodes = 0;
+        if (ok) {
+            RegEntry &R = P.reg[qi];
+            R.val = Q.bound - Q.forced;
+            R.live = 1;
+            R.link = -1;
+            R.lock = 0;
+            R.has_w = 0;
+            R.wlo = 0;
+            R.nw = (Q.np - 1) / 32 + 1;
+            R.q = qi;
+            R.kind = 0;
+            R.next = -1;
+            Q.root_entry = qi;
+            Q.budget = P.node_budget;
+            const long long t = (long long)atomicAdd(&ctlw(P.ctl, kWlTail), 1ull);
+            const unsigned ws = (unsigned)t & (P.wl_cap - 1);
+            int it = 0;
+            while (ld_acquire_u32(&P.wl_seq[ws]) != (unsigned)t) {   // free once consumed
+                if (++it > (1 << 20)) { set_error(P.ctl, VC_ETIMEOUT, 21); ok = 0; break; }
+                __nanosleep(64);
+            }
+            s_t = t;
+        }
+        s_ok = ok;
+    }
+    __syncthreads();
+    if (!s_ok) return;
+    const long long t = s_t;
+    const unsigned ws = (unsigned)t & (P.wl_cap - 1);
+    char *s = P.wl_slots + (size_t)ws * P.slot_bytes;
+    const int np = Q.np;
+    if (threadIdx.x == 0) {
+        NodeHdr *h = (NodeHdr *)s;
+        h->S = 0; h->comp = qi; h->lo = 0; h->hi = np - 1; h->clo = 0; h->chi = np - 1;
+        h->op = -1; h->q = qi; h->cov_empty = 1; h->depth = 0; h->gen = Q.gen;
+    }
+    T *dd = (T *)(s + sizeof(NodeHdr));
+    const int lim = align_up(np, V);
+    for (int v = threadIdx.x; v < lim; v += blockDim.x)
+        dd[v] = v < np ? (T)(Q.rp2[v + 1] - Q.rp2[v]) : (T)0;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        st_release_u32(&P.wl_seq[ws], (unsigned)t + 1u);
+        atomicAdd(&ctlw(P.ctl, kWlCount), 1ull);
+        atomicAdd(&ctlw(P.ctl, kRemaining), 1ull);
+    }
 }
 
 }  // namespace vcg
@@ -1550,6 +1662,43 @@ static cudaError_t run_t(const SearchPlan &pl, SearchParams &P, const int *d_roo
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (ev1) cudaEventRecord(ev1, s);
     return cudaSuccess;
+}
+
+template <typename T>
+static cudaError_t slice_t(const SearchPlan &pl, const SearchParams &P, cudaStream_t s)
+{
+    if (pl.warp_team)
+        search_kernel<T, 1><<<pl.blocks, pl.threads, pl.smem, s>>>(P);
+    else
+        search_kernel<T, 0><<<pl.blocks, pl.threads, pl.smem, s>>>(P);
+    return cudaGetLastError();
+}
+
+cudaError_t search_slice_run(const SearchPlan &pl, const SearchParams &P, cudaStream_t s)
+{
+    switch (pl.dtype) {
+    case 1: return slice_t<uint8_t>(pl, P, s);
+    case 2: return slice_t<uint16_t>(pl, P, s);
+    default: return slice_t<uint32_t>(pl, P, s);
+    }
+}
+
+cudaError_t search_reset_run(const SearchParams &P, int first, cudaStream_t s)
+{
+    search_init_kernel<uint8_t><<<256, 256, 0, s>>>(P, first);
+    return cudaGetLastError();
+}
+
+cudaError_t serve_place_run(const SearchPlan &pl, const SearchParams &P, const QueryDesc *d_staging,
+                            const int *d_slot_idx, int na, int max_np, cudaStream_t s)
+{
+    if (na <= 0) return cudaSuccess;
+    switch (pl.dtype) {
+    case 1: serve_place_kernel<uint8_t><<<na, 256, 0, s>>>(P, d_staging, d_slot_idx, max_np); break;
+    case 2: serve_place_kernel<uint16_t><<<na, 256, 0, s>>>(P, d_staging, d_slot_idx, max_np); break;
+    default: serve_place_kernel<uint32_t><<<na, 256, 0, s>>>(P, d_staging, d_slot_idx, max_np); break;
+    }
+    return cudaGetLastError();
 }
 
 cudaError_t search_run(const SearchPlan &pl, SearchParams &P, const int *d_root_slot, int nq, int nroots,

@@ -91,3 +91,34 @@ def test_missing_library_fails_loudly(tmp_path, monkeypatch):
     monkeypatch.setattr(L, "_lib", None)
     with pytest.raises(ImportError):
         L.lib()
+
+
+def test_every_field_offset_matches_header(lib, tmp_path):
+    # each ctypes mirror against gcc's layout of the C declaration, field by field
+    structs = {"vc_options": lib.Options, "vc_stats": lib.Stats, "vc_server_config": lib.ServerConfig,
+               "vc_server_result": lib.ServerResult, "vc_server_stats": lib.ServerStats}
+    lines = []
+    for cname, cls in structs.items():
+        lines.append(f'  printf("%zu\\n", sizeof({cname}));')
+        for fname, _ in cls._fields_:
+            lines.append(f'  printf("%zu\\n", offsetof({cname}, {fname}));')
+    src = tmp_path / "fields.c"
+    src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "vc_gb300.h"\nint main(void) {\n'
+                   + "\n".join(lines) + "\n  return 0;\n}\n")
+    exe = tmp_path / "fields"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    vals = [int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True,
+                                           check=True).stdout.split()]
+    want = []
+    for cls in structs.values():
+        want.append(ctypes.sizeof(cls))
+        want.extend(getattr(cls, f).offset for f, _ in cls._fields_)
+    assert vals == want
+
+
+def test_server_config_default_without_gpu(lib):
+    c = lib.ServerConfig()
+    assert lib.lib().vc_server_config_default(ctypes.byref(c)) == 0
+    assert c.max_inflight == 1024 and c.max_induced == 2048 and c.quantum_us == 2000
+    assert c.dtype_bytes == 2 and c.use_components == 1 and c.arena_bytes == 2 << 30
+    assert lib.lib().vc_server_config_default(None) == -1
