@@ -182,7 +182,7 @@ def reference_main(args, rank, world):
         "e2e": {"value": round(value, 6), "unit": "graphs/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
-    print(json.dumps(line), flush=True)
+    print(json.dumps(line, default=_json_default), flush=True)
 
 
 # ------------------------------------------------------------------ our arm
@@ -273,6 +273,181 @@ def extra_workloads(vc, torch, stream, peak):
         "batched_nodes_per_s": round(bst["nodes"] / (bms / 1e3), 1)}
     for d in dms:
         d.close()
+    return out
+
+
+def _log(msg):
+    print(f"[bench] {msg}", file=sys.stderr, flush=True)
+
+
+def _json_default(o):
+    """numpy scalars in the JSON line."""
+    if hasattr(o, "item"):
+        return o.item()
+    raise TypeError(f"not JSON serializable: {type(o).__name__}")
+
+
+def cover_ok(g, cover) -> bool:
+    """Every edge has an end in the cover (a plain edge check, no solver)."""
+    flags = np.zeros(max(g.n, 1), bool)
+    flags[np.asarray(cover, np.int64)] = True
+    src = np.repeat(np.arange(g.n), np.diff(g.row_ptr))
+    return bool(np.all(flags[src] | flags[g.col]))
+
+
+def extra_pvc_batch(vc, stream, count=4096, budget=200_000):
+    """4,096 graphs, n ~ U[40, 1500] (half G(n,p), half Chung-Lu 2.5), each
+    queried at k = opt (yes) and k = opt - 1 (no) in ONE persistent launch.
+    opt comes from a first batched MVC launch under the same per-query node
+    budget; graphs over budget there are dropped and counted."""
+    mix = gg.batch_pvc_mix(count, 11)
+    dms = [vc.Graph.from_csr(h.row_ptr, h.col, stream=stream) for h in mix]
+    t0 = time.perf_counter()
+    sizes, _, status, _, _ = vc.solve_batch(dms, node_budget=budget, want_covers=False, raise_on_error=False)
+    mvc_s = time.perf_counter() - t0
+    solved = [i for i in range(count) if status[i] == 0]
+    qg = [dms[i] for i in solved] * 2
+    ks = [int(sizes[i]) for i in solved] + [int(sizes[i]) - 1 for i in solved]
+    vc.solve_batch(qg[:64], ks[:64], node_budget=budget, raise_on_error=False)
+    t0 = time.perf_counter()
+    psz, pyes, pst, covers, bst = vc.solve_batch(qg, ks, node_budget=budget, raise_on_error=False)
+    batch_s = time.perf_counter() - t0
+    ns = len(solved)
+    ok = pst == 0
+    wrong = int(np.sum(ok[:ns] & ~pyes[:ns])) + int(np.sum(ok[ns:] & pyes[ns:]))
+    bad_cover = sum(1 for j in range(ns) if ok[j] and not cover_ok(mix[solved[j]], covers[j]))
+    # plain: one launch per query on a sample of the same queries
+    rng = np.random.default_rng(3)
+    sample = rng.choice(len(qg), size=min(512, len(qg)), replace=False)
+    t0 = time.perf_counter()
+    plain_ok = 0
+    for j in sample:
+        try:
+            y, _, _ = vc.solve_k(qg[j], ks[j], node_budget=budget, want_cover=True)
+            plain_ok += int(y == (int(j) < ns))
+        except vc.VcError:
+            pass
+    plain_s = time.perf_counter() - t0
+    for d in dms:
+        d.close()
+    return {"graphs": count, "node_budget_per_query": budget, "mvc_launch_s": round(mvc_s, 3),
+            "dropped_over_budget_in_mvc": count - ns, "queries": len(qg),
+            "batched_queries_per_s": round(int(ok.sum()) / batch_s, 1), "batched_s": round(batch_s, 3),
+            "batched_over_budget": int((pst == vc.VC_EBUDGET).sum()), "wrong_answers": wrong,
+            "covers_failing_edge_check": bad_cover, "batched_nodes_per_s": round(bst["nodes"] / batch_s, 1),
+            "plain_sample": len(sample), "plain_queries_per_s": round(len(sample) / plain_s, 1),
+            "plain_matching_answers": plain_ok}
+
+
+def extra_component_heavy_full(vc, stream, peak, budget=100_000_000):
+    """The component-heavy shape at full size (256 copies of G(48, 0.12) on a
+    32-vertex chain, about 12.3k vertices) under a node budget: it does not
+    finish within it, so this measures the search rate and its roofline."""
+    g = gg.component_heavy(0, copies=256, copy_n=48, p=0.12, chain=32)
+    d = vc.Graph.from_csr(g.row_ptr, g.col, stream=stream)
+    try:
+        size, _, st = vc.solve_min(d, node_budget=budget)
+        status = 0
+    except vc.VcError as e:
+        size, st, status = -1, e.stats, e.status
+    d.close()
+    ms = st["ms_search"]
+    gbs = st["search_bytes"] / (ms / 1e3) / 1e9 if ms > 0 else 0.0
+    return {"n": g.n, "n_induced": st["n_induced"], "status": status, "answer": size, "node_budget": budget,
+            "nodes": st["nodes"], "ms_search_kernel": round(ms, 3),
+            "nodes_per_s": round(st["nodes"] / (ms / 1e3), 1) if ms > 0 else None,
+            "component_branches": st["component_branches"], "workers": st["workers"], "team": st["team"],
+            "search_roofline": {"bound": "hbm", "kernel": "search_kernel", "achieved": round(gbs, 3),
+                                "peak": peak, "unit": "GB/s", "frac": round(gbs / peak, 6),
+                                "bytes_per_node": round(st["search_bytes"] / max(1, st["nodes"]), 1)}}
+
+
+def _pct(xs, q):
+    return round(float(np.percentile(xs, q)), 3) if len(xs) else None
+
+
+def extra_served_stream(vc, stream, count=1000, rates=(250.0, 1000.0, 4000.0), budget=100_000, seed=5):
+    """Served stream: Chung-Lu requests (n log-uniform on [30, 20000],
+    exponent U[2.2, 3.0], mean degree U[4, 10], maximum degree n / 4) with
+    Poisson arrivals, at each offered rate.  Served: requests are submitted
+    at their arrival times and the server is stepped continuously (real
+    time).  Plain: one vc_load_csr + vc_solve_min + vc_free per request, FIFO;
+    each request's service time is measured and its latency follows from the
+    single-server queue (finish = max(arrival, previous finish) + service).
+    Latency = retirement - arrival."""
+    tg = time.perf_counter()
+    t_unit, specs = gg.stream_requests(count, seed, 1.0)
+    graphs = [gg.chung_lu(n, gam, d, max(4.0, n / 4.0), s) for (n, gam, d, s) in specs]
+    _log(f"served_stream: {count} graphs generated in {time.perf_counter() - tg:.1f} s")
+    srv = vc.Server(stream=stream, node_budget=budget)
+    for g in graphs[:32]:                       # warm-up
+        srv.submit(g.row_ptr, g.col)
+    srv.drain()
+    out = {"requests": count, "node_budget_per_request": budget, "rates": []}
+    served_ans = None
+    for rate in rates:
+        arr = np.asarray(t_unit) / rate
+        lat = np.zeros(count)
+        ans = {}
+        t0 = time.perf_counter()
+        i = 0
+        while len(ans) < count:
+            now = time.perf_counter() - t0
+            while i < count and arr[i] <= now:
+                srv.submit(graphs[i].row_ptr, graphs[i].col, tag=i)
+                i += 1
+            q, f, _ = srv.counts()
+            if q or f:
+                srv.step()
+            elif i < count:
+                time.sleep(max(0.0, min(arr[i] - now, 0.002)))
+            for r in srv.poll():
+                j = r["tag"]
+                lat[j] = (time.perf_counter() - t0) - arr[j]
+                ans[j] = (r["status"], r["size"], r["n_induced"])
+        wall = time.perf_counter() - t0
+        _log(f"served_stream: rate {rate}/s served in {wall:.2f} s")
+        served_ans = ans
+        okm = np.array([ans[j][0] == 0 for j in range(count)])
+        out["rates"].append({"offered_per_s": rate, "served_graphs_per_s": round(count / wall, 1),
+                             "served_wall_s": round(wall, 3), "ok": int(okm.sum()),
+                             "over_budget": int(sum(ans[j][0] == vc.VC_EBUDGET for j in range(count))),
+                             "over_capacity": int(sum(ans[j][0] == vc.VC_ECAPACITY for j in range(count))),
+                             "p50_ms": _pct(lat * 1e3, 50), "p95_ms": _pct(lat * 1e3, 95),
+                             "p99_ms": _pct(lat * 1e3, 99)})
+    sst = srv.stats()
+    srv.close()
+    # plain per-graph launches: service times
+    service = np.zeros(count)
+    plain_ans = {}
+    for j, g in enumerate(graphs):
+        t0 = time.perf_counter()
+        d = vc.Graph.from_csr(g.row_ptr, g.col, stream=stream)
+        try:
+            size, _, _ = vc.solve_min(d, node_budget=budget)
+            plain_ans[j] = (0, size)
+        except vc.VcError as e:
+            plain_ans[j] = (e.status, -1)
+        d.close()
+        service[j] = time.perf_counter() - t0
+    _log(f"served_stream: plain service total {service.sum():.2f} s")
+    for k, rate in enumerate(rates):
+        arr = np.asarray(t_unit) / rate
+        fin = np.zeros(count)
+        prev = 0.0
+        for j in range(count):
+            prev = max(arr[j], prev) + service[j]
+            fin[j] = prev
+        lat = fin - arr
+        out["rates"][k].update({"plain_graphs_per_s": round(count / (fin[-1] - arr[0]), 1),
+                                "plain_p50_ms": _pct(lat * 1e3, 50), "plain_p95_ms": _pct(lat * 1e3, 95),
+                                "plain_p99_ms": _pct(lat * 1e3, 99)})
+    both = [j for j in range(count) if served_ans[j][0] == 0 and plain_ans[j][0] == 0]
+    out["answers_compared"] = len(both)
+    out["answers_differing"] = sum(served_ans[j][1] != plain_ans[j][1] for j in both)
+    out["plain_service_s"] = round(float(service.sum()), 3)
+    out["server"] = {k: sst[k] for k in ("workers", "team", "dtype_bytes", "max_induced", "slices", "steps",
+                                         "nodes", "ms_search", "ms_admit", "ms_retire", "resets")}
     return out
 
 
@@ -388,7 +563,20 @@ def ours_main(args, rank, world, local_rank):
 
     also = None
     if rank == 0 and not args.no_extra:
-        also = extra_workloads(vc, torch, stream, peak)
+        legs = [("small_graphs", lambda: extra_workloads(vc, torch, stream, peak)),
+                ("served_stream", lambda: extra_served_stream(vc, stream, count=args.stream_requests)),
+                ("pvc_batch_4096", lambda: extra_pvc_batch(vc, stream)),
+                ("component_heavy_256x48", lambda: extra_component_heavy_full(vc, stream, peak))]
+        also = {}
+        for name, fn in legs:
+            t0 = time.perf_counter()
+            r = fn()
+            r["wall_s"] = round(time.perf_counter() - t0, 2)
+            if name == "small_graphs":
+                also.update(r)
+            else:
+                also[name] = r
+            print(f"[bench] {name}: {json.dumps(r, default=_json_default)}", file=sys.stderr, flush=True)
 
     if rank == 0:
         line = {
@@ -413,7 +601,7 @@ def ours_main(args, rank, world, local_rank):
             "gpu_launches": launches,
             "also": also,
         }
-        print(json.dumps(line), flush=True)
+        print(json.dumps(line, default=_json_default), flush=True)
     dg.close()
     if world > 1:
         torch.distributed.destroy_process_group()
@@ -428,6 +616,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the context workloads")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="chung_lu_50k")
+    ap.add_argument("--stream-requests", type=int, default=1000,
+                    help="requests in the served-stream context measurement")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     global WORKLOAD

@@ -270,6 +270,10 @@ typedef struct vc_server_stats {
     int32_t workers, team, dtype_bytes, max_induced;
     int32_t slot_bytes, max_stack;
     int64_t device_bytes;      /* device memory held by the server */
+    int64_t wait_polls;        /* polls of worklist sequence words (contention) */
+    int64_t preemptions;       /* nodes stored at the end of a time slice */
+    int64_t max_node_ns;       /* longest single node (with its left descendants) in the last slice */
+    int64_t max_exit_ns;       /* longest worker exit phase in the last slice */
 } vc_server_stats;
 
 /* Fill *cfg with the defaults. */

@@ -142,6 +142,10 @@ class ServerStats(ctypes.Structure):
         ("slot_bytes", ctypes.c_int32),
         ("max_stack", ctypes.c_int32),
         ("device_bytes", ctypes.c_int64),
+        ("wait_polls", ctypes.c_int64),
+        ("preemptions", ctypes.c_int64),
+        ("max_node_ns", ctypes.c_int64),
+        ("max_exit_ns", ctypes.c_int64),
     ]
 
     def to_dict(self) -> dict:

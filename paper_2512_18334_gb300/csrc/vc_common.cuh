@@ -200,7 +200,11 @@ enum Ctl : int {
     kRegBump = 16,    // next never-used registry entry
     kHist = 17,       // kHistBins entries
     kBytes = 33,      // algorithmic bytes moved by the search (slots, CSR rows, bitmaps)
-    kCtlEntries = 34
+    kWaitIters = 34,  // polls spent waiting for worklist sequence words (diagnostics)
+    kPreempts = 35,   // nodes stored at the end of a time slice
+    kMaxProcNs = 36,  // longest single process() call (ns, diagnostics)
+    kMaxExitNs = 37,  // longest exit phase of a worker (ns, diagnostics)
+    kCtlEntries = 38
 };
 constexpr int kCtlStride = 16;
 constexpr int kCtlWords = kCtlEntries * kCtlStride;

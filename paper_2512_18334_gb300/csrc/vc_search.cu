@@ -476,16 +476,24 @@ struct Worker {
         }
     }
 
-    // Load a node from a slot into shared memory.
-    __device__ void read_slot(const char *slot)
+    // Load a node from a slot into shared memory.  Returns false, having
+    // read only the header, when the node's request is finished (PVC answer,
+    // node budget) or the node is left over from an earlier request of a
+    // recycled query slot: such a node must not be expanded, since its
+    // pending operation refers to a graph the slot may no longer hold.
+    __device__ bool read_slot(const char *slot)
     {
         constexpr int V = Vec<T>::kPer16;
         const NodeHdr *h = (const NodeHdr *)slot;
         // every thread reads the header (broadcast loads, L2 only: the slot
         // may have been written by another SM)
-        S = __ldcg(&h->S); comp = __ldcg(&h->comp); wlo = __ldcg(&h->lo); whi = __ldcg(&h->hi);
-        clo = __ldcg(&h->clo); chi = __ldcg(&h->chi); q = __ldcg(&h->q); depth = __ldcg(&h->depth);
+        q = __ldcg(&h->q);
         gen = __ldcg(&h->gen);
+        int stale = 0;
+        if (tm.leader()) stale = query_is_done(P, q) || vld(P.queries[q].gen) != gen;
+        if (tm.bcast(stale)) return false;
+        S = __ldcg(&h->S); comp = __ldcg(&h->comp); wlo = __ldcg(&h->lo); whi = __ldcg(&h->hi);
+        clo = __ldcg(&h->clo); chi = __ldcg(&h->chi); depth = __ldcg(&h->depth);
         const int op = __ldcg(&h->op), cov_empty = __ldcg(&h->cov_empty);
         lo = wlo; hi = whi;
 #ifdef VC_CHECKS
@@ -527,6 +535,7 @@ struct Worker {
             const int c = take_count();
             apply_marks(c);
         }
+        return true;
     }
 
     // ------------------------------------------------------------ worklist
@@ -551,6 +560,7 @@ struct Worker {
                     if (++it > (1 << 24) || aborted(P.ctl)) { set_error(P.ctl, VC_ETIMEOUT, 3); ok = 0; break; }
                     __nanosleep(32);
                 }
+                if (it) atomicAdd(&ctlw(P.ctl, kWaitIters), (unsigned long long)it);
             }
             sc[4] = ok;
             sc[5] = (int)(t & 0x7fffffff);
@@ -579,10 +589,11 @@ struct Worker {
         return P.wl_slots + (size_t)((unsigned)t & (P.wl_cap - 1)) * P.slot_bytes;
     }
 
-    // Try to take a node from the worklist into shared memory.  The item
-    // counter is only decremented while it is positive (read, then CAS), so
-    // idle workers polling an empty worklist never write to it.
-    __device__ bool wl_pop()
+    // Try to take a node from the worklist into shared memory: 0 nothing
+    // there, 1 node loaded, 2 a finished request's node taken and dropped.
+    // The item counter is only decremented while it is positive (read, then
+    // CAS), so idle workers polling an empty worklist never write to it.
+    __device__ int wl_pop()
     {
         int ok = 0;
         if (tm.leader()) {
@@ -600,6 +611,7 @@ struct Worker {
                     if (++it > (1 << 24) || aborted(P.ctl)) { set_error(P.ctl, VC_ETIMEOUT, 4); ok = 0; break; }
                     __nanosleep(32);
                 }
+                if (it) atomicAdd(&ctlw(P.ctl, kWaitIters), (unsigned long long)it);
                 sc[5] = (int)(t & 0x7fffffff);
                 sc[6] = (int)(t >> 31);
             }
@@ -609,14 +621,14 @@ struct Worker {
         ok = sc[4];
         const long long t = ((long long)sc[6] << 31) | (unsigned)sc[5];
         tm.sync();
-        if (!ok) return false;
-        read_slot(wl_slot(t));
+        if (!ok) return 0;
+        const bool loaded = read_slot(wl_slot(t));
         tm.sync();
         if (tm.leader()) {
             const unsigned slot = (unsigned)t & (P.wl_cap - 1);
             st_release_u32(&P.wl_seq[slot], (unsigned)t + (unsigned)P.wl_cap);
         }
-        return true;
+        return loaded ? 1 : 2;
     }
 
     // Store a child: the worklist when it is hungry (load balancing,
@@ -1262,6 +1274,7 @@ struct Worker {
                 // the slice is over: store this node (no pending operation) so
                 // that the next slice resumes it; it stays live in its context
                 push_child(0, -1, -1, clo, chi, comp, S, hi);
+                if (tm.leader()) atomicAdd(&ctlw(P.ctl, kPreempts), 1ull);
                 preempted = true;
                 return;
             }
@@ -1358,26 +1371,34 @@ struct Worker {
             int ab = 0;
             if (tm.leader()) ab = aborted(P.ctl) || (t_end && globaltimer() > t_end);
             if (tm.bcast(ab)) break;
-            bool got = false;
+            // 0 nothing, 1 node loaded, 2 node of a finished request (or of an
+            // earlier request of a recycled slot) dropped unexpanded
+            int got = 0;
             if (top > 0) {
                 top--;
-                read_slot(stack_slot(top));
-                got = true;
+                got = read_slot(stack_slot(top)) ? 1 : 2;
             } else {
                 got = wl_pop();
             }
-            if (got) {
+            if (got == 2) {
+                backoff = 32;
+                idle_since = 0;
+                tm.sync();
+                continue;
+            }
+            if (got == 1) {
                 backoff = 32;
                 idle_since = 0;
                 if (q != qcur) {
                     flush_query_nodes();
                     qcur = q;
                 }
-                // finished meanwhile (PVC answer, node budget), or a node of an
-                // earlier request of a recycled slot: drop it
-                int qd = tm.leader() ? (int)(query_is_done(P, q) || vld(P.queries[q].gen) != gen) : 0;
-                if (tm.bcast(qd)) { tm.sync(); continue; }
+                const unsigned long long tp = tm.leader() ? globaltimer() : 0ull;
                 process();
+                if (tm.leader()) {
+                    const unsigned long long dt = globaltimer() - tp;
+                    if (dt > 100000ull) atomicMax(&ctlw(P.ctl, kMaxProcNs), dt);
+                }
                 if (preempted) break;
                 if (nodes_local - last_flush >= flush_every) flush_counters();
                 tm.sync();
@@ -1397,12 +1418,14 @@ struct Worker {
             stop = tm.bcast(stop);
             if (stop) break;
         }
+        const unsigned long long tx = tm.leader() ? globaltimer() : 0ull;
         flush_counters();
         if (tm.leader()) {
             if (lf_count > 0) reg_chunk_push(P, lf_head, lf_count);
             lf_head = -1;
             lf_count = 0;
             if (P.stack_top) P.stack_top[wid] = top;
+            atomicMax(&ctlw(P.ctl, kMaxExitNs), globaltimer() - tx);
         }
     }
 };

@@ -144,6 +144,7 @@ struct vc_server {
     vc_server_stats st{};
     unsigned long long snap[kCtlEntries] = {};   // control words after the last step
     long long base_nodes = 0, base_bytes = 0;    // counters accumulated before resets
+    long long base_waits = 0, base_preempts = 0;
     bool dirty = false;                          // resident state holds work of earlier requests
     std::chrono::steady_clock::time_point t0;
 
@@ -172,6 +173,8 @@ int reset_state(vc_server *s)
 {
     s->base_nodes += (long long)s->snap[kNodes];
     s->base_bytes += (long long)s->snap[kBytes];
+    s->base_waits += (long long)s->snap[kWaitIters];
+    s->base_preempts += (long long)s->snap[kPreempts];
     SV_CK(search_reset_run(s->P, s->cfg.max_inflight, s->stream));
     SV_CK(cudaMemsetAsync(s->stack_top.p, 0, s->stack_top.bytes, s->stream));
     memset(s->snap, 0, sizeof(s->snap));
@@ -326,6 +329,8 @@ int step(vc_server *s, int *completed)
     if (nact == 0) return VC_OK;
     const bool slice = na > 0 || s->snap[kRemaining] > 0;
     if (slice) {
+        SV_CK(cudaMemsetAsync(&ctlw(s->P.ctl, kMaxProcNs), 0, 8, st));
+        SV_CK(cudaMemsetAsync(&ctlw(s->P.ctl, kMaxExitNs), 0, 8, st));
         SV_CK(cudaEventRecord(s->ev[2], st));
         SV_CK(search_slice_run(s->pl, s->P, st));
         SV_CK(cudaEventRecord(s->ev[3], st));
@@ -593,6 +598,10 @@ int vc_server_get_stats(const vc_server *s, vc_server_stats *st)
     *st = s->st;
     st->nodes = s->base_nodes + (long long)s->snap[kNodes];
     st->search_bytes = s->base_bytes + (long long)s->snap[kBytes];
+    st->wait_polls = s->base_waits + (long long)s->snap[kWaitIters];
+    st->preemptions = s->base_preempts + (long long)s->snap[kPreempts];
+    st->max_node_ns = (long long)s->snap[kMaxProcNs];
+    st->max_exit_ns = (long long)s->snap[kMaxExitNs];
     return VC_OK;
 }
 

@@ -194,3 +194,28 @@ def test_slot_recycling_after_requests_that_leave_nodes(vc):
             assert r["status"] == vc.VC_OK and r["size"] == opts[i]
             verify(graphs[i], r)
     srv.close()
+
+
+def test_leftover_nodes_are_never_expanded_against_a_new_graph(vc):
+    # One slot.  A hard request stops on its node budget with right children
+    # (pending "remove N(v)" operations over its own 80-vertex graph) left in
+    # the stacks and the worklist; the slot then holds tiny graphs.  Expanding
+    # a leftover node against the new graph would read rows that do not exist
+    # there and run for seconds; it must be dropped unexpanded instead.
+    srv = vc.Server(max_inflight=1, node_budget=3000, quantum_us=200)
+    hard = gg.gnm(80, 260, 11)
+    tiny = [gg.gnm(12, 20, s) for s in range(6)]
+    plan = []
+    for g in tiny:
+        plan.append((srv.submit(hard.row_ptr, hard.col), None))
+        plan.append((srv.submit(g.row_ptr, g.col), g))
+    res = {r["tag"]: r for r in srv.drain()}
+    for tag, g in plan:
+        if g is None:
+            assert res[tag]["status"] in (vc.VC_EBUDGET, vc.VC_OK)
+            continue
+        assert res[tag]["status"] == vc.VC_OK and res[tag]["size"] == opt_of(g)
+        verify(g, res[tag])
+    st = srv.stats()
+    assert st["ms_search"] / max(1, st["slices"]) < 20.0     # slices end at their deadline
+    srv.close()
