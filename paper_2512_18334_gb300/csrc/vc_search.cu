@@ -1432,8 +1432,11 @@ struct Worker {
 
 // ---------------------------------------------------------------- kernels
 
+// Register caps keep the occupancy the planner counts on: block workers fit
+// two 512-thread (four 256-thread) blocks per SM, warp workers three blocks
+// of eight warps.
 template <typename T, int WT>
-__global__ void search_kernel(const __grid_constant__ SearchParams P)
+__global__ void __launch_bounds__(WT ? 256 : 1024, WT ? 3 : 1) search_kernel(const __grid_constant__ SearchParams P)
 {
     extern __shared__ __align__(16) char smem_all[];
     // single-query launches keep the induced CSR (row pointers, then
