@@ -362,6 +362,44 @@ def extra_component_heavy_full(vc, stream, peak, budget=100_000_000):
                                 "bytes_per_node": round(st["search_bytes"] / max(1, st["nodes"]), 1)}}
 
 
+def extra_ablation(vc, stream, budget=200_000_000):
+    """The paper's ablation (Tables 2-4, Figure 4) on synthetic graphs: each
+    optimisation switched off in turn, under a node budget (a run over it is
+    reported with status VC_EBUDGET and the nodes it visited), plus the
+    execution-time breakdown of the full method."""
+    cases = {"component_heavy_8x48": gg.component_heavy(1, copies=8, copy_n=48, p=0.12, chain=2),
+             "gnm_40_90_x100": gg.disjoint_union([gg.gnm(40, 90, 500 + s) for s in range(100)])}
+    variants = [("all_on", dict(breakdown=1)), ("components_off", dict(use_components=0)),
+                ("root_reduction_off", dict(disable_root_rules=1)), ("bounds_off", dict(disable_bounds=1)),
+                ("load_balance_off", dict(load_balance=0))]
+    out = {}
+    for name, g in cases.items():
+        d = vc.Graph.from_csr(g.row_ptr, g.col, stream=stream)
+        vc.solve_min(d)
+        rows = {}
+        for vname, kw in variants:
+            t0 = time.perf_counter()
+            try:
+                size, _, st = vc.solve_min(d, node_budget=budget, want_cover=False, **kw)
+                status = 0
+            except vc.VcError as e:
+                size, st, status = -1, e.stats, e.status
+            wall = time.perf_counter() - t0
+            row = {"status": status, "answer": size, "s": round(wall, 4), "nodes": st["nodes"],
+                   "component_branches": st["component_branches"], "comp_hist": st["comp_hist"],
+                   "vertices_in_degree_array": st["n_induced"], "dtype_bytes": st["dtype_bytes"],
+                   "workers": st["workers"], "team": st["team"],
+                   "bytes_per_node": round(st["search_bytes"] / max(1, st["nodes"]), 1)}
+            if kw.get("breakdown"):
+                ph = st["phase_cycles"]
+                tot = sum(ph.values())
+                row["breakdown"] = {k: round(v / tot, 4) for k, v in ph.items()} if tot else None
+            rows[vname] = row
+        d.close()
+        out[name] = {"n": g.n, "node_budget": budget, "runs": rows}
+    return out
+
+
 def _pct(xs, q):
     return round(float(np.percentile(xs, q)), 3) if len(xs) else None
 
@@ -566,7 +604,8 @@ def ours_main(args, rank, world, local_rank):
         legs = [("small_graphs", lambda: extra_workloads(vc, torch, stream, peak)),
                 ("served_stream", lambda: extra_served_stream(vc, stream, count=args.stream_requests)),
                 ("pvc_batch_4096", lambda: extra_pvc_batch(vc, stream)),
-                ("component_heavy_256x48", lambda: extra_component_heavy_full(vc, stream, peak))]
+                ("component_heavy_256x48", lambda: extra_component_heavy_full(vc, stream, peak)),
+                ("ablation", lambda: extra_ablation(vc, stream))]
         also = {}
         for name, fn in legs:
             t0 = time.perf_counter()

@@ -47,8 +47,11 @@ extern "C" {
 
 typedef struct vc_graph vc_graph;
 
-/* Solver options.  Zero-initialised fields mean "automatic / default";
- * vc_options_default() fills the defaults explicitly. */
+/* Solver options.  Start from vc_options_default().  For team, dtype_bytes,
+ * stack_depth, worklist_capacity, registry_capacity, idle_timeout_ms and
+ * node_budget, 0 means automatic / the default; use_components and
+ * load_balance are 1 in the defaults (0 switches them off); the ablation
+ * switches are 0 (off) in the defaults. */
 typedef struct vc_options {
     int32_t use_components;   /* 1: branch on components (Algorithm 2); 0: Algorithm 1 */
     int32_t team;             /* threads per worker: 0 auto, 32 (one warp per
@@ -63,6 +66,13 @@ typedef struct vc_options {
                                  any worker making progress; 0 = 60000              */
     int64_t node_budget;      /* 0 = unlimited; else a query that needs more search-tree
                                  nodes stops with VC_EBUDGET (per query in a batch) */
+    /* Ablations of the paper's optimisations (answers do not change): */
+    int32_t disable_bounds;   /* 1: every node keeps the whole degree array as its
+                                 window instead of the non-zero bounds (Section 4.3) */
+    int32_t disable_root_rules; /* 1: no reduction at the root (Section 4.2): the
+                                 search starts from every vertex that has an edge */
+    int32_t breakdown;        /* 1: count SM cycles per activity (vc_stats.phase_cycles) */
+    int32_t reserved;
 } vc_options;
 
 /* What a solve did.  All counters are totals over the launch. */
@@ -93,6 +103,11 @@ typedef struct vc_stats {
                                    bound, greedy bound, rules with the bound, induce */
     int64_t search_bytes;       /* algorithmic bytes the search moved: node slots
                                    read and written, CSR rows read, witness bitmaps */
+    int64_t phase_cycles[6];    /* with opt.breakdown: SM cycles summed over workers,
+                                   per activity: take a node from the stack or the
+                                   worklist, reduction rules, components (finding,
+                                   registering, closing cliques and cycles), vertex
+                                   branch, completion through the registry, idle */
 } vc_stats;
 
 /* Fill *opt with the defaults. */
@@ -187,6 +202,15 @@ int vc_root_reduce_static(int32_t n, int32_t m2, const int32_t *d_row_ptr, const
                           int32_t k, int32_t *d_forced, int32_t *d_induced_row_ptr,
                           int32_t *d_induced_col, int32_t *d_induced_orig, int32_t *d_info,
                           void *cuda_stream);
+
+/* Exact maximum independent set: the complement of a minimum vertex cover
+ * (the paper notes that its techniques carry over; related work, "Independent
+ * set").  Writes the
+ * maximum size n - OPT to *set_size and, when `set` is non-NULL, an
+ * independent set of that size (ascending original ids, capacity n) and its
+ * length to *set_len.  Same options, statistics and errors as vc_solve_min. */
+int vc_solve_mis(vc_graph *g, const vc_options *opt, int32_t *set_size, int32_t *set,
+                 int32_t *set_len, vc_stats *stats);
 
 /* Release the handle and all device memory it owns.  NULL is a no-op. */
 void vc_free(vc_graph *g);

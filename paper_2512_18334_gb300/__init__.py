@@ -26,7 +26,7 @@ from ._lib import (VC_OK, VC_EINVAL, VC_ENOMEM, VC_ECAPACITY, VC_ETIMEOUT, VC_EC
                    VcError, Options, Stats, ServerConfig, ServerResult, ServerStats, lib_path)
 
 __all__ = [
-    "Graph", "solve_min", "solve_k", "solve_batch", "options", "Server", "VcError", "lib_path",
+    "Graph", "solve_min", "solve_k", "solve_mis", "solve_batch", "options", "Server", "VcError", "lib_path",
     "VC_OK", "VC_EINVAL", "VC_ENOMEM", "VC_ECAPACITY", "VC_ETIMEOUT", "VC_ECUDA", "VC_EBUDGET",
 ]
 
@@ -130,6 +130,20 @@ def solve_k(g: Graph, k: int, opts: Options | None = None, want_cover: bool = Tr
                                  cover.ctypes.data_as(ctypes.c_void_p) if want_cover else None,
                                  ctypes.byref(clen), ctypes.byref(st)), st)
     return bool(yes.value), (cover[:clen.value].copy() if want_cover and yes.value else None), st.to_dict()
+
+
+def solve_mis(g: Graph, opts: Options | None = None, want_set: bool = True, **kw):
+    """Exact maximum independent set (complement of a minimum cover):
+    (size, vertex int32 array or None, stats dict)."""
+    o = _opts(opts, kw)
+    size = ctypes.c_int32(-1)
+    out = np.zeros(max(g.n, 1), np.int32)
+    slen = ctypes.c_int32(0)
+    st = Stats()
+    _L.check(_L.lib().vc_solve_mis(g._h, ctypes.byref(o), ctypes.byref(size),
+                                   out.ctypes.data_as(ctypes.c_void_p) if want_set else None,
+                                   ctypes.byref(slen), ctypes.byref(st)), st)
+    return size.value, (out[:slen.value].copy() if want_set else None), st.to_dict()
 
 
 def solve_batch(graphs, ks=None, opts: Options | None = None, want_covers: bool = True,

@@ -39,7 +39,14 @@ class Options(ctypes.Structure):
         ("load_balance", ctypes.c_int32),
         ("idle_timeout_ms", ctypes.c_int32),
         ("node_budget", ctypes.c_int64),
+        ("disable_bounds", ctypes.c_int32),
+        ("disable_root_rules", ctypes.c_int32),
+        ("breakdown", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
     ]
+
+
+PHASES = ("pop", "reduce", "components", "branch", "complete", "idle")
 
 
 class Stats(ctypes.Structure):
@@ -68,6 +75,7 @@ class Stats(ctypes.Structure):
         ("ms_total", ctypes.c_double),
         ("root_cycles", ctypes.c_int64 * 4),
         ("search_bytes", ctypes.c_int64),
+        ("phase_cycles", ctypes.c_int64 * 6),
     ]
 
     def to_dict(self) -> dict:
@@ -78,6 +86,8 @@ class Stats(ctypes.Structure):
                 d[name] = {i + 2: int(v[i]) for i in range(16) if v[i]}
             elif name == "root_cycles":
                 d[name] = [int(x) for x in v]
+            elif name == "phase_cycles":
+                d[name] = {PHASES[i]: int(v[i]) for i in range(6)}
             else:
                 d[name] = v
         return d
@@ -162,6 +172,7 @@ SIGNATURES = {
     "vc_solve_min": (ctypes.c_int, [_P, _P, _P, _P, _P, _P]),
     "vc_solve_k": (ctypes.c_int, [_P, _I, _P, _P, _P, _P, _P]),
     "vc_solve_batch": (ctypes.c_int, [_I, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
+    "vc_solve_mis": (ctypes.c_int, [_P, _P, _P, _P, _P, _P]),
     "vc_root_reduce_static": (ctypes.c_int, [_I, _I, _P, _P, _I, _P, _P, _P, _P, _P, _P]),
     "vc_free": (None, [_P]),
     "vc_strerror": (ctypes.c_char_p, [ctypes.c_int]),

@@ -112,6 +112,7 @@ namespace {
 struct QueryRef {
     vc_graph *g;
     int k;
+    int complement = 0;   // output the complement of the cover
 };
 
 struct QueryOut {
@@ -160,6 +161,8 @@ int solve_queries(vc_graph *g0, const std::vector<QueryRef> &qs, const vc_option
         Q.col = qs[i].g->col.as<int>();
         Q.k = qs[i].k;
         Q.maxdeg_in = qs[i].g->maxdeg;
+        Q.skip_root_rules = opt.disable_root_rules ? 1 : 0;
+        Q.emit_complement = qs[i].complement;
         Q.status = VC_OK;
         carve_query_scratch(Q, ws.qscratch.as<char>() + offs[i]);
     }
@@ -272,6 +275,8 @@ int solve_queries(vc_graph *g0, const std::vector<QueryRef> &qs, const vc_option
         P.load_balance = opt.load_balance;
         P.csr_smem = pl.csr_bytes;
         P.csr_query = csr_query;
+        P.no_bounds = opt.disable_bounds ? 1 : 0;
+        P.breakdown = opt.breakdown ? 1 : 0;
         VC_CK(search_run(pl, P, ws.root_slot.as<int>(), nq, nroots, s, ws.ev[2], ws.ev[3]));
         VC_CK(finalize_run(dq, nq, P.reg, P.reg_words, wcap, s));
         VC_CK(cudaMemcpyAsync(ws.hctl.p, P.ctl, kCtlWords * 8, cudaMemcpyDeviceToHost, s));
@@ -321,6 +326,7 @@ int solve_queries(vc_graph *g0, const std::vector<QueryRef> &qs, const vc_option
         memset(stats, 0, sizeof(*stats));
         stats->nodes = (int64_t)ctlw(hctl_local, kNodes);
         stats->search_bytes = (int64_t)ctlw(hctl_local, kBytes);
+        for (int k = 0; k < kPhases; k++) stats->phase_cycles[k] = (int64_t)ctlw(hctl_local, kPhase + k);
         stats->component_branches = (int64_t)ctlw(hctl_local, kCompBranches);
         stats->leaves = (int64_t)ctlw(hctl_local, kLeaves);
         stats->pruned = (int64_t)ctlw(hctl_local, kPruned);
@@ -443,6 +449,22 @@ int vc_solve_min(vc_graph *g, const vc_options *opt, int32_t *cover_size, int32_
     if (out[0].status != VC_OK) return out[0].status;
     *cover_size = out[0].size;
     if (cover_len) *cover_len = len;
+    return VC_OK;
+}
+
+int vc_solve_mis(vc_graph *g, const vc_options *opt, int32_t *set_size, int32_t *set, int32_t *set_len,
+                 vc_stats *stats)
+{
+    if (!g || !set_size) return VC_EINVAL;
+    std::vector<QueryRef> qs{{g, -1, 1}};
+    std::vector<QueryOut> out;
+    int32_t *sets[1] = {set};
+    int32_t len = 0;
+    int rc = solve_queries(g, qs, opt, out, set ? sets : nullptr, &len, stats);
+    if (rc != VC_OK) return rc;
+    if (out[0].status != VC_OK) return out[0].status;
+    *set_size = g->n - out[0].size;
+    if (set_len) *set_len = len;
     return VC_OK;
 }
 

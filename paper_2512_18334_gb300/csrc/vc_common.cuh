@@ -75,6 +75,10 @@ struct QueryDesc {
     int gen;             // generation of the query slot (served requests): node
                          // headers carry it; a node whose generation differs
                          // belongs to an earlier request of the slot and is dropped
+    int skip_root_rules; // 1: no reduction rules at the root (ablation); the
+                         // induced graph is every vertex with an edge
+    int emit_complement; // 1: the output list is the complement of the cover
+                         // (a maximum independent set when the cover is minimum)
     long long root_cycles[4];  // clock64 cycles: phase 1, greedy, phase 2, induce
     long long nodes;     // search-tree nodes spent on this query
     long long budget;    // node budget of this query (0: none)
@@ -175,6 +179,9 @@ struct SearchParams {
     int *stack_top;           // non-null: per-worker private stack depth, read at
                               // start and written at exit (the stacks stay resident
                               // between slices)
+    int no_bounds;            // 1: keep the whole degree array as every node's
+                              // window (ablation of Section 4.3)
+    int breakdown;            // 1: count SM cycles per activity (kPhase*)
 };
 
 // Control block: one unsigned long long per entry, each entry on its own
@@ -204,9 +211,20 @@ enum Ctl : int {
     kPreempts = 35,   // nodes stored at the end of a time slice
     kMaxProcNs = 36,  // longest single process() call (ns, diagnostics)
     kMaxExitNs = 37,  // longest exit phase of a worker (ns, diagnostics)
-    kCtlEntries = 38
+    kPhase = 38,      // kPhases entries: SM cycles per activity, summed over workers
+    kCtlEntries = 44
 };
 constexpr int kCtlStride = 16;
+// activities of the execution-time breakdown
+enum Phase : int {
+    kPhPop = 0,       // taking a node from the private stack or the worklist
+    kPhReduce = 1,    // reduction rules, prune test
+    kPhComp = 2,      // finding components, registering a branch on them, closing cliques/cycles
+    kPhBranch = 3,    // vertex branch: choosing v_max, storing the right child
+    kPhDone = 4,      // completion and aggregation through the registry, new best covers
+    kPhIdle = 5,      // waiting for work
+    kPhases = 6
+};
 constexpr int kCtlWords = kCtlEntries * kCtlStride;
 
 __host__ __device__ __forceinline__ unsigned long long &ctlw(unsigned long long *ctl, int e)

@@ -636,7 +636,7 @@ struct Root {
 
         // phase 1: degree-one and degree-two-triangle rules (need no bound)
         long long t0 = clock64();
-        reduce_rounds(false, INT_MAX);
+        if (!Q.skip_root_rules) reduce_rounds(false, INT_MAX);
         long long t1 = clock64();
         if (threadIdx.x == 0) Q.root_cycles[0] = t1 - t0;
         if (live_edges2() == 0) {
@@ -669,7 +669,7 @@ struct Root {
         const int bound = Q.k >= 0 ? Q.k + 1 : greedy_size;
 
         // phase 2: all three rules; high-degree budget b = bound - |F| - 1
-        const bool feasible = reduce_rounds(true, bound);
+        const bool feasible = Q.skip_root_rules ? true : reduce_rounds(true, bound);
         t1 = clock64();
         if (threadIdx.x == 0) Q.root_cycles[2] = t1 - t0;
         const int e2 = live_edges2();
@@ -1239,7 +1239,7 @@ struct ClusterRoot {
         }
         cl.sync();
         long long t0 = clock64();
-        reduce_rounds(false, INT_MAX);
+        if (!Q.skip_root_rules) reduce_rounds(false, INT_MAX);
         long long t1 = clock64();
         if (rank == 0 && threadIdx.x == 0) Q.root_cycles[0] = t1 - t0;
         if (live_edges2() == 0) {
@@ -1264,7 +1264,7 @@ struct ClusterRoot {
             return;
         }
         const int bound = Q.k >= 0 ? Q.k + 1 : greedy_size;
-        const bool feasible = reduce_rounds(true, bound);
+        const bool feasible = Q.skip_root_rules ? true : reduce_rounds(true, bound);
         t1 = clock64();
         if (rank == 0 && threadIdx.x == 0) Q.root_cycles[2] = t1 - t0;
         const long long e2 = live_edges2();
@@ -1337,14 +1337,15 @@ __device__ void finalize_query(QueryDesc &Q, const RegEntry *reg, const uint32_t
     const int chunk = (n + T - 1) / T;
     const int beg = min(n, threadIdx.x * chunk), end = min(n, beg + chunk);
     const bool emit = Q.yes != 0;
+    const bool flip = Q.emit_complement != 0;   // the vertices outside the cover
     int c = 0;
     if (emit)
-        for (int v = beg; v < end; v++) c += Q.cover_flags[v] != 0;
+        for (int v = beg; v < end; v++) c += (Q.cover_flags[v] != 0) != flip;
     int tot;
     int off = block_excl_scan(c, red, &tot);
     if (emit)
         for (int v = beg; v < end; v++)
-            if (Q.cover_flags[v]) Q.cover_list[off++] = v;
+            if ((Q.cover_flags[v] != 0) != flip) Q.cover_list[off++] = v;
     if (threadIdx.x == 0) Q.cover_len = emit ? tot : 0;
 }
 

@@ -73,7 +73,7 @@ __host__ __device__ inline int slot_bytes_for(int ncap, int wcap)
 template <typename T>
 __host__ __device__ inline int worker_smem_bytes(int ncap, int wcap)
 {
-    return deg_region_bytes<T>(ncap) + align_up(ncap, 16) + ncap * 4 + align_up(wcap * 4, 16) + 64 + 34 * 8;
+    return deg_region_bytes<T>(ncap) + align_up(ncap, 16) + ncap * 4 + align_up(wcap * 4, 16) + 128 + 34 * 8;
 }
 
 // ---------------------------------------------------------------- registry
@@ -185,7 +185,8 @@ struct Worker {
     uint8_t *mark;    // mark bytes, same indexing
     int *lab;         // union-find labels / mark list
     uint32_t *cov;    // cover bitmap of the context window
-    int *sc;          // scalars
+    int *sc;          // scalars (16 ints)
+    unsigned long long *ph;   // breakdown: cycles per activity [kPhases], last mark [kPhases]
 
     const int *csr_s;   // staged CSR in shared memory (single-query launches) or null
 
@@ -219,7 +220,8 @@ struct Worker {
         mark = (uint8_t *)s;       s += align_up(ncap, 16);
         lab = (int *)s;            s += ncap * 4;
         cov = (uint32_t *)s;       s += align_up(wcap * 4, 16);
-        sc = (int *)s;             s += 64;
+        sc = (int *)s;             s += 128;
+        ph = (unsigned long long *)(sc + 16);
         if constexpr (WT == 0) tm.red = (long long *)s;
         stack = P.stack_slots + (size_t)wid * P.stack_depth * P.slot_bytes;
         top = P.stack_top ? P.stack_top[wid] : 0;
@@ -322,6 +324,17 @@ struct Worker {
         }
         S += c;
         tm.sync();
+    }
+
+    // Breakdown of the execution time (the paper's SM-clock instrumentation):
+    // the cycles since the last mark go to activity k.
+    __device__ __forceinline__ void lap(int k)
+    {
+        if (P.breakdown && tm.leader()) {
+            const unsigned long long now = clock64();
+            ph[k] += now - ph[kPhases];
+            ph[kPhases] = now;
+        }
     }
 
     __device__ int take_count()
@@ -433,8 +446,10 @@ struct Worker {
                                int S_c, int hi_c)
     {
         constexpr int V = Vec<T>::kPer16;
-        const int slo = align_down(kind == 0 ? lo : clo_c, V);
-        const int shi = kind == 0 ? hi : hi_c;
+        // the stored degree window: the node's live window, or (bounds off)
+        // the whole array
+        const int slo = P.no_bounds ? wlo : align_down(kind == 0 ? lo : clo_c, V);
+        const int shi = P.no_bounds ? whi : (kind == 0 ? hi : hi_c);
         const int nvec = (align_up(shi + 1, V) - slo) / V;
         NodeHdr *h = (NodeHdr *)slot;
         if (tm.leader()) {
@@ -1044,6 +1059,7 @@ struct Worker {
     // Narrow [lo, hi] to the live vertices.
     __device__ void shrink_window()
     {
+        if (P.no_bounds) return;
         int nlo = INT_MAX, nhi = -1;
         for (int v = lo + tm.rank; v <= hi; v += tm.size())
             if (d[v - wlo] > 0) { nlo = min(nlo, v); nhi = max(nhi, v); }
@@ -1281,25 +1297,31 @@ struct Worker {
             nodes_local++;
             qnodes++;
             Stats st = reduce(B);
+            lap(kPhReduce);
             if (st.pruned) {
                 if (tm.leader()) atomicAdd(&ctlw(P.ctl, kPruned), 1ull);
                 complete(comp);
+                lap(kPhDone);
                 return;
             }
             const long long bud = (long long)B - S - 1;
             if (S >= B || st.e2 / 2 > bud * bud) {      // stopping condition
                 if (tm.leader()) atomicAdd(&ctlw(P.ctl, kPruned), 1ull);
                 complete(comp);
+                lap(kPhDone);
                 return;
             }
             if (st.e2 == 0) {                            // a new best cover
                 if (tm.leader()) atomicAdd(&ctlw(P.ctl, kLeaves), 1ull);
                 improve();
                 complete(comp);
+                lap(kPhDone);
                 return;
             }
-            lo = st.lo;
-            hi = st.hi;
+            if (!P.no_bounds) {      // Section 4.3: only the non-zero window
+                lo = st.lo;
+                hi = st.hi;
+            }
             int vmax = st.vmax;
             if (P.use_components) {
                 const int ncomp = find_components();
@@ -1307,10 +1329,12 @@ struct Worker {
                 const bool cycle = st.dmax == 2 && st.e2 == 2ll * st.live;
                 if (ncomp >= 2 || clique || cycle) {
                     const int r = handle_components(B);
-                    if (r == kComplete) { complete(comp); return; }
+                    lap(kPhComp);
+                    if (r == kComplete) { complete(comp); lap(kPhDone); return; }
                     if (r != kVertexBranch) return;
                     vmax = find_vmax();
                 }
+                lap(kPhComp);
             }
             // ---- branch on v_max (Algorithm 1 lines 9-11)
             if (vmax < lo || vmax > hi) {                         // cannot happen with edges left
@@ -1325,6 +1349,7 @@ struct Worker {
             const int c = take_count();
             apply_marks(c);
             depth++;
+            lap(kPhBranch);
         }
     }
 
@@ -1362,6 +1387,10 @@ struct Worker {
     __device__ void run()
     {
         if (P.quantum_ns > 0 && tm.leader()) t_end = globaltimer() + (unsigned long long)P.quantum_ns;
+        if (P.breakdown && tm.leader()) {
+            for (int k = 0; k < kPhases; k++) ph[k] = 0;
+            ph[kPhases] = clock64();
+        }
         unsigned long long idle_since = 0, seen_progress = ~0ull;
         int backoff = 32;
         // counters are flushed every 64 nodes, more often under a small node budget
@@ -1383,10 +1412,12 @@ struct Worker {
             if (got == 2) {
                 backoff = 32;
                 idle_since = 0;
+                lap(kPhPop);
                 tm.sync();
                 continue;
             }
             if (got == 1) {
+                lap(kPhPop);
                 backoff = 32;
                 idle_since = 0;
                 if (q != qcur) {
@@ -1416,6 +1447,7 @@ struct Worker {
             }
             backoff = min(backoff * 2, 4096);
             stop = tm.bcast(stop);
+            lap(kPhIdle);
             if (stop) break;
         }
         const unsigned long long tx = tm.leader() ? globaltimer() : 0ull;
@@ -1426,6 +1458,8 @@ struct Worker {
             lf_count = 0;
             if (P.stack_top) P.stack_top[wid] = top;
             atomicMax(&ctlw(P.ctl, kMaxExitNs), globaltimer() - tx);
+            if (P.breakdown)
+                for (int k = 0; k < kPhases; k++) atomicAdd(&ctlw(P.ctl, kPhase + k), ph[k]);
         }
     }
 };
