@@ -81,6 +81,21 @@ def dist_env():
             int(os.environ.get("LOCAL_RANK", "0")))
 
 
+def combine_over_ranks(local_ms: float, steps: int, world: int):
+    """Replicas: the timed region is the slowest rank's (MAX over ranks) and
+    the value counts the graphs of every rank: (max_ms, world * steps / max_s).
+    Uses the default process group when world > 1 (a CUDA tensor under NCCL,
+    a CPU tensor under gloo)."""
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        dev = torch.device("cuda", torch.cuda.current_device()) if dist.get_backend() == "nccl" else "cpu"
+        t = torch.tensor([float(local_ms)], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        local_ms = float(t.item())
+    return local_ms, world * steps / (local_ms / 1e3)
+
+
 def load_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -539,12 +554,7 @@ def ours_main(args, rank, world, local_rank):
         launches += st["launches"]       # the L2-flush fill is torch's kernel, not counted
     barrier()
     clk = clocks.stop()
-    total_ms = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = world * args.steps / (total_ms / 1e3)
+    total_ms, value = combine_over_ranks(sum(step_ms), args.steps, world)
     p99 = float(np.percentile(step_ms, 99))
 
     # ---- e2e: pinned host CSR -> vc_load_csr -> solve -> cover to host -> free
@@ -564,12 +574,7 @@ def ours_main(args, rank, world, local_rank):
         e2e_ms.append(ev0.elapsed_time(ev1))
         d2h = 4 * len(cov2) + 4
     barrier()
-    e2e_total = sum(e2e_ms)
-    if world > 1:
-        t = torch.tensor([e2e_total], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_total = float(t.item())
-    e2e_value = world * args.steps / (e2e_total / 1e3)
+    e2e_total, e2e_value = combine_over_ranks(sum(e2e_ms), args.steps, world)
 
     # ---- roofline of the dominant kernel, timed by the library with CUDA
     # events on the launching stream
