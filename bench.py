@@ -235,14 +235,16 @@ def extra_workloads(vc, torch, stream, peak):
         (size, _, st), ms = timed(lambda: vc.solve_min(d))
         lat.append(ms)
         nodes += st["nodes"]
-    vc.solve_batch(dgs[:16])
-    (sizes, _, status, _, bst), bms = timed(lambda: vc.solve_batch(dgs))
+    tuned, _, _ = vc.autotune(dgs, repeats=2)
+    vc.solve_batch(dgs[:16], opts=tuned)
+    (sizes, _, status, _, bst), bms = timed(lambda: vc.solve_batch(dgs, opts=tuned))
     out["gnm_80_200"] = {
         "graphs": len(dgs), "plain_graphs_per_s": round(len(dgs) / (sum(lat) / 1e3), 1),
         "plain_p50_ms": round(float(np.percentile(lat, 50)), 4), "plain_p99_ms": round(float(np.percentile(lat, 99)), 4),
         "plain_nodes_per_s": round(nodes / (sum(lat) / 1e3), 1),
         "batched_graphs_per_s": round(len(dgs) / (bms / 1e3), 1), "batched_ms": round(bms, 3),
-        "batched_nodes_per_s": round(bst["nodes"] / (bms / 1e3), 1)}
+        "batched_nodes_per_s": round(bst["nodes"] / (bms / 1e3), 1),
+        "batched_options": {f: getattr(tuned, f) for f in vc.TUNED_FIELDS}}
     for d in dgs:
         d.close()
 
@@ -323,9 +325,10 @@ def extra_pvc_batch(vc, stream, count=4096, budget=200_000):
     solved = [i for i in range(count) if status[i] == 0]
     qg = [dms[i] for i in solved] * 2
     ks = [int(sizes[i]) for i in solved] + [int(sizes[i]) - 1 for i in solved]
-    vc.solve_batch(qg[:64], ks[:64], node_budget=budget, raise_on_error=False)
+    tuned, _, _ = vc.autotune(qg, ks, repeats=1, node_budget=budget)
+    vc.solve_batch(qg[:64], ks[:64], opts=tuned, raise_on_error=False)
     t0 = time.perf_counter()
-    psz, pyes, pst, covers, bst = vc.solve_batch(qg, ks, node_budget=budget, raise_on_error=False)
+    psz, pyes, pst, covers, bst = vc.solve_batch(qg, ks, opts=tuned, raise_on_error=False)
     batch_s = time.perf_counter() - t0
     ns = len(solved)
     ok = pst == 0
@@ -350,6 +353,7 @@ def extra_pvc_batch(vc, stream, count=4096, budget=200_000):
             "batched_queries_per_s": round(int(ok.sum()) / batch_s, 1), "batched_s": round(batch_s, 3),
             "batched_over_budget": int((pst == vc.VC_EBUDGET).sum()), "wrong_answers": wrong,
             "covers_failing_edge_check": bad_cover, "batched_nodes_per_s": round(bst["nodes"] / batch_s, 1),
+            "batched_options": {f: getattr(tuned, f) for f in vc.TUNED_FIELDS},
             "plain_sample": len(sample), "plain_queries_per_s": round(len(sample) / plain_s, 1),
             "plain_matching_answers": plain_ok}
 

@@ -54,8 +54,9 @@ typedef struct vc_graph vc_graph;
  * switches are 0 (off) in the defaults. */
 typedef struct vc_options {
     int32_t use_components;   /* 1: branch on components (Algorithm 2); 0: Algorithm 1 */
-    int32_t team;             /* threads per worker: 0 auto, 32 (one warp per
-                                 worker) or 128/256/512/1024 (one block per worker) */
+    int32_t team;             /* threads per worker: 0 auto (128-thread blocks up to
+                                 4,096 induced vertices, 256 above), 32 (one warp
+                                 per worker) or 64..1024 (one block per worker) */
     int32_t dtype_bytes;      /* degree-array entry size: 0 auto, 1, 2 or 4 (Section 4.4) */
     int32_t stack_depth;      /* private stack slots per worker, 0 auto             */
     int32_t worklist_capacity;/* shared worklist slots, 0 auto                      */
@@ -72,7 +73,9 @@ typedef struct vc_options {
     int32_t disable_root_rules; /* 1: no reduction at the root (Section 4.2): the
                                  search starts from every vertex that has an edge */
     int32_t breakdown;        /* 1: count SM cycles per activity (vc_stats.phase_cycles) */
-    int32_t reserved;
+    int32_t offload_below;    /* load balancing: a new right child goes to the shared
+                                 worklist while it holds fewer items than this;
+                                 0 = half the number of workers */
 } vc_options;
 
 /* What a solve did.  All counters are totals over the launch. */
@@ -202,6 +205,20 @@ int vc_root_reduce_static(int32_t n, int32_t m2, const int32_t *d_row_ptr, const
                           int32_t k, int32_t *d_forced, int32_t *d_induced_row_ptr,
                           int32_t *d_induced_col, int32_t *d_induced_orig, int32_t *d_info,
                           void *cuda_stream);
+
+/* Autotuner for a batch of queries (same arguments as vc_solve_batch).
+ * Starting from *base (NULL = defaults), it tunes by coordinate descent, on
+ * the given queries themselves: the worker size (team), the degree type
+ * (the dtype threshold: the smallest type that fits, or a wider one), the
+ * worklist hunger threshold (offload_below), the stack depth and the
+ * worklist capacity.  Each candidate runs `repeats` times (>= 1) and scores
+ * the best wall time of a whole vc_solve_batch; candidates that fail are
+ * skipped.  Writes the best options to *best and its time to *best_ms; up to
+ * max_trials tried candidates and their times (-1: failed) to tried /
+ * tried_ms (nullable), and their number to *trials. */
+int vc_autotune(int32_t count, vc_graph *const *graphs, const int32_t *ks, const vc_options *base,
+                int32_t repeats, vc_options *best, double *best_ms, vc_options *tried, double *tried_ms,
+                int32_t max_trials, int32_t *trials);
 
 /* Exact maximum independent set: the complement of a minimum vertex cover
  * (the paper notes that its techniques carry over; related work, "Independent

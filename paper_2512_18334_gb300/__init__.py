@@ -26,7 +26,8 @@ from ._lib import (VC_OK, VC_EINVAL, VC_ENOMEM, VC_ECAPACITY, VC_ETIMEOUT, VC_EC
                    VcError, Options, Stats, ServerConfig, ServerResult, ServerStats, lib_path)
 
 __all__ = [
-    "Graph", "solve_min", "solve_k", "solve_mis", "solve_batch", "options", "Server", "VcError", "lib_path",
+    "Graph", "solve_min", "solve_k", "solve_mis", "solve_batch", "autotune", "options", "Server", "VcError",
+    "lib_path",
     "VC_OK", "VC_EINVAL", "VC_ENOMEM", "VC_ECAPACITY", "VC_ETIMEOUT", "VC_ECUDA", "VC_EBUDGET",
 ]
 
@@ -144,6 +145,29 @@ def solve_mis(g: Graph, opts: Options | None = None, want_set: bool = True, **kw
                                    out.ctypes.data_as(ctypes.c_void_p) if want_set else None,
                                    ctypes.byref(slen), ctypes.byref(st)), st)
     return size.value, (out[:slen.value].copy() if want_set else None), st.to_dict()
+
+
+TUNED_FIELDS = ("team", "dtype_bytes", "offload_below", "stack_depth", "worklist_capacity")
+
+
+def autotune(graphs, ks=None, opts: Options | None = None, repeats: int = 2, max_trials: int = 64, **kw):
+    """vc_autotune on a batch: (best Options, best ms, [(options dict, ms), ...])."""
+    o = _opts(opts, kw)
+    count = len(graphs)
+    arr = (ctypes.c_void_p * count)(*[gr._h for gr in graphs])
+    ks_arr = None
+    if ks is not None:
+        ks_np = np.ascontiguousarray(ks, dtype=np.int32)
+        ks_arr = ks_np.ctypes.data_as(ctypes.c_void_p)
+    best = Options()
+    best_ms = ctypes.c_double(0.0)
+    tried = (Options * max_trials)()
+    tried_ms = (ctypes.c_double * max_trials)()
+    n = ctypes.c_int32(0)
+    _L.check(_L.lib().vc_autotune(count, arr, ks_arr, ctypes.byref(o), int(repeats), ctypes.byref(best),
+                                  ctypes.byref(best_ms), tried, tried_ms, max_trials, ctypes.byref(n)))
+    table = [({f: getattr(tried[i], f) for f in TUNED_FIELDS}, tried_ms[i]) for i in range(min(n.value, max_trials))]
+    return best, best_ms.value, table
 
 
 def solve_batch(graphs, ks=None, opts: Options | None = None, want_covers: bool = True,

@@ -42,7 +42,7 @@ class Options(ctypes.Structure):
         ("disable_bounds", ctypes.c_int32),
         ("disable_root_rules", ctypes.c_int32),
         ("breakdown", ctypes.c_int32),
-        ("reserved", ctypes.c_int32),
+        ("offload_below", ctypes.c_int32),
     ]
 
 
@@ -173,6 +173,7 @@ SIGNATURES = {
     "vc_solve_k": (ctypes.c_int, [_P, _I, _P, _P, _P, _P, _P]),
     "vc_solve_batch": (ctypes.c_int, [_I, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
     "vc_solve_mis": (ctypes.c_int, [_P, _P, _P, _P, _P, _P]),
+    "vc_autotune": (ctypes.c_int, [_I, _P, _P, _P, _I, _P, _P, _P, _P, _I, _P]),
     "vc_root_reduce_static": (ctypes.c_int, [_I, _I, _P, _P, _I, _P, _P, _P, _P, _P, _P]),
     "vc_free": (None, [_P]),
     "vc_strerror": (ctypes.c_char_p, [ctypes.c_int]),

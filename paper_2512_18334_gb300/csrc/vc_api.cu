@@ -263,7 +263,7 @@ int solve_queries(vc_graph *g0, const std::vector<QueryRef> &qs, const vc_option
         P.wl_slots = ws.wl.as<char>();
         P.wl_seq = ws.wl_seq.as<unsigned>();
         P.wl_cap = wl_cap;
-        P.wl_low = opt.load_balance ? std::max(8, pl.workers / 2) : 0;
+        P.wl_low = !opt.load_balance ? 0 : (opt.offload_below > 0 ? opt.offload_below : std::max(8, pl.workers / 2));
         P.reg = ws.reg.as<RegEntry>();
         P.reg_words = ws.reg_words.as<uint32_t>();
         P.reg_cap = reg_cap;
@@ -449,6 +449,60 @@ int vc_solve_min(vc_graph *g, const vc_options *opt, int32_t *cover_size, int32_
     if (out[0].status != VC_OK) return out[0].status;
     *cover_size = out[0].size;
     if (cover_len) *cover_len = len;
+    return VC_OK;
+}
+
+int vc_autotune(int32_t count, vc_graph *const *graphs, const int32_t *ks, const vc_options *base,
+                int32_t repeats, vc_options *best, double *best_ms, vc_options *tried, double *tried_ms,
+                int32_t max_trials, int32_t *trials)
+{
+    if (count <= 0 || !graphs || !best || !best_ms) return VC_EINVAL;
+    for (int i = 0; i < count; i++)
+        if (!graphs[i]) return VC_EINVAL;
+    if (repeats < 1) repeats = 1;
+    vc_options cur;
+    if (base) cur = *base;
+    else vc_options_default(&cur);
+    std::vector<QueryRef> qs(count);
+    for (int i = 0; i < count; i++) qs[i] = QueryRef{graphs[i], ks ? ks[i] : -1};
+    int ntried = 0;
+    std::vector<QueryOut> out;
+    // best wall time of `repeats` runs of the whole batch; < 0: failed
+    auto score = [&](const vc_options &o) -> double {
+        double b = -1.0;
+        for (int r = 0; r < repeats; r++) {
+            vc_stats st;
+            const int rc = solve_queries(graphs[0], qs, &o, out, nullptr, nullptr, &st);
+            if (rc != VC_OK) return -1.0;
+            for (const QueryOut &q : out)
+                if (q.status != VC_OK && q.status != VC_EBUDGET) return -1.0;
+            if (b < 0 || st.ms_total < b) b = st.ms_total;
+        }
+        if (tried && ntried < max_trials) tried[ntried] = o;
+        if (tried_ms && ntried < max_trials) tried_ms[ntried] = b;
+        ntried++;
+        return b;
+    };
+    double bms = score(cur);
+    if (bms < 0) return VC_EINVAL;   // the starting point itself fails
+    auto stage = [&](auto apply, std::initializer_list<int> values) {
+        vc_options keep = cur;
+        for (int v : values) {
+            vc_options o = keep;
+            apply(o, v);
+            if (memcmp(&o, &keep, sizeof(o)) == 0) continue;
+            const double t = score(o);
+            if (t >= 0 && t < bms) { bms = t; cur = o; }
+        }
+    };
+    stage([](vc_options &o, int v) { o.team = v; }, {32, 64, 128, 256, 512});
+    stage([](vc_options &o, int v) { o.dtype_bytes = v; }, {1, 2, 4});
+    stage([](vc_options &o, int v) { o.offload_below = v; }, {64, 256, 1024, 4096});
+    stage([](vc_options &o, int v) { o.stack_depth = v; }, {32, 256});
+    stage([](vc_options &o, int v) { o.worklist_capacity = v; }, {1 << 14, 1 << 16});
+    *best = cur;
+    *best_ms = bms;
+    if (trials) *trials = ntried;
     return VC_OK;
 }
 

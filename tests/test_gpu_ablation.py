@@ -113,3 +113,17 @@ def test_maximum_independent_set(vc):
         inside[iset] = True
         src = np.repeat(np.arange(g.n), np.diff(g.row_ptr))
         assert not np.any(inside[src] & inside[g.col])      # no edge inside the set
+
+
+def test_autotuner_picks_a_working_configuration(vc):
+    gs = [gg.gnm(80, 200, s) for s in range(16)] + [gg.component_heavy(1, copies=4, copy_n=24, p=0.2, chain=2)]
+    dgs = [vc.Graph.from_csr(g.row_ptr, g.col) for g in gs]
+    best, best_ms, table = vc.autotune(dgs, repeats=1)
+    assert best_ms > 0 and len(table) >= 5
+    assert best_ms <= table[0][1] + 1e-9            # never worse than where it started
+    sizes, _, status, covers, _ = vc.solve_batch(dgs, opts=best)
+    for g, s, st, cov in zip(gs, sizes, status, covers):
+        assert st == 0 and s == oracle.mvc(g.n, g.row_ptr, g.col, node_budget=5_000_000)[0]
+        check_cover(g, cov, s)
+    for d in dgs:
+        d.close()

@@ -257,3 +257,17 @@ def test_registry_exhaustion_reports_cleanly(vc):
     size, _, _ = vc.solve_min(dg)
     dg.close()
     assert size == oracle.mvc(g.n, g.row_ptr, g.col, node_budget=5_000_000)[0]
+
+
+@pytest.mark.parametrize("team", [64, 128, 256, 512, 1024])
+def test_component_labels_with_every_block_size(vc, team):
+    # one block labels every vertex of a node's components; with path
+    # halving in the final pass, vertices could keep a stale (non-root)
+    # label and a cycle was counted short -- nearly every run at 128+ threads
+    for g, want in [(gg.cycle(1001), 501), (gg.cycle(1000), 500)]:
+        for _ in range(5):
+            assert gpu_min(vc, g, team=team)[0] == want
+    u = gg.disjoint_union([gg.cycle(5 + (s % 7)) for s in range(300)] + [gg.complete(4 + s % 3) for s in range(50)])
+    want = oracle.mvc(u.n, u.row_ptr, u.col)[0]
+    for _ in range(3):
+        assert gpu_min(vc, u, team=team)[0] == want
