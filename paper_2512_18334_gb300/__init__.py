@@ -26,7 +26,7 @@ from ._lib import (VC_OK, VC_EINVAL, VC_ENOMEM, VC_ECAPACITY, VC_ETIMEOUT, VC_EC
                    VcError, Options, Stats, ServerConfig, ServerResult, ServerStats, lib_path)
 
 __all__ = [
-    "Graph", "solve_min", "solve_k", "solve_mis", "solve_batch", "autotune", "options", "Server", "VcError",
+    "Graph", "solve_min", "solve_k", "solve_mis", "solve_batch", "autotune", "trim", "options", "Server", "VcError",
     "lib_path",
     "VC_OK", "VC_EINVAL", "VC_ENOMEM", "VC_ECAPACITY", "VC_ETIMEOUT", "VC_ECUDA", "VC_EBUDGET",
 ]
@@ -97,6 +97,11 @@ class Graph:
             self.close()
         except Exception:
             pass
+
+
+def trim() -> int:
+    """Free the search workspaces kept between solves (vc_trim)."""
+    return int(_L.lib().vc_trim())
 
 
 def _opts(opts, kw):

@@ -176,6 +176,7 @@ SIGNATURES = {
     "vc_autotune": (ctypes.c_int, [_I, _P, _P, _P, _I, _P, _P, _P, _P, _I, _P]),
     "vc_root_reduce_static": (ctypes.c_int, [_I, _I, _P, _P, _I, _P, _P, _P, _P, _P, _P]),
     "vc_free": (None, [_P]),
+    "vc_trim": (ctypes.c_int, []),
     "vc_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "vc_last_cuda_error": (ctypes.c_char_p, []),
     "vc_server_config_default": (ctypes.c_int, [_P]),

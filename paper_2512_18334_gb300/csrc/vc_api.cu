@@ -12,6 +12,8 @@
 #include <chrono>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <vector>
 
 #include "vc_internal.h"
@@ -51,6 +53,44 @@ struct Workspace {
         hcov.release();
         for (auto &e : ev)
             if (e) { cudaEventDestroy(e); e = nullptr; }
+    }
+};
+
+// Search workspaces are pooled per device and shared by every handle: a solve
+// borrows one and gives it back after its final synchronisation, so repeated
+// solves (of any graph) allocate nothing once the buffers have grown to size.
+// Solves running at the same time (other host threads) get other workspaces.
+std::mutex &pool_mutex()
+{
+    static std::mutex m;
+    return m;
+}
+
+std::map<int, std::vector<Workspace *>> &pool()
+{
+    static std::map<int, std::vector<Workspace *>> p;
+    return p;
+}
+
+struct WsLease {
+    int dev;
+    cudaStream_t stream;
+    Workspace *ws;
+    WsLease(int d, cudaStream_t s) : dev(d), stream(s), ws(nullptr)
+    {
+        std::lock_guard<std::mutex> lk(pool_mutex());
+        auto &v = pool()[d];
+        if (!v.empty()) {
+            ws = v.back();
+            v.pop_back();
+        }
+        if (!ws) ws = new Workspace();
+    }
+    ~WsLease()
+    {
+        cudaStreamSynchronize(stream);   // nothing of this solve is still in flight
+        std::lock_guard<std::mutex> lk(pool_mutex());
+        pool()[dev].push_back(ws);
     }
 };
 
@@ -104,7 +144,6 @@ struct vc_graph {
     int m2 = 0;
     int maxdeg = 0;
     DevBuf rp, col, err;
-    Workspace ws;
 };
 
 namespace {
@@ -136,8 +175,9 @@ int solve_queries(vc_graph *g0, const std::vector<QueryRef> &qs, const vc_option
     const int nq = (int)qs.size();
     out.assign(nq, QueryOut{VC_OK, -1, 0, 0});
     if (nq == 0) return VC_OK;
-    Workspace &ws = g0->ws;
     cudaStream_t s = g0->stream;
+    WsLease lease(g0->device, s);
+    Workspace &ws = *lease.ws;
     int rc;
     if ((rc = ws.init()) != VC_OK) return rc;
 
@@ -565,8 +605,26 @@ void vc_free(vc_graph *g)
     g->rp.release();
     g->col.release();
     g->err.release();
-    g->ws.release();
     delete g;
+}
+
+int vc_trim(void)
+{
+    std::lock_guard<std::mutex> lk(pool_mutex());
+    int n = 0;
+    for (auto &kv : pool()) {
+        int cur = 0;
+        cudaGetDevice(&cur);
+        cudaSetDevice(kv.first);
+        for (Workspace *w : kv.second) {
+            w->release();
+            delete w;
+            n++;
+        }
+        kv.second.clear();
+        cudaSetDevice(cur);
+    }
+    return n;
 }
 
 const char *vc_last_cuda_error(void)

@@ -122,3 +122,8 @@ def test_server_config_default_without_gpu(lib):
     assert c.max_inflight == 1024 and c.max_induced == 2048 and c.quantum_us == 2000
     assert c.dtype_bytes == 2 and c.use_components == 1 and c.arena_bytes == 2 << 30
     assert lib.lib().vc_server_config_default(None) == -1
+
+
+def test_trim_without_gpu(lib):
+    # nothing pooled yet in this process: frees nothing and needs no device
+    assert lib.lib().vc_trim() == 0

@@ -271,3 +271,14 @@ def test_component_labels_with_every_block_size(vc, team):
     want = oracle.mvc(u.n, u.row_ptr, u.col)[0]
     for _ in range(3):
         assert gpu_min(vc, u, team=team)[0] == want
+
+
+def test_workspace_pool_reuse_and_trim(vc):
+    # solves on different handles share pooled workspaces; trimming between
+    # solves is safe and the next solve rebuilds what it needs
+    gs = [gg.gnm(80, 200, 60 + s) for s in range(6)]
+    for i, g in enumerate(gs):
+        assert gpu_min(vc, g)[0] == oracle.mvc(g.n, g.row_ptr, g.col)[0]
+        if i == 2:
+            assert vc.trim() >= 1
+    assert gpu_min(vc, gg.cycle(501))[0] == 251
