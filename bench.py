@@ -390,6 +390,7 @@ def extra_ablation(vc, stream, budget=200_000_000):
              "gnm_40_90_x100": gg.disjoint_union([gg.gnm(40, 90, 500 + s) for s in range(100)])}
     variants = [("all_on", dict(breakdown=1)), ("components_off", dict(use_components=0)),
                 ("root_reduction_off", dict(disable_root_rules=1)), ("bounds_off", dict(disable_bounds=1)),
+                ("dynamic_component_bounds_off", dict(disable_dyn_bounds=1)),
                 ("load_balance_off", dict(load_balance=0))]
     out = {}
     for name, g in cases.items():

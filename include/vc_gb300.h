@@ -76,6 +76,10 @@ typedef struct vc_options {
     int32_t offload_below;    /* load balancing: a new right child goes to the shared
                                  worklist while it holds fewer items than this;
                                  0 = half the number of workers */
+    int32_t disable_dyn_bounds; /* 1: a component's bound stays the one fixed when it
+                                 was registered (no dynamic tightening from the
+                                 enclosing Best and the finished siblings) */
+    int32_t reserved;
 } vc_options;
 
 /* What a solve did.  All counters are totals over the launch. */

@@ -43,6 +43,8 @@ class Options(ctypes.Structure):
         ("disable_root_rules", ctypes.c_int32),
         ("breakdown", ctypes.c_int32),
         ("offload_below", ctypes.c_int32),
+        ("disable_dyn_bounds", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
     ]
 
 

@@ -317,6 +317,7 @@ int solve_queries(vc_graph *g0, const std::vector<QueryRef> &qs, const vc_option
         P.csr_query = csr_query;
         P.no_bounds = opt.disable_bounds ? 1 : 0;
         P.breakdown = opt.breakdown ? 1 : 0;
+        P.no_dyn_bounds = opt.disable_dyn_bounds ? 1 : 0;
         VC_CK(search_run(pl, P, ws.root_slot.as<int>(), nq, nroots, s, ws.ev[2], ws.ev[3]));
         VC_CK(finalize_run(dq, nq, P.reg, P.reg_words, wcap, s));
         VC_CK(cudaMemcpyAsync(ws.hctl.p, P.ctl, kCtlWords * 8, cudaMemcpyDeviceToHost, s));

@@ -112,7 +112,11 @@ struct NodeHdr {            // 64 bytes; the payload after it stays 16-aligned
     int32_t cov_empty;      // 1: cover bitmap not stored (all zero)
     int32_t depth;          // search-tree depth (statistics only)
     int32_t gen;            // generation of the query slot when the node was made
-    int32_t pad[5];
+    // dynamic component bound (minimum covers): the parent entry of the
+    // node's component context, that parent's ancestor, and the context's
+    // lower bound (dpar = -1: the context is a root entry)
+    int32_t dpar, danc, dlb;
+    int32_t pad[2];
 };
 static_assert(sizeof(NodeHdr) == 64, "node header must stay 64 bytes");
 
@@ -138,6 +142,12 @@ struct RegEntry {
     int32_t sib;     // component: next child of the same parent (-1 ends)
     int32_t first;   // parent: first child
     int32_t tot;     // parent: |S_P| + sum of its children's cur
+    // pad: while the entry is free, the chunk link and size of the free
+    // stack; while in use, dynamic component bounds (minimum covers):
+    //   component: pad[0] = its lower bound LB_i
+    //   parent:    pad as one 64-bit word {high: sum of the LB of the children
+    //              still running, low: |S_P| + Best of the children finished},
+    //              updated with one atomic so that readers see a consistent pair
     int32_t pad[2];
 };
 static_assert(sizeof(RegEntry) == 64, "registry entry must stay 64 bytes");
@@ -182,6 +192,7 @@ struct SearchParams {
     int no_bounds;            // 1: keep the whole degree array as every node's
                               // window (ablation of Section 4.3)
     int breakdown;            // 1: count SM cycles per activity (kPhase*)
+    int no_dyn_bounds;        // 1: no dynamic tightening of component bounds (ablation)
 };
 
 // Control block: one unsigned long long per entry, each entry on its own
@@ -259,6 +270,13 @@ __device__ __forceinline__ int ld_relaxed(const int *p)
 {
     int v;
     asm volatile("ld.relaxed.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long *p)
+{
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.b64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
     return v;
 }
 

@@ -195,6 +195,7 @@ struct Worker {
     const int *rp, *col;
     int S, comp, lo, hi, clo, chi, wlo, whi, depth;
     int gen;          // generation of the node's query slot
+    int dpar, danc, dlb;   // dynamic component bound of the context (dpar < 0: none)
     int cntbuf;       // double-buffer index of the mark counter
 
     // private stack
@@ -226,6 +227,9 @@ struct Worker {
         stack = P.stack_slots + (size_t)wid * P.stack_depth * P.slot_bytes;
         top = P.stack_top ? P.stack_top[wid] : 0;
         gen = 0;
+        dpar = -1;
+        danc = -1;
+        dlb = 0;
         t_end = 0;
         preempted = false;
         nodes_local = 0;
@@ -443,7 +447,7 @@ struct Worker {
     //   kind 0: the current array with a pending op (right child G - N(op))
     //   kind 1: component child: only vertices whose label is `root` (rel.)
     __device__ void write_slot(char *slot, int kind, int op, int root, int clo_c, int chi_c, int comp_c,
-                               int S_c, int hi_c)
+                               int S_c, int hi_c, int dpar_c, int danc_c, int dlb_c)
     {
         constexpr int V = Vec<T>::kPer16;
         // the stored degree window: the node's live window, or (bounds off)
@@ -464,6 +468,9 @@ struct Worker {
             h->cov_empty = kind == 1;
             h->depth = depth + 1;
             h->gen = gen;
+            h->dpar = kind == 0 ? dpar : dpar_c;
+            h->danc = kind == 0 ? danc : danc_c;
+            h->dlb = kind == 0 ? dlb : dlb_c;
         }
         uint4 *dst = (uint4 *)(slot + sizeof(NodeHdr));
         if (tm.leader())
@@ -509,6 +516,7 @@ struct Worker {
         if (tm.bcast(stale)) return false;
         S = __ldcg(&h->S); comp = __ldcg(&h->comp); wlo = __ldcg(&h->lo); whi = __ldcg(&h->hi);
         clo = __ldcg(&h->clo); chi = __ldcg(&h->chi); depth = __ldcg(&h->depth);
+        dpar = __ldcg(&h->dpar); danc = __ldcg(&h->danc); dlb = __ldcg(&h->dlb);
         const int op = __ldcg(&h->op), cov_empty = __ldcg(&h->cov_empty);
         lo = wlo; hi = whi;
 #ifdef VC_CHECKS
@@ -649,7 +657,8 @@ struct Worker {
     // Store a child: the worklist when it is hungry (load balancing,
     // Section 2.3), else the private stack, else the worklist.  Returns false
     // on overflow (error already recorded).
-    __device__ bool push_child(int kind, int op, int root, int clo_c, int chi_c, int comp_c, int S_c, int hi_c)
+    __device__ bool push_child(int kind, int op, int root, int clo_c, int chi_c, int comp_c, int S_c, int hi_c,
+                               int dpar_c = -1, int danc_c = -1, int dlb_c = 0)
     {
         int to_wl = 0;
         if (P.load_balance && tm.leader()) {
@@ -658,7 +667,7 @@ struct Worker {
         }
         to_wl = tm.bcast(to_wl);   // uniform decision: the team must take one path
         if (!to_wl && top < P.stack_depth) {
-            write_slot(stack_slot(top), kind, op, root, clo_c, chi_c, comp_c, S_c, hi_c);
+            write_slot(stack_slot(top), kind, op, root, clo_c, chi_c, comp_c, S_c, hi_c, dpar_c, danc_c, dlb_c);
             top++;
             max_top = max(max_top, top);
             tm.sync();
@@ -667,7 +676,7 @@ struct Worker {
         long long t = wl_reserve();
         if (t < 0) {
             if (top < P.stack_depth) {
-                write_slot(stack_slot(top), kind, op, root, clo_c, chi_c, comp_c, S_c, hi_c);
+                write_slot(stack_slot(top), kind, op, root, clo_c, chi_c, comp_c, S_c, hi_c, dpar_c, danc_c, dlb_c);
                 top++;
                 max_top = max(max_top, top);
                 tm.sync();
@@ -677,7 +686,7 @@ struct Worker {
             tm.sync();
             return false;
         }
-        write_slot(wl_slot(t), kind, op, root, clo_c, chi_c, comp_c, S_c, hi_c);
+        write_slot(wl_slot(t), kind, op, root, clo_c, chi_c, comp_c, S_c, hi_c, dpar_c, danc_c, dlb_c);
         wl_publish(t);
         tm.sync();
         return true;
@@ -871,6 +880,10 @@ struct Worker {
             int r2 = 0;
             if (tm.leader()) {
                 atomicAdd(&P.reg[par].val, bestc);
+                // the child leaves the running set: its LB out, its Best in
+                const int lbc = vld(C.pad[0]);
+                atomicAdd((unsigned long long *)&P.reg[par].pad[0],
+                          (unsigned long long)(unsigned)bestc - ((unsigned long long)(unsigned)lbc << 32));
                 reg_free(c);
                 r2 = atom_add_acq_rel(&P.reg[par].live, -1) - 1;
             }
@@ -1194,6 +1207,8 @@ struct Worker {
                 E.kind = 1;
                 E.first = -1;
                 E.tot = S;      // + each child's cur, added as the children are registered
+                // dynamic bounds: {LB of the running children, |S_P| + Best of the finished}
+                *(unsigned long long *)&E.pad[0] = ((unsigned long long)(unsigned)lb_sum << 32) | (unsigned)S;
             }
             uint32_t *w = reg_words(P, pidx);
             const int nw = (chi >> 5) - (clo >> 5) + 1;
@@ -1215,13 +1230,14 @@ struct Worker {
                     // the thread holding the j-th root of this stripe broadcasts it
                     const int r = tm.max((isroot && pos == j) ? i : -1);
                     const int clo_c = lo + r, chi_c = lo + __ldcg(chiv + r);
-                    if (pass == 1) {
-                        if (!push_child(1, -1, r, clo_c, chi_c, __ldcg(cmin + r), 0, chi_c)) return kError;
-                        continue;
-                    }
                     const int sz = __ldcg(csize + r), mx = __ldcg(cmax + r);
                     const int m = __ldcg(csum + r) / 2;
                     const int lb = (m + mx - 1) / mx;
+                    if (pass == 1) {
+                        if (!push_child(1, -1, r, clo_c, chi_c, __ldcg(cmin + r), 0, chi_c, pidx, comp, lb))
+                            return kError;
+                        continue;
+                    }
                     int bi = B - S - (lb_sum - lb);
                     if (bi > sz - 1) bi = sz - 1;
                     int cidx = -1;
@@ -1250,6 +1266,7 @@ struct Worker {
                         C.nw = cnw;
                         C.q = q;
                         C.kind = 0;
+                        C.pad[0] = lb;
                         cmin[r] = cidx;
                     }
                     if (has) {
@@ -1288,7 +1305,22 @@ struct Worker {
             if (tm.leader()) {
                 if (aborted(P.ctl)) B = INT_MIN;
                 else if (iter > 0 && t_end && globaltimer() > t_end) B = kPreempt;
-                else B = ld_relaxed(&P.reg[comp].val);
+                else {
+                    B = ld_relaxed(&P.reg[comp].val);
+                    if (dpar >= 0 && !P.no_dyn_bounds && !pvc()) {
+                        // Best of the enclosing context minus what the parent
+                        // and its other children already need: if this
+                        // component cannot beat it, the parent's sum cannot
+                        // beat the ancestor (every running sibling needs at
+                        // least its LB), so no cover is lost
+                        const unsigned long long pk =
+                            ld_relaxed_u64((const unsigned long long *)&P.reg[dpar].pad[0]);
+                        const long long bd = (long long)ld_relaxed(&P.reg[danc].val) -
+                                             (long long)(unsigned)(pk & 0xffffffffull) -
+                                             ((long long)(pk >> 32) - dlb);
+                        if (bd < B) B = bd < 0 ? 0 : (int)bd;
+                    }
+                }
             }
             B = tm.bcast(B);
             if (B == INT_MIN) return;   // aborted (decided by the leader for the whole team)
@@ -1559,6 +1591,7 @@ __global__ void search_roots_kernel(SearchParams P, const int *root_slot)
     if (threadIdx.x == 0) {
         h->S = 0; h->comp = qi; h->lo = 0; h->hi = np - 1; h->clo = 0; h->chi = np - 1;
         h->op = -1; h->q = qi; h->cov_empty = 1; h->depth = 0; h->gen = Q.gen;
+        h->dpar = -1; h->danc = -1; h->dlb = 0;
     }
     T *dd = (T *)(s + sizeof(NodeHdr));
     const int lim = align_up(np, V);
@@ -1637,6 +1670,7 @@ __global__ void serve_place_kernel(SearchParams P, const QueryDesc *staging, con
         NodeHdr *h = (NodeHdr *)s;
         h->S = 0; h->comp = qi; h->lo = 0; h->hi = np - 1; h->clo = 0; h->chi = np - 1;
         h->op = -1; h->q = qi; h->cov_empty = 1; h->depth = 0; h->gen = Q.gen;
+        h->dpar = -1; h->danc = -1; h->dlb = 0;
     }
     T *dd = (T *)(s + sizeof(NodeHdr));
     const int lim = align_up(np, V);

@@ -512,6 +512,7 @@ int vc_server_create(const vc_server_config *cfg_in, void *cuda_stream, vc_serve
     P.stack_top = s->stack_top.as<int>();
     P.no_bounds = 0;
     P.breakdown = 0;
+    P.no_dyn_bounds = 0;
 
     s->slot.assign(cfg.max_inflight, Slot{});
     for (int i = cfg.max_inflight - 1; i >= 0; i--) s->free_slots.push_back(i);
