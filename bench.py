@@ -263,7 +263,8 @@ def extra_workloads(vc, torch, stream, peak):
         "search_roofline": {"bound": "hbm", "kernel": "search_kernel", "achieved": round(gbs, 3),
                             "peak": peak, "unit": "GB/s", "frac": round(gbs / peak, 6),
                             "algorithmic_bytes": st["search_bytes"],
-                            "bytes_per_node": round(st["search_bytes"] / max(1, st["nodes"]), 1)}}
+                            "bytes_per_node": round(st["search_bytes"] / max(1, st["nodes"]), 1),
+                   "crown_forced": st["crown_forced"], "crown_removed": st["crown_removed"]}}
 
     # mixed batch (n in [40, 400]; half G(n,p), half Chung-Lu), per-query budget
     mix = gg.batch_pvc_mix(512, 7, n_lo=40, n_hi=400)
@@ -378,7 +379,8 @@ def extra_component_heavy_full(vc, stream, peak, budget=100_000_000):
             "component_branches": st["component_branches"], "workers": st["workers"], "team": st["team"],
             "search_roofline": {"bound": "hbm", "kernel": "search_kernel", "achieved": round(gbs, 3),
                                 "peak": peak, "unit": "GB/s", "frac": round(gbs / peak, 6),
-                                "bytes_per_node": round(st["search_bytes"] / max(1, st["nodes"]), 1)}}
+                                "bytes_per_node": round(st["search_bytes"] / max(1, st["nodes"]), 1),
+                   "crown_forced": st["crown_forced"], "crown_removed": st["crown_removed"]}}
 
 
 def extra_ablation(vc, stream, budget=200_000_000):
@@ -391,6 +393,7 @@ def extra_ablation(vc, stream, budget=200_000_000):
     variants = [("all_on", dict(breakdown=1)), ("components_off", dict(use_components=0)),
                 ("root_reduction_off", dict(disable_root_rules=1)), ("bounds_off", dict(disable_bounds=1)),
                 ("dynamic_component_bounds_off", dict(disable_dyn_bounds=1)),
+                ("crown_on", dict(crown=1)),
                 ("load_balance_off", dict(load_balance=0))]
     out = {}
     for name, g in cases.items():
@@ -409,7 +412,8 @@ def extra_ablation(vc, stream, budget=200_000_000):
                    "component_branches": st["component_branches"], "comp_hist": st["comp_hist"],
                    "vertices_in_degree_array": st["n_induced"], "dtype_bytes": st["dtype_bytes"],
                    "workers": st["workers"], "team": st["team"],
-                   "bytes_per_node": round(st["search_bytes"] / max(1, st["nodes"]), 1)}
+                   "bytes_per_node": round(st["search_bytes"] / max(1, st["nodes"]), 1),
+                   "crown_forced": st["crown_forced"], "crown_removed": st["crown_removed"]}
             if kw.get("breakdown"):
                 ph = st["phase_cycles"]
                 tot = sum(ph.values())

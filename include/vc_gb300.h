@@ -79,7 +79,9 @@ typedef struct vc_options {
     int32_t disable_dyn_bounds; /* 1: a component's bound stays the one fixed when it
                                  was registered (no dynamic tightening from the
                                  enclosing Best and the finished siblings) */
-    int32_t reserved;
+    int32_t crown;            /* 1: crown reduction at the root (Section 4.2), applied
+                                 as the Nemhauser-Trotter LP reduction on the device
+                                 after the other root rules; answers do not change */
 } vc_options;
 
 /* What a solve did.  All counters are totals over the launch. */
@@ -115,6 +117,11 @@ typedef struct vc_stats {
                                    worklist, reduction rules, components (finding,
                                    registering, closing cliques and cycles), vertex
                                    branch, completion through the registry, idle */
+    int32_t crown_forced;       /* with opt.crown: vertices it put in the cover     */
+    int32_t crown_removed;      /* ... and vertices it removed in all               */
+    int32_t crown_skipped;      /* queries where its matching check failed (nothing
+                                   was removed)                                     */
+    int32_t reserved;
 } vc_stats;
 
 /* Fill *opt with the defaults. */

@@ -44,7 +44,7 @@ class Options(ctypes.Structure):
         ("breakdown", ctypes.c_int32),
         ("offload_below", ctypes.c_int32),
         ("disable_dyn_bounds", ctypes.c_int32),
-        ("reserved", ctypes.c_int32),
+        ("crown", ctypes.c_int32),
     ]
 
 
@@ -78,6 +78,10 @@ class Stats(ctypes.Structure):
         ("root_cycles", ctypes.c_int64 * 4),
         ("search_bytes", ctypes.c_int64),
         ("phase_cycles", ctypes.c_int64 * 6),
+        ("crown_forced", ctypes.c_int32),
+        ("crown_removed", ctypes.c_int32),
+        ("crown_skipped", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
     ]
 
     def to_dict(self) -> dict:

@@ -183,10 +183,14 @@ int solve_queries(vc_graph *g0, const std::vector<QueryRef> &qs, const vc_option
 
     // ---- query descriptors + per-query scratch
     size_t scratch = 0;
-    std::vector<size_t> offs(nq);
+    std::vector<size_t> offs(nq), croff(nq, 0);
     for (int i = 0; i < nq; i++) {
         offs[i] = scratch;
         scratch += query_scratch_bytes(qs[i].g->n, qs[i].g->m2);
+        if (opt.crown) {   // crown workspace: 13 n + 1 + 2|E| ints
+            croff[i] = scratch;
+            scratch += align256(((size_t)13 * std::max(qs[i].g->n, 1) + 1 + (size_t)std::max(qs[i].g->m2, 1)) * 4);
+        }
     }
     if ((rc = ws.qscratch.ensure(scratch)) != VC_OK) return rc;
     if ((rc = ws.queries.ensure(sizeof(QueryDesc) * nq)) != VC_OK) return rc;
@@ -205,6 +209,7 @@ int solve_queries(vc_graph *g0, const std::vector<QueryRef> &qs, const vc_option
         Q.emit_complement = qs[i].complement;
         Q.status = VC_OK;
         carve_query_scratch(Q, ws.qscratch.as<char>() + offs[i]);
+        Q.crown_ws = opt.crown ? (int *)(ws.qscratch.as<char>() + croff[i]) : nullptr;
     }
     QueryDesc *dq = ws.queries.as<QueryDesc>();
     VC_CK(cudaMemcpyAsync(dq, hq, sizeof(QueryDesc) * nq, cudaMemcpyHostToDevice, s));
@@ -217,6 +222,7 @@ int solve_queries(vc_graph *g0, const std::vector<QueryRef> &qs, const vc_option
         max_deg_in = std::max(max_deg_in, qs[i].g->maxdeg);
     }
     VC_CK(root_run(dq, nq, max_n_in, max_deg_in, s));
+    if (opt.crown) VC_CK(crown_run(dq, nq, s));
     VC_CK(cudaEventRecord(ws.ev[1], s));
     VC_CK(cudaMemcpyAsync(hq, dq, sizeof(QueryDesc) * nq, cudaMemcpyDeviceToHost, s));
     VC_CK(cudaStreamSynchronize(s));
@@ -382,6 +388,9 @@ int solve_queries(vc_graph *g0, const std::vector<QueryRef> &qs, const vc_option
             stats->m_induced += hq[i].m2p / 2;
             stats->forced += hq[i].forced;
             stats->greedy_size += hq[i].greedy;
+            stats->crown_forced += hq[i].crown_forced;
+            stats->crown_removed += hq[i].crown_removed;
+            stats->crown_skipped += hq[i].crown_status < 0;
         }
         stats->dtype_bytes = nroots ? pl.dtype : 0;
         stats->team = nroots ? (pl.warp_team ? 32 : pl.threads) : 0;

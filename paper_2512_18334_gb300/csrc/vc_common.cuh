@@ -79,6 +79,11 @@ struct QueryDesc {
                          // induced graph is every vertex with an edge
     int emit_complement; // 1: the output list is the complement of the cover
                          // (a maximum independent set when the cover is minimum)
+    int *crown_ws;       // non-null: apply the crown reduction after the root phase
+                         // (scratch of 13 * n + 1 + 2|E| ints)
+    int crown_status;    // 0 nothing removed, 1 applied, -1 skipped (check failed)
+    int crown_forced;    // vertices the crown reduction put in the cover
+    int crown_removed;   // vertices it removed in all (cover + excluded)
     long long root_cycles[4];  // clock64 cycles: phase 1, greedy, phase 2, induce
     long long nodes;     // search-tree nodes spent on this query
     long long budget;    // node budget of this query (0: none)

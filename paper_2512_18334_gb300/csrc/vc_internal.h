@@ -79,6 +79,9 @@ cudaError_t validate_run(int n, int m2, const int *rp, const int *col, int *d_er
 cudaError_t root_run(QueryDesc *d_q, int nq, int max_n, int max_deg, cudaStream_t s);
 cudaError_t finalize_run(QueryDesc *d_q, int nq, const RegEntry *reg, const uint32_t *reg_words, int wcap,
                          cudaStream_t s);
+// Crown (Nemhauser-Trotter) reduction of each query's induced graph, for the
+// queries whose descriptor has a crown workspace (after root_run).
+cudaError_t crown_run(QueryDesc *d_q, int nq, cudaStream_t s);
 
 // ---- search (vc_search.cu)
 struct SearchPlan {

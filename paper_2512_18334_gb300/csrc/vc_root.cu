@@ -1358,6 +1358,248 @@ __global__ void __launch_bounds__(kRootThreads) finalize_kernel(QueryDesc *qs, c
     finalize_query(Q, reg, reg_words, wcap, red);
 }
 
+// ------------------------------------------------------------ crown reduction
+//
+// The crown rule at the root (Section 4.2; the paper cites it without
+// defining it), applied as the Nemhauser-Trotter reduction, which removes
+// every crown: a maximum matching of the bipartite double cover (u_L - v_R
+// for every edge uv) gives, through Koenig's theorem, a minimum cover C_B of
+// the double cover and so a half-integral optimal LP solution
+// x_v = (|{v_L, v_R} & C_B|) / 2.  Some minimum vertex cover contains every
+// vertex with x = 1 and no vertex with x = 0 (whose neighbours all have
+// x = 1), so those go to the cover / are dropped and the search runs on the
+// x = 1/2 part.  The matching is Hopcroft-Karp: layered BFS from the free L
+// vertices, then vertex-disjoint shortest augmenting paths found by parallel
+// DFS with exclusive claims on R vertices (per-vertex edge pointers and
+// parent links instead of stacks).  Before anything is removed, C_B is
+// checked to be a cover of the double cover of size |matching| (so it is
+// minimum); if not, nothing is removed.  One block per query, on the
+// induced graph of the root phase.
+__global__ void __launch_bounds__(kRootThreads) crown_kernel(QueryDesc *qs)
+{
+    __shared__ int red[33];
+    __shared__ int s_a, s_b, s_c;
+    QueryDesc &Q = qs[blockIdx.x];
+    if (Q.status != VC_OK || Q.answered || Q.np <= 0 || Q.crown_ws == nullptr) return;
+    const int n = Q.np, T = blockDim.x, t = threadIdx.x;
+    const int *rp = Q.rp2, *col = Q.col2;
+    int *w = Q.crown_ws;
+    int *mateL = w, *mateR = w + n, *dL = w + 2 * n, *dR = w + 3 * n, *used = w + 4 * n, *itp = w + 5 * n,
+        *parL = w + 6 * n, *fa = w + 7 * n, *fb = w + 8 * n, *x2 = w + 9 * n, *rpn = w + 10 * n,
+        *orn = w + 11 * n + 1, *coln = w + 12 * n + 1;
+    const int INF = INT_MAX;
+    for (int u = t; u < n; u += T) { mateL[u] = -1; mateR[u] = -1; }
+    __syncthreads();
+    for (int u = t; u < n; u += T)                       // greedy start
+        for (int e = rp[u]; e < rp[u + 1]; e++)
+            if (atomicCAS(&mateR[col[e]], -1, u) == -1) { mateL[u] = col[e]; break; }
+    __syncthreads();
+
+    for (int phase = 0; phase <= n; phase++) {
+        // ---- layered BFS from the free L vertices
+        if (t == 0) { s_a = 0; s_b = 0; }
+        __syncthreads();
+        for (int u = t; u < n; u += T) {
+            dR[u] = INF;
+            if (__ldcg(mateL + u) < 0) { dL[u] = 0; fa[atomicAdd(&s_a, 1)] = u; }
+            else dL[u] = INF;
+        }
+        __syncthreads();
+        int fsz = s_a, level = 0;
+        int *cur = fa, *nxt = fb;
+        for (int guard = 0; fsz > 0 && guard <= 2 * n + 2; guard++) {
+            __syncthreads();
+            if (t == 0) s_c = 0;
+            __syncthreads();
+            for (int i = t; i < fsz; i += T) {
+                const int u = __ldcg(cur + i);
+                for (int e = rp[u]; e < rp[u + 1]; e++) {
+                    const int v = col[e];
+                    if (atomicCAS(&dR[v], INF, level + 1) == INF) {
+                        const int m = __ldcg(mateR + v);
+                        if (m < 0) s_b = 1;
+                        else { dL[m] = level + 2; nxt[atomicAdd(&s_c, 1)] = m; }
+                    }
+                }
+            }
+            __threadfence_block();
+            __syncthreads();
+            fsz = s_b ? 0 : s_c;      // stop at the first layer that reaches a free R vertex
+            int *tmp = cur; cur = nxt; nxt = tmp;
+            level += 2;
+        }
+        __syncthreads();
+        const int found = s_b;
+        __syncthreads();
+        if (!found) break;
+        // ---- vertex-disjoint shortest augmenting paths
+        for (int v = t; v < n; v += T) { used[v] = 0; itp[v] = rp[v]; }
+        __threadfence_block();
+        __syncthreads();
+        for (int u0 = t; u0 < n; u0 += T) {
+            if (__ldcg(dL + u0) != 0) continue;
+            int x = u0;
+            parL[u0] = -1;
+            for (int guard = 0; guard < 2 * Q.m2p + 2 * n + 8; guard++) {
+                int e = __ldcg(itp + x), v = -1;
+                const int end = rp[x + 1], dx = __ldcg(dL + x);
+                for (; e < end; e++) {
+                    const int cv = col[e];
+                    if (__ldcg(dR + cv) == dx + 1 && atomicCAS(&used[cv], 0, 1) == 0) { v = cv; e++; break; }
+                }
+                itp[x] = e;
+                if (v >= 0) {
+                    const int m = __ldcg(mateR + v);
+                    if (m < 0) {                        // augment back to u0
+                        int cl = x, cr = v;
+                        for (int g2 = 0; g2 <= n; g2++) {
+                            const int nr = __ldcg(mateL + cl);
+                            mateL[cl] = cr;
+                            mateR[cr] = cl;
+                            if (cl == u0) break;
+                            cr = nr;
+                            cl = __ldcg(parL + cl);
+                        }
+                        break;
+                    }
+                    parL[m] = x;
+                    x = m;
+                } else {
+                    if (x == u0) break;
+                    x = __ldcg(parL + x);
+                }
+            }
+        }
+        __threadfence_block();
+        __syncthreads();
+    }
+
+    // ---- Koenig: Z = reachable from the free L vertices by alternating paths
+    if (t == 0) { s_a = 0; }
+    __syncthreads();
+    for (int u = t; u < n; u += T) {
+        dR[u] = 0;
+        if (__ldcg(mateL + u) < 0) { dL[u] = 1; fa[atomicAdd(&s_a, 1)] = u; }
+        else dL[u] = 0;
+    }
+    __threadfence_block();
+    __syncthreads();
+    {
+        int fsz = s_a;
+        int *cur = fa, *nxt = fb;
+        for (int guard = 0; fsz > 0 && guard <= 2 * n + 2; guard++) {
+            __syncthreads();
+            if (t == 0) s_c = 0;
+            __syncthreads();
+            for (int i = t; i < fsz; i += T) {
+                const int u = __ldcg(cur + i), mu = __ldcg(mateL + u);
+                for (int e = rp[u]; e < rp[u + 1]; e++) {
+                    const int v = col[e];
+                    if (v == mu) continue;             // non-matching edges from L
+                    if (atomicCAS(&dR[v], 0, 1) == 0) {
+                        const int m = __ldcg(mateR + v);
+                        if (m >= 0 && atomicCAS(&dL[m], 0, 1) == 0) nxt[atomicAdd(&s_c, 1)] = m;
+                    }
+                }
+            }
+            __threadfence_block();
+            __syncthreads();
+            fsz = s_c;
+            int *tmp = cur; cur = nxt; nxt = tmp;
+        }
+    }
+    __syncthreads();
+    // C_B = (L \ Z) + (R & Z); check it is a cover of size |M|
+    int csz = 0, msz = 0, bad = 0, v1 = 0, v0 = 0;
+    for (int u = t; u < n; u += T) {
+        const int inL = __ldcg(dL + u) ? 0 : 1, inR = __ldcg(dR + u) ? 1 : 0;
+        csz += inL + inR;
+        msz += __ldcg(mateL + u) >= 0;
+        x2[u] = inL + inR;
+        v1 += inL + inR == 2;
+        v0 += inL + inR == 0;
+        for (int e = rp[u]; e < rp[u + 1] && !bad; e++)
+            if (!inL && !__ldcg(dR + col[e])) bad = 1;  // edge u_L - v_R uncovered
+    }
+    csz = block_sum(csz, red);
+    msz = block_sum(msz, red);
+    bad = block_sum(bad, red);
+    v1 = block_sum(v1, red);
+    v0 = block_sum(v0, red);
+    __threadfence_block();
+    __syncthreads();
+    if (bad || csz != msz) {
+        if (t == 0) Q.crown_status = -1;
+        return;
+    }
+    if (v1 + v0 == 0) {
+        if (t == 0) Q.crown_status = 0;
+        return;
+    }
+    // ---- induce the x = 1/2 part (ids in increasing order), record x = 1
+    int *nid = fa;
+    int base = 0;
+    for (int b = 0; b < n; b += T) {
+        const int v = b + t;
+        const int k = v < n && x2[v] == 1;
+        int tot;
+        const int off = block_excl_scan(k, red, &tot);
+        if (v < n) nid[v] = k ? base + off : -1;
+        base += tot;
+    }
+    const int n2 = base;
+    __threadfence_block();
+    __syncthreads();
+    int ebase = 0, dmax = 0;
+    for (int b = 0; b < n; b += T) {
+        const int v = b + t;
+        int d = 0;
+        if (v < n && nid[v] >= 0)
+            for (int e = rp[v]; e < rp[v + 1]; e++) d += nid[col[e]] >= 0;
+        dmax = max(dmax, d);
+        int tot;
+        const int off = block_excl_scan(d, red, &tot);
+        if (v < n && nid[v] >= 0) { rpn[nid[v]] = ebase + off; orn[nid[v]] = Q.orig[v]; }
+        ebase += tot;
+    }
+    dmax = block_max(dmax, red);
+    __threadfence_block();
+    __syncthreads();
+    for (int v = t; v < n; v += T) {
+        if (x2[v] == 2) Q.st[Q.orig[v]] = 1;            // in the cover
+        if (nid[v] < 0) continue;
+        int o = rpn[nid[v]];
+        for (int e = rp[v]; e < rp[v + 1]; e++) {
+            const int c2 = nid[col[e]];
+            if (c2 >= 0) coln[o++] = c2;
+        }
+    }
+    __threadfence();
+    __syncthreads();
+    if (t == 0) {
+        rpn[n2] = ebase;
+        Q.rp2 = rpn;
+        Q.col2 = coln;
+        Q.orig = orn;
+        Q.np = n2;
+        Q.m2p = ebase;
+        Q.maxdeg = dmax;
+        Q.forced += v1;
+        Q.crown_status = 1;
+        Q.crown_forced = v1;
+        Q.crown_removed = v1 + v0;
+    }
+    __syncthreads();
+    if (n2 == 0 || (Q.k >= 0 && Q.forced > Q.k)) {   // settled here
+        for (int v = t; v < Q.n; v += T) Q.cover_flags[v] = Q.st[v] == 1;
+        if (t == 0) {
+            Q.answered = 1;
+            if (Q.k < 0) { Q.result = Q.forced; Q.yes = 1; }
+            else { Q.yes = Q.forced <= Q.k; Q.result = Q.yes ? Q.forced : -1; }
+        }
+    }
+}
+
 // ------------------------------------------------------------ served requests
 
 // One block per staged request: the CSR checks of vc_load_csr (row pointers
@@ -1554,6 +1796,13 @@ cudaError_t finalize_run(QueryDesc *d_q, int nq, const RegEntry *reg, const uint
 {
     if (nq <= 0) return cudaSuccess;
     finalize_kernel<<<nq, kRootThreads, 0, s>>>(d_q, reg, reg_words, wcap);
+    return cudaGetLastError();
+}
+
+cudaError_t crown_run(QueryDesc *d_q, int nq, cudaStream_t s)
+{
+    if (nq <= 0) return cudaSuccess;
+    crown_kernel<<<nq, kRootThreads, 0, s>>>(d_q);
     return cudaGetLastError();
 }
 

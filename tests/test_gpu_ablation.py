@@ -128,3 +128,50 @@ def test_autotuner_picks_a_working_configuration(vc):
         check_cover(g, cov, s)
     for d in dgs:
         d.close()
+
+
+def crown_graphs():
+    gs = graphs()
+    gs += [gg.random_bipartite_chung_lu(300, 200, 2.5, 3.0, 50.0, s) for s in range(3)]
+    gs += [gg.complete_bipartite(5, 9), gg.star(40), gg.cycle(11), gg.complete(7), gg.petersen()]
+    return gs
+
+
+def test_crown_reduction_keeps_answers(vc):
+    for g in crown_graphs():
+        want = oracle.mvc(g.n, g.row_ptr, g.col, node_budget=5_000_000)[0]
+        dg = vc.Graph.from_csr(g.row_ptr, g.col)
+        size, cover, st = vc.solve_min(dg, crown=1)
+        assert st["crown_skipped"] == 0, g.name
+        assert size == want, g.name
+        check_cover(g, cover, size)
+        yes, cover2, _ = vc.solve_k(dg, want, crown=1)
+        assert yes
+        check_cover(g, cover2, len(cover2))
+        assert not vc.solve_k(dg, want - 1, crown=1)[0]
+        dg.close()
+
+
+def test_crown_removes_a_known_crown(vc):
+    # K_{2,5} beside a Petersen graph: no degree-one vertex, no triangle and a
+    # loose greedy bound, so the other root rules keep all 17 vertices; the
+    # LP optimum of K_{2,5} is integral (hubs 1, the rest 0) while Petersen's
+    # is all 1/2, so the crown reduction removes exactly K_{2,5}
+    g = gg.disjoint_union([gg.complete_bipartite(2, 5), gg.petersen()])
+    dg = vc.Graph.from_csr(g.row_ptr, g.col)
+    size, cover, st = vc.solve_min(dg, crown=1)
+    _, _, st_off = vc.solve_min(dg)
+    dg.close()
+    assert size == 8
+    check_cover(g, cover, size)
+    assert st_off["n_induced"] == 17
+    assert st["crown_forced"] == 2 and st["crown_removed"] == 7 and st["n_induced"] == 10
+    # K_{2,4} beside an odd cycle (all 1/2 in the LP): the greedy bound 5 is
+    # optimal, and the hubs' degree 4 stays within the high-degree budget 4,
+    # so the root keeps both; the crown reduction leaves only the cycle
+    u = gg.disjoint_union([gg.complete_bipartite(2, 4), gg.cycle(5)])
+    du = vc.Graph.from_csr(u.row_ptr, u.col)
+    size, cover, st = vc.solve_min(du, crown=1)
+    du.close()
+    assert size == 5 and st["crown_forced"] == 2 and st["crown_removed"] == 6 and st["n_induced"] == 5
+    check_cover(u, cover, size)
