@@ -240,14 +240,16 @@ int vc_autotune(int32_t count, vc_graph *const *graphs, const int32_t *ks, const
 int vc_solve_mis(vc_graph *g, const vc_options *opt, int32_t *set_size, int32_t *set,
                  int32_t *set_len, vc_stats *stats);
 
-/* Release the handle and all device memory it owns.  NULL is a no-op.
- * The search workspaces (node slots, worklist, registry) are not owned by
- * handles: they are kept per device, shared by every handle and reused by
- * later solves; vc_trim() frees the idle ones. */
+/* Release the handle.  NULL is a no-op.  Its graph buffers go back to a
+ * per-device cache that later vc_load_csr calls reuse; the search workspaces
+ * (node slots, worklist, registry) are not owned by handles either: they are
+ * kept per device, shared by every handle and reused by later solves.
+ * vc_trim() frees what is idle in both. */
 void vc_free(vc_graph *g);
 
-/* Free the search workspaces kept between solves on every device (those not
- * in use by a running solve).  Returns the number freed. */
+/* Free the idle search workspaces and cached graph buffers on every device
+ * (nothing in use by a live handle or a running solve).  Returns the number
+ * of search workspaces freed. */
 int vc_trim(void);
 
 /* ------------------------------------------------------------------ serving

@@ -96,6 +96,63 @@ struct WsLease {
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
+// Graph buffers come from a per-device cache of power-of-two blocks, so that
+// loading and freeing graph handles in a loop allocates nothing after the
+// first round (cudaMalloc / cudaFree cost tens of microseconds each and may
+// synchronise the device).  vc_trim() returns the idle blocks.
+std::map<int, std::multimap<size_t, void *>> &block_cache()
+{
+    static std::map<int, std::multimap<size_t, void *>> c;
+    return c;
+}
+
+size_t size_class(size_t b)
+{
+    size_t s = 256;
+    while (s < b) s <<= 1;
+    return s;
+}
+
+struct CachedBuf {
+    void *p = nullptr;
+    size_t bytes = 0;   // size class
+    int dev = 0;
+    int ensure(size_t want)
+    {
+        if (want <= bytes) return VC_OK;
+        release();
+        const size_t sc = size_class(want);
+        cudaGetDevice(&dev);
+        {
+            std::lock_guard<std::mutex> lk(pool_mutex());
+            auto &m = block_cache()[dev];
+            auto it = m.find(sc);
+            if (it != m.end()) {
+                p = it->second;
+                m.erase(it);
+                bytes = sc;
+                return VC_OK;
+            }
+        }
+        if (cudaMalloc(&p, sc) != cudaSuccess) {
+            p = nullptr;
+            return VC_ENOMEM;
+        }
+        bytes = sc;
+        return VC_OK;
+    }
+    void release()
+    {
+        if (!p) return;
+        std::lock_guard<std::mutex> lk(pool_mutex());
+        block_cache()[dev].emplace(bytes, p);
+        p = nullptr;
+        bytes = 0;
+    }
+    template <class X>
+    X *as() const { return (X *)p; }
+};
+
 // Per-query device scratch of the root phase and the final answer.
 size_t query_scratch_bytes(int n, int m2)
 {
@@ -143,7 +200,7 @@ struct vc_graph {
     int n = 0;
     int m2 = 0;
     int maxdeg = 0;
-    DevBuf rp, col, err;
+    CachedBuf rp, col, err;
 };
 
 namespace {
@@ -622,9 +679,9 @@ int vc_trim(void)
 {
     std::lock_guard<std::mutex> lk(pool_mutex());
     int n = 0;
+    int cur = 0;
+    if (!pool().empty() || !block_cache().empty()) cudaGetDevice(&cur);
     for (auto &kv : pool()) {
-        int cur = 0;
-        cudaGetDevice(&cur);
         cudaSetDevice(kv.first);
         for (Workspace *w : kv.second) {
             w->release();
@@ -632,8 +689,13 @@ int vc_trim(void)
             n++;
         }
         kv.second.clear();
-        cudaSetDevice(cur);
     }
+    for (auto &kv : block_cache()) {
+        cudaSetDevice(kv.first);
+        for (auto &b : kv.second) cudaFree(b.second);
+        kv.second.clear();
+    }
+    if (n || !block_cache().empty()) cudaSetDevice(cur);
     return n;
 }
 
