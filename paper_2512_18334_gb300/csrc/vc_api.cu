@@ -34,7 +34,7 @@ namespace {
 
 // Search workspace: node slots, worklist, registry, scratch, control block.
 struct Workspace {
-    DevBuf stack, wl, wl_seq, reg, reg_words, comp_scratch, ctl, root_slot, queries, qscratch;
+    DevBuf stack, wl, wl_seq, reg, reg_words, comp_scratch, ctl, root_slot, queries, qscratch, wglobal;
     HostBuf hq, hctl, hcov;
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
     int init()
@@ -46,7 +46,7 @@ struct Workspace {
     void release()
     {
         for (DevBuf *b : {&stack, &wl, &wl_seq, &reg, &reg_words, &comp_scratch, &ctl, &root_slot, &queries,
-                          &qscratch})
+                          &qscratch, &wglobal})
             b->release();
         hq.release();
         hctl.release();
@@ -347,6 +347,8 @@ int solve_queries(vc_graph *g0, const std::vector<QueryRef> &qs, const vc_option
         if ((rc = ws.reg.ensure((size_t)reg_cap * sizeof(RegEntry))) != VC_OK) return rc;
         if ((rc = ws.reg_words.ensure((size_t)reg_cap * wcap * 4)) != VC_OK) return rc;
         if ((rc = ws.comp_scratch.ensure((size_t)pl.workers * 5 * ncap * 4)) != VC_OK) return rc;
+        if (pl.wglobal_bytes > 0 && (rc = ws.wglobal.ensure((size_t)pl.workers * (size_t)pl.wglobal_bytes)) != VC_OK)
+            return rc;
         if ((rc = ws.ctl.ensure(kCtlWords * 8)) != VC_OK) return rc;
         if ((rc = ws.root_slot.ensure((size_t)nq * 4)) != VC_OK) return rc;
         if ((rc = ws.hctl.ensure(kCtlWords * 8 + (size_t)nq * 4)) != VC_OK) return rc;
@@ -381,6 +383,8 @@ int solve_queries(vc_graph *g0, const std::vector<QueryRef> &qs, const vc_option
         P.no_bounds = opt.disable_bounds ? 1 : 0;
         P.breakdown = opt.breakdown ? 1 : 0;
         P.no_dyn_bounds = opt.disable_dyn_bounds ? 1 : 0;
+        P.wglobal = pl.wglobal_bytes > 0 ? ws.wglobal.as<char>() : nullptr;
+        P.wglobal_stride = pl.wglobal_bytes;
         VC_CK(search_run(pl, P, ws.root_slot.as<int>(), nq, nroots, s, ws.ev[2], ws.ev[3]));
         VC_CK(finalize_run(dq, nq, P.reg, P.reg_words, wcap, s));
         VC_CK(cudaMemcpyAsync(ws.hctl.p, P.ctl, kCtlWords * 8, cudaMemcpyDeviceToHost, s));

@@ -93,6 +93,8 @@ struct SearchPlan {
     size_t smem;        // dynamic shared memory per block
     int slot_bytes;     // bytes per node slot
     int csr_bytes;      // shared memory reserved for a staged CSR (0: none)
+    long long wglobal_bytes;  // > 0: bytes of global memory per worker for its node
+                              // arrays (they do not fit in shared memory)
 };
 
 // Choose the worker shape for induced graphs of up to ncap vertices.

@@ -69,11 +69,23 @@ __host__ __device__ inline int slot_bytes_for(int ncap, int wcap)
     return (int)sizeof(NodeHdr) + deg_region_bytes<T>(ncap) + align_up(wcap * 4, 16);
 }
 
+// A worker's node arrays: degrees, mark bytes, labels / mark list, cover
+// bitmap.  They live in shared memory when they fit, else in a per-worker
+// region of global memory (Section 4.1: the degree array is staged in shared
+// memory if it fits); the scalars and the team's reduction scratch always
+// live in shared memory.
+template <typename T>
+__host__ __device__ inline int worker_array_bytes(int ncap, int wcap)
+{
+    return deg_region_bytes<T>(ncap) + align_up(ncap, 16) + ncap * 4 + align_up(wcap * 4, 16);
+}
+constexpr int kWorkerScalarBytes = 128 + 34 * 8;
+
 // shared-memory bytes of one worker (team)
 template <typename T>
-__host__ __device__ inline int worker_smem_bytes(int ncap, int wcap)
+__host__ __device__ inline int worker_smem_bytes(int ncap, int wcap, bool arrays_global)
 {
-    return deg_region_bytes<T>(ncap) + align_up(ncap, 16) + ncap * 4 + align_up(wcap * 4, 16) + 128 + 34 * 8;
+    return (arrays_global ? 0 : worker_array_bytes<T>(ncap, wcap)) + kWorkerScalarBytes;
 }
 
 // ---------------------------------------------------------------- registry
@@ -216,11 +228,12 @@ struct Worker {
         : P(p), tm(t), wid(w), csr_s(csr)
     {
         const int ncap = P.ncap, wcap = P.wcap;
-        char *s = smem;
-        d = (T *)s;                s += deg_region_bytes<T>(ncap);
-        mark = (uint8_t *)s;       s += align_up(ncap, 16);
-        lab = (int *)s;            s += ncap * 4;
-        cov = (uint32_t *)s;       s += align_up(wcap * 4, 16);
+        char *a = P.wglobal ? P.wglobal + (size_t)wid * (size_t)P.wglobal_stride : smem;
+        d = (T *)a;                a += deg_region_bytes<T>(ncap);
+        mark = (uint8_t *)a;       a += align_up(ncap, 16);
+        lab = (int *)a;            a += ncap * 4;
+        cov = (uint32_t *)a;       a += align_up(wcap * 4, 16);
+        char *s = P.wglobal ? smem : a;
         sc = (int *)s;             s += 128;
         ph = (unsigned long long *)(sc + 16);
         if constexpr (WT == 0) tm.red = (long long *)s;
@@ -1531,7 +1544,7 @@ __global__ void __launch_bounds__(WT ? 256 : 1024, WT ? 3 : 1) search_kernel(con
         const int wid = blockIdx.x * wpb + warp;
         Team<1> t;
         t.rank = threadIdx.x & 31;
-        char *mine = smem + (size_t)warp * align_up(worker_smem_bytes<T>(P.ncap, P.wcap), 16);
+        char *mine = smem + (size_t)warp * align_up(worker_smem_bytes<T>(P.ncap, P.wcap, P.wglobal != nullptr), 16);
         Worker<T, 1> w(P, t, wid, mine, csr);
         w.run();
     } else {
@@ -1705,10 +1718,11 @@ static cudaError_t plan_one(int threads, size_t smem, int *blocks_per_sm)
 template <typename T>
 static int plan_t(int team_req, int ncap, int wcap, int sms, int csr_bytes, SearchPlan *pl)
 {
-    const int wsm = align_up(worker_smem_bytes<T>(ncap, wcap), 16);
+    const int wsm = align_up(worker_smem_bytes<T>(ncap, wcap, false), 16);
     const int kMaxSmem = 227 * 1024 - csr_bytes;
     pl->dtype = sizeof(T);
     pl->slot_bytes = slot_bytes_for<T>(ncap, wcap);
+    pl->wglobal_bytes = 0;
     // automatic: 128-thread block workers for induced graphs up to 4,096
     // vertices, 256-thread ones above (measured faster on GB300 than warp
     // workers or 512-thread blocks); warp workers on request
@@ -1723,12 +1737,21 @@ static int plan_t(int team_req, int ncap, int wcap, int sms, int csr_bytes, Sear
         pl->smem = (size_t)wpb * wsm + csr_bytes;
         if (plan_one<T, 1>(pl->threads, pl->smem, &bps) != cudaSuccess) return VC_ECUDA;
     } else {
-        if (wsm > kMaxSmem) return VC_ECAPACITY;
         int th = team_req >= 64 ? team_req : (ncap > 4096 ? 256 : 128);
         pl->warp_team = 0;
         pl->threads = th;
-        pl->smem = (size_t)wsm + csr_bytes;
-        if (plan_one<T, 0>(pl->threads, pl->smem, &bps) != cudaSuccess) return VC_ECUDA;
+        if (wsm <= kMaxSmem) {
+            pl->smem = (size_t)wsm + csr_bytes;
+            if (plan_one<T, 0>(pl->threads, pl->smem, &bps) != cudaSuccess) return VC_ECUDA;
+        }
+        if (wsm > kMaxSmem || bps < 1) {
+            // node arrays too large for shared memory: keep them in global
+            // memory (no staged CSR either)
+            pl->wglobal_bytes = ((long long)worker_array_bytes<T>(ncap, wcap) + 255) / 256 * 256;
+            pl->csr_bytes = 0;
+            pl->smem = (size_t)align_up(worker_smem_bytes<T>(ncap, wcap, true), 16);
+            if (plan_one<T, 0>(pl->threads, pl->smem, &bps) != cudaSuccess) return VC_ECUDA;
+        }
     }
     if (bps < 1) return VC_ECAPACITY;
     pl->blocks = bps * sms;

@@ -131,7 +131,7 @@ struct vc_server {
     SearchPlan pl{};
     SearchParams P{};
     int ncap = 0, wcap = 0;
-    DevBuf stack, wl, wl_seq, reg, reg_words, comp_scratch, ctl, stack_top, slots, admit, arena, cover_ctr;
+    DevBuf stack, wl, wl_seq, reg, reg_words, comp_scratch, ctl, stack_top, slots, admit, arena, cover_ctr, wglobal;
     HostBuf h_up;                          // pinned: the packed admission upload
     HostBuf m_rec, m_cover, m_ctl, m_act;  // mapped: retire records, covers, control words, active slots
     cudaEvent_t ev[6] = {};
@@ -156,7 +156,7 @@ struct vc_server {
     void release()
     {
         for (DevBuf *b : {&stack, &wl, &wl_seq, &reg, &reg_words, &comp_scratch, &ctl, &stack_top, &slots, &admit,
-                          &arena, &cover_ctr})
+                          &arena, &cover_ctr, &wglobal})
             b->release();
         for (HostBuf *b : {&h_up, &m_rec, &m_cover, &m_ctl, &m_act}) b->release();
         for (auto &e : ev)
@@ -479,7 +479,8 @@ int vc_server_create(const vc_server_config *cfg_in, void *cuda_stream, vc_serve
         (rc = s->m_rec.ensure(sizeof(RetireRec) * cfg.max_inflight, true)) != VC_OK ||
         (rc = s->m_cover.ensure((size_t)cfg.cover_buffer * 4, true)) != VC_OK ||
         (rc = s->m_ctl.ensure(kCtlEntries * 8, true)) != VC_OK ||
-        (rc = s->m_act.ensure(sizeof(int) * cfg.max_inflight, true)) != VC_OK)
+        (rc = s->m_act.ensure(sizeof(int) * cfg.max_inflight, true)) != VC_OK ||
+        (pl.wglobal_bytes > 0 && (rc = s->wglobal.ensure((size_t)pl.workers * (size_t)pl.wglobal_bytes)) != VC_OK))
         return fail(rc);
     s->arena_alloc.init((size_t)cfg.arena_bytes);
 
@@ -513,6 +514,8 @@ int vc_server_create(const vc_server_config *cfg_in, void *cuda_stream, vc_serve
     P.no_bounds = 0;
     P.breakdown = 0;
     P.no_dyn_bounds = 0;
+    P.wglobal = pl.wglobal_bytes > 0 ? s->wglobal.as<char>() : nullptr;
+    P.wglobal_stride = pl.wglobal_bytes;
 
     s->slot.assign(cfg.max_inflight, Slot{});
     for (int i = cfg.max_inflight - 1; i >= 0; i--) s->free_slots.push_back(i);

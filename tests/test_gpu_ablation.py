@@ -175,3 +175,27 @@ def test_crown_removes_a_known_crown(vc):
     du.close()
     assert size == 5 and st["crown_forced"] == 2 and st["crown_removed"] == 6 and st["n_induced"] == 5
     check_cover(u, cover, size)
+
+
+def test_node_arrays_in_global_memory_when_too_large(vc):
+    # without root rules the induced graph keeps every vertex with an edge:
+    # ~45k here, too many for a worker's arrays to fit in shared memory, so
+    # the search keeps degrees, marks, labels and cover in global memory
+    g = gg.chung_lu(50_000, 2.5, 6.0, 2000.0, 0)
+    want = oracle.mvc(g.n, g.row_ptr, g.col)[0]
+    dg = vc.Graph.from_csr(g.row_ptr, g.col)
+    size, cover, st = vc.solve_min(dg, disable_root_rules=1)
+    dg.close()
+    assert st["n_induced"] > 40_000
+    assert size == want
+    check_cover(g, cover, size)
+    # the same with a real branch on ~1,000 components at the first node
+    parts = [gg.gnm(45, 110, 900 + s) for s in range(1000)]
+    u = gg.disjoint_union(parts)
+    want = sum(oracle.mvc(p.n, p.row_ptr, p.col)[0] for p in parts)
+    du = vc.Graph.from_csr(u.row_ptr, u.col)
+    size, cover, st = vc.solve_min(du, disable_root_rules=1)
+    du.close()
+    assert st["n_induced"] > 40_000 and st["component_branches"] >= 1
+    assert size == want
+    check_cover(u, cover, size)
