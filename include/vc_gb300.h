@@ -82,6 +82,12 @@ typedef struct vc_options {
     int32_t crown;            /* 1: crown reduction at the root (Section 4.2), applied
                                  as the Nemhauser-Trotter LP reduction on the device
                                  after the other root rules; answers do not change */
+    int32_t cuda_graph;       /* 1 (default): the search phase (root-slot upload,
+                                 registry and worklist set-up, root placement, the
+                                 persistent search, finalisation, read-back) is
+                                 captured once per launch shape into a CUDA graph
+                                 kept with the workspace and replayed with one
+                                 launch; 0: its kernels are launched one by one */
 } vc_options;
 
 /* What a solve did.  All counters are totals over the launch. */
@@ -121,7 +127,9 @@ typedef struct vc_stats {
     int32_t crown_removed;      /* ... and vertices it removed in all               */
     int32_t crown_skipped;      /* queries where its matching check failed (nothing
                                    was removed)                                     */
-    int32_t reserved;
+    int32_t cuda_graph;         /* search phase: 0 launched kernel by kernel (or no
+                                   search), 1 captured into a graph by this call,
+                                   2 replayed from the graph of an earlier call     */
 } vc_stats;
 
 /* Fill *opt with the defaults. */

@@ -45,6 +45,7 @@ class Options(ctypes.Structure):
         ("offload_below", ctypes.c_int32),
         ("disable_dyn_bounds", ctypes.c_int32),
         ("crown", ctypes.c_int32),
+        ("cuda_graph", ctypes.c_int32),
     ]
 
 
@@ -81,7 +82,7 @@ class Stats(ctypes.Structure):
         ("crown_forced", ctypes.c_int32),
         ("crown_removed", ctypes.c_int32),
         ("crown_skipped", ctypes.c_int32),
-        ("reserved", ctypes.c_int32),
+        ("cuda_graph", ctypes.c_int32),
     ]
 
     def to_dict(self) -> dict:

@@ -33,10 +33,34 @@ namespace {
 
 
 // Search workspace: node slots, worklist, registry, scratch, control block.
+// A CUDA graph of one enqueue sequence, kept with the workspace whose
+// buffers its nodes name.  `key` holds every value the captured launches and
+// copies were built from (kernels, shapes, arguments, buffer addresses, copy
+// sizes); while the key is unchanged the graph is replayed with one launch.
+// The data behind the buffers is read when the graph runs, so a replay sees
+// the current queries.  A key is captured the second time it comes in a row:
+// capture and instantiation cost more than the launches they replace, so
+// calls whose shape changes every time (one graph after another of
+// different sizes) keep launching directly.
+struct GraphSlot {
+    cudaGraphExec_t exec = nullptr;
+    bool failed = false;   // capture or instantiation failed for this key: launch directly
+    std::vector<unsigned char> key;   // the key of the graph, or of the last direct launch
+    void release()
+    {
+        if (exec) cudaGraphExecDestroy(exec);
+        exec = nullptr;
+        failed = false;
+        key.clear();
+    }
+};
+
 struct Workspace {
     DevBuf stack, wl, wl_seq, reg, reg_words, comp_scratch, ctl, root_slot, queries, qscratch, wglobal;
     HostBuf hq, hctl, hcov;
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    cudaStream_t cap = nullptr;   // capture stream (the caller's may be the legacy default stream)
+    GraphSlot search_graph;
     int init()
     {
         for (auto &e : ev)
@@ -53,8 +77,53 @@ struct Workspace {
         hcov.release();
         for (auto &e : ev)
             if (e) { cudaEventDestroy(e); e = nullptr; }
+        search_graph.release();
+        if (cap) cudaStreamDestroy(cap);
+        cap = nullptr;
     }
 };
+
+// Enqueue body(stream, capturing) on s through the graph in gs: replay it
+// when `key` matches the captured one; on the second call in a row with a
+// key, capture body on the workspace's capture stream, instantiate and
+// launch; otherwise (a new key, or capture refused) run body directly on s.
+// Returns 2 (replayed), 1 (captured now) or 0 (direct); *err receives the
+// CUDA status of the enqueue.
+template <class F>
+int graph_enqueue(Workspace &ws, GraphSlot &gs, const void *key, size_t kbytes, cudaStream_t s, F body,
+                  cudaError_t *err)
+{
+    const bool same = gs.key.size() == kbytes && memcmp(gs.key.data(), key, kbytes) == 0;
+    if (same && gs.exec) {
+        *err = cudaGraphLaunch(gs.exec, s);
+        return 2;
+    }
+    if (!same) {   // first call with this key: remember it, launch directly
+        gs.release();
+        gs.key.assign((const unsigned char *)key, (const unsigned char *)key + kbytes);
+    } else if (!gs.failed) {
+        if (!ws.cap && cudaStreamCreateWithFlags(&ws.cap, cudaStreamNonBlocking) != cudaSuccess) {
+            cudaGetLastError();
+            ws.cap = nullptr;
+        }
+        cudaGraph_t g = nullptr;
+        if (ws.cap && cudaStreamBeginCapture(ws.cap, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+            const cudaError_t eb = body(ws.cap, true);
+            const cudaError_t ee = cudaStreamEndCapture(ws.cap, &g);
+            if (eb == cudaSuccess && ee == cudaSuccess && g && cudaGraphInstantiate(&gs.exec, g, 0) == cudaSuccess) {
+                cudaGraphDestroy(g);
+                *err = cudaGraphLaunch(gs.exec, s);
+                return 1;
+            }
+            if (g) cudaGraphDestroy(g);
+            gs.exec = nullptr;
+        }
+        cudaGetLastError();   // a refused capture leaves no sticky error
+        gs.failed = true;
+    }
+    *err = body(s, false);
+    return 0;
+}
 
 // Search workspaces are pooled per device and shared by every handle: a solve
 // borrows one and gives it back after its final synchronisation, so repeated
@@ -215,6 +284,16 @@ struct QueryOut {
     int status, size, yes, cover_len;
 };
 
+// Everything the search phase's graph is built from (zeroed, then filled
+// field by field so that padding compares equal).
+struct SearchGraphKey {
+    SearchParams P;
+    size_t smem;
+    int dtype, warp_team, threads, blocks, nq, nroots, wcap;
+    const void *root_slot_d, *root_slot_h, *hctl, *hq;
+    cudaEvent_t ev2, ev3;
+};
+
 // Run a set of queries in one root launch + one persistent search launch.
 // covers (nullable) / cover_lens receive the covers.
 int solve_queries(vc_graph *g0, const std::vector<QueryRef> &qs, const vc_options *opt_in,
@@ -252,6 +331,19 @@ int solve_queries(vc_graph *g0, const std::vector<QueryRef> &qs, const vc_option
     if ((rc = ws.qscratch.ensure(scratch)) != VC_OK) return rc;
     if ((rc = ws.queries.ensure(sizeof(QueryDesc) * nq)) != VC_OK) return rc;
     if ((rc = ws.hq.ensure(sizeof(QueryDesc) * nq)) != VC_OK) return rc;
+    // covers: finalisation writes each list straight into mapped host memory
+    // (room for n entries per query), so no copy or extra synchronisation
+    // follows the last kernel
+    const bool want_cov = covers != nullptr;
+    std::vector<size_t> coff(nq, 0);
+    if (want_cov) {
+        size_t total = 0;
+        for (int i = 0; i < nq; i++) {
+            coff[i] = total;
+            total += (size_t)std::max(qs[i].g->n, 1);
+        }
+        if ((rc = ws.hcov.ensure(total * 4, true)) != VC_OK) return rc;
+    }
     QueryDesc *hq = (QueryDesc *)ws.hq.p;
     for (int i = 0; i < nq; i++) {
         QueryDesc &Q = hq[i];
@@ -267,6 +359,7 @@ int solve_queries(vc_graph *g0, const std::vector<QueryRef> &qs, const vc_option
         Q.status = VC_OK;
         carve_query_scratch(Q, ws.qscratch.as<char>() + offs[i]);
         Q.crown_ws = opt.crown ? (int *)(ws.qscratch.as<char>() + croff[i]) : nullptr;
+        Q.cover_out = want_cov && covers[i] ? ws.hcov.dev_as<int>() + coff[i] : nullptr;
     }
     QueryDesc *dq = ws.queries.as<QueryDesc>();
     VC_CK(cudaMemcpyAsync(dq, hq, sizeof(QueryDesc) * nq, cudaMemcpyHostToDevice, s));
@@ -281,6 +374,8 @@ int solve_queries(vc_graph *g0, const std::vector<QueryRef> &qs, const vc_option
     VC_CK(root_run(dq, nq, max_n_in, max_deg_in, s));
     if (opt.crown) VC_CK(crown_run(dq, nq, s));
     VC_CK(cudaEventRecord(ws.ev[1], s));
+    // the queries the root phase settled are final now
+    VC_CK(finalize_run(dq, nq, nullptr, nullptr, 0, s, 1));
     VC_CK(cudaMemcpyAsync(hq, dq, sizeof(QueryDesc) * nq, cudaMemcpyDeviceToHost, s));
     VC_CK(cudaStreamSynchronize(s));
 
@@ -296,7 +391,9 @@ int solve_queries(vc_graph *g0, const std::vector<QueryRef> &qs, const vc_option
 
     float ms_search = 0.f;
     SearchPlan pl{};
-    SearchParams P{};
+    SearchParams P;
+    memset(&P, 0, sizeof(P));   // zero padding: P is compared byte by byte as part of a graph key
+    int graph_state = 0;
     unsigned long long hctl_local[kCtlWords] = {};
     if (nroots > 0) {
         // ---- phase 2: size and run the persistent search
@@ -354,8 +451,6 @@ int solve_queries(vc_graph *g0, const std::vector<QueryRef> &qs, const vc_option
         if ((rc = ws.hctl.ensure(kCtlWords * 8 + (size_t)nq * 4)) != VC_OK) return rc;
         int *h_root_slot = (int *)((char *)ws.hctl.p + kCtlWords * 8);
         memcpy(h_root_slot, root_slot.data(), (size_t)nq * 4);
-        VC_CK(cudaMemcpyAsync(ws.root_slot.p, h_root_slot, (size_t)nq * 4, cudaMemcpyHostToDevice, s));
-
         P.queries = dq;
         P.nq = nq;
         P.team = pl.warp_team ? 32 : pl.threads;
@@ -385,15 +480,43 @@ int solve_queries(vc_graph *g0, const std::vector<QueryRef> &qs, const vc_option
         P.no_dyn_bounds = opt.disable_dyn_bounds ? 1 : 0;
         P.wglobal = pl.wglobal_bytes > 0 ? ws.wglobal.as<char>() : nullptr;
         P.wglobal_stride = pl.wglobal_bytes;
-        VC_CK(search_run(pl, P, ws.root_slot.as<int>(), nq, nroots, s, ws.ev[2], ws.ev[3]));
-        VC_CK(finalize_run(dq, nq, P.reg, P.reg_words, wcap, s));
-        VC_CK(cudaMemcpyAsync(ws.hctl.p, P.ctl, kCtlWords * 8, cudaMemcpyDeviceToHost, s));
-    } else {
-        VC_CK(finalize_run(dq, nq, nullptr, nullptr, 0, s));
-    }
-    VC_CK(cudaMemcpyAsync(hq, dq, sizeof(QueryDesc) * nq, cudaMemcpyDeviceToHost, s));
-    VC_CK(cudaStreamSynchronize(s));
-    if (nroots > 0) {
+        // upload of the root slots, search, finalisation and read-back: one
+        // graph launch once this launch shape has been seen
+        auto enqueue = [&](cudaStream_t st, bool capturing) -> cudaError_t {
+            cudaError_t e = cudaMemcpyAsync(ws.root_slot.p, h_root_slot, (size_t)nq * 4, cudaMemcpyHostToDevice, st);
+            if (e == cudaSuccess)
+                e = search_run(pl, P, ws.root_slot.as<int>(), nq, nroots, st, ws.ev[2], ws.ev[3],
+                               capturing ? cudaEventRecordExternal : 0u);
+            if (e == cudaSuccess) e = finalize_run(dq, nq, P.reg, P.reg_words, wcap, st, 2);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(ws.hctl.p, P.ctl, kCtlWords * 8, cudaMemcpyDeviceToHost, st);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(hq, dq, sizeof(QueryDesc) * nq, cudaMemcpyDeviceToHost, st);
+            return e;
+        };
+        cudaError_t e = cudaSuccess;
+        if (opt.cuda_graph) {
+            SearchGraphKey key;
+            memset(&key, 0, sizeof(key));
+            memcpy(&key.P, &P, sizeof(P));
+            key.dtype = pl.dtype;
+            key.warp_team = pl.warp_team;
+            key.threads = pl.threads;
+            key.blocks = pl.blocks;
+            key.smem = pl.smem;
+            key.nq = nq;
+            key.nroots = nroots;
+            key.wcap = wcap;
+            key.root_slot_d = ws.root_slot.p;
+            key.root_slot_h = h_root_slot;
+            key.hctl = ws.hctl.p;
+            key.hq = hq;
+            key.ev2 = ws.ev[2];
+            key.ev3 = ws.ev[3];
+            graph_state = graph_enqueue(ws, ws.search_graph, &key, sizeof(key), s, enqueue, &e);
+        } else {
+            e = enqueue(s, false);
+        }
+        VC_CK(e);
+        VC_CK(cudaStreamSynchronize(s));
         memcpy(hctl_local, ws.hctl.p, kCtlWords * 8);
         VC_CK(cudaEventElapsedTime(&ms_search, ws.ev[2], ws.ev[3]));
     }
@@ -401,24 +524,11 @@ int solve_queries(vc_graph *g0, const std::vector<QueryRef> &qs, const vc_option
     VC_CK(cudaEventElapsedTime(&ms_root, ws.ev[0], ws.ev[1]));
 
     const int kstatus = (int)(int64_t)ctlw(hctl_local, kStatus);
-    // ---- covers: one device-to-host copy of every cover list
-    size_t total = 0;
-    std::vector<size_t> coff(nq);
-    for (int i = 0; i < nq; i++) {
-        coff[i] = total;
-        total += (size_t)std::max(hq[i].cover_len, 0);
-    }
-    const bool want_cov = covers != nullptr;
-    if (want_cov && total > 0 && kstatus == 0) {
-        if ((rc = ws.hcov.ensure(total * 4)) != VC_OK) return rc;
-        int32_t *hc = (int32_t *)ws.hcov.p;
+    if (want_cov && kstatus == 0) {
+        const int32_t *hc = (const int32_t *)ws.hcov.p;
         for (int i = 0; i < nq; i++)
-            if (hq[i].cover_len > 0 && covers[i])
-                VC_CK(cudaMemcpyAsync(hc + coff[i], hq[i].cover_list, (size_t)hq[i].cover_len * 4,
-                                      cudaMemcpyDeviceToHost, s));
-        VC_CK(cudaStreamSynchronize(s));
-        for (int i = 0; i < nq; i++)
-            if (covers[i] && hq[i].cover_len > 0) memcpy(covers[i], hc + coff[i], (size_t)hq[i].cover_len * 4);
+            if (covers[i] && hq[i].status == VC_OK && hq[i].cover_len > 0)
+                memcpy(covers[i], hc + coff[i], (size_t)std::min(hq[i].cover_len, std::max(hq[i].n, 1)) * 4);
     }
     for (int i = 0; i < nq; i++) {
         QueryOut &o = out[i];
@@ -458,7 +568,9 @@ int solve_queries(vc_graph *g0, const std::vector<QueryRef> &qs, const vc_option
         stats->workers = nroots ? pl.workers : 0;
         stats->max_stack = (int32_t)ctlw(hctl_local, kMaxStack);
         stats->err_where = (int32_t)ctlw(hctl_local, kErrWhere);
-        stats->launches = nroots > 0 ? 6 : 2;   // root [+ init, roots, publish, search] + finalize
+        // root [+ crown] [+ init, roots, publish, search] + finalize
+        stats->launches = (nroots > 0 ? 6 : 2) + (opt.crown ? 1 : 0);
+        stats->cuda_graph = graph_state;
         stats->ms_root = ms_root;
         stats->ms_search = ms_search;
         stats->ms_total =
@@ -533,6 +645,7 @@ int vc_options_default(vc_options *opt)
     opt->use_components = 1;
     opt->load_balance = 1;
     opt->idle_timeout_ms = 60000;
+    opt->cuda_graph = 1;
     return VC_OK;
 }
 

@@ -84,10 +84,14 @@ struct QueryDesc {
     int crown_status;    // 0 nothing removed, 1 applied, -1 skipped (check failed)
     int crown_forced;    // vertices the crown reduction put in the cover
     int crown_removed;   // vertices it removed in all (cover + excluded)
+    int listed;          // 1: the root phase already wrote cover_list / cover_out
+                         // and cover_len (the answer is its forced set)
     long long root_cycles[4];  // clock64 cycles: phase 1, greedy, phase 2, induce
     long long nodes;     // search-tree nodes spent on this query
     long long budget;    // node budget of this query (0: none)
     int *cover_list;     // ascending original ids (device, >= n)
+    int *cover_out;      // non-null: finalisation writes the same list here too
+                         // (mapped host memory, >= n entries)
 };
 
 // One served request as seen after a time slice, written by the device into

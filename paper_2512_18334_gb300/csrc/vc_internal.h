@@ -47,7 +47,7 @@ struct HostBuf {
     size_t bytes = 0;
     int ensure(size_t want, bool mapped = false)
     {
-        if (want <= bytes) return VC_OK;
+        if (want <= bytes && (!mapped || dev)) return VC_OK;
         release();
         if (cudaHostAlloc(&p, want, mapped ? cudaHostAllocMapped : cudaHostAllocDefault) != cudaSuccess) {
             p = nullptr;
@@ -77,8 +77,11 @@ struct HostBuf {
 cudaError_t validate_run(int n, int m2, const int *rp, const int *col, int *d_err, cudaStream_t s);
 // max_n / max_deg: the largest input graph and degree among the queries
 cudaError_t root_run(QueryDesc *d_q, int nq, int max_n, int max_deg, cudaStream_t s);
+// Answers and ascending cover lists (also into Q.cover_out when set).
+// mode 0: every query; 1: only the queries the root phase settled (reg may be
+// null); 2: only the searched ones.
 cudaError_t finalize_run(QueryDesc *d_q, int nq, const RegEntry *reg, const uint32_t *reg_words, int wcap,
-                         cudaStream_t s);
+                         cudaStream_t s, int mode = 0);
 // Crown (Nemhauser-Trotter) reduction of each query's induced graph, for the
 // queries whose descriptor has a crown workspace (after root_run).
 cudaError_t crown_run(QueryDesc *d_q, int nq, cudaStream_t s);
@@ -103,9 +106,11 @@ struct SearchPlan {
 int search_plan(int dtype, int team_req, int ncap, int wcap, int sms, int csr_bytes, SearchPlan *out);
 
 // Initialise the registry / worklist, place each root node (root_slot[q] >= 0
-// for searched queries) and run the persistent kernel.
+// for searched queries) and run the persistent kernel; ev0 / ev1 (nullable)
+// are recorded around it with ev_flags (cudaEventRecordExternal while the
+// stream is being captured into a graph).
 cudaError_t search_run(const SearchPlan &pl, SearchParams &P, const int *d_root_slot, int nq, int nroots,
-                       cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1);
+                       cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1, unsigned ev_flags = 0);
 
 // ---- served requests (resident search state, vc_search.cu)
 // Launch only the persistent search kernel (one time slice when

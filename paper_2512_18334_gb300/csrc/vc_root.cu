@@ -15,6 +15,9 @@
 // cover gives the bound, then phase 2 adds the high-degree rule.
 #include <algorithm>
 #include <climits>
+#include <map>
+#include <mutex>
+#include <set>
 
 #include "vc_common.cuh"
 
@@ -630,6 +633,7 @@ struct Root {
             Q.np = 0; Q.m2p = 0; Q.maxdeg = 0; Q.answered = 0; Q.greedy = -1;
             Q.improved = 0; Q.result = -1; Q.yes = 0; Q.cover_len = 0;
             Q.rounds = 0;
+            Q.listed = 0;
             for (int i = 0; i < 4; i++) Q.root_cycles[i] = 0;
         }
         __syncthreads();
@@ -1218,6 +1222,47 @@ struct ClusterRoot {
         for (int i = threadIdx.x; i < vcnt; i += blockDim.x) Q.st[vbeg + i] = forced(vbeg + i) ? 1 : 0;
     }
 
+    // The answer is the forced set: write it as the ascending output list
+    // (cover_list, and cover_out when set) here instead of in a separate
+    // finalisation launch.  Each thread takes four consecutive words of this
+    // CTA's forced bitmap, so thread order is id order; CTAs are ordered by
+    // rank.  One cluster barrier.  Called by every thread of every CTA.
+    __device__ void list_forced()
+    {
+        const volatile uint32_t *fw = forcedp(rank);
+        const int nw = chunk >> 5;
+        uint32_t m[4];
+        int c = 0;
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            const int i = threadIdx.x * 4 + j;
+            m[j] = i < nw ? fw[i] : 0u;
+            c += __popc(m[j]);
+        }
+        int mine;
+        int off = block_excl_scan(c, sh.red, &mine);
+        int cta_off, all, o2, t2;
+        exchange_prefix(mine, 0, cta_off, all, o2, t2);
+        off += cta_off;
+        int *list = Q.cover_list, *out = Q.cover_out;
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            uint32_t x = m[j];
+            const int v0 = vbeg + (threadIdx.x * 4 + j) * 32;
+            while (x) {
+                const int v = v0 + __ffs(x) - 1;
+                list[off] = v;
+                if (out) out[off] = v;
+                off++;
+                x &= x - 1;
+            }
+        }
+        if (rank == 0 && threadIdx.x == 0) {
+            Q.cover_len = all;
+            Q.listed = 1;
+        }
+    }
+
     __device__ void run()
     {
         if (rank == 0) {
@@ -1235,6 +1280,7 @@ struct ClusterRoot {
             Q.np = 0; Q.m2p = 0; Q.maxdeg = 0; Q.answered = 0; Q.greedy = -1;
             Q.improved = 0; Q.result = -1; Q.yes = 0; Q.cover_len = 0;
             Q.rounds = 0;
+            Q.listed = 0;
             for (int i = 0; i < 4; i++) Q.root_cycles[i] = 0;
         }
         cl.sync();
@@ -1251,6 +1297,7 @@ struct ClusterRoot {
                 if (Q.k < 0) { Q.result = ftot; Q.yes = 1; }
                 else { Q.yes = ftot <= Q.k; Q.result = Q.yes ? ftot : -1; }
             }
+            if ((Q.k < 0 || ftot <= Q.k) && !Q.emit_complement && Q.cover_list) list_forced();   // uniform
             return;
         }
         const int greedy_size = ftot + greedy();
@@ -1282,6 +1329,7 @@ struct ClusterRoot {
             if (rank == 0 && threadIdx.x == 0) {
                 Q.answered = 1; Q.bound = bound; Q.result = ftot; Q.yes = 1;
             }
+            if (!Q.emit_complement && Q.cover_list) list_forced();
             return;
         }
         induce();
@@ -1309,6 +1357,7 @@ __global__ void __launch_bounds__(kRootThreads, 1) root_cluster_kernel(QueryDesc
 // Called by every thread of the block.
 __device__ void finalize_query(QueryDesc &Q, const RegEntry *reg, const uint32_t *reg_words, int wcap, int *red)
 {
+    if (Q.listed) return;   // the root phase wrote the list already
     const int n = Q.n;
     if (!Q.answered) {
         const RegEntry &R = reg[Q.root_entry];
@@ -1343,18 +1392,26 @@ __device__ void finalize_query(QueryDesc &Q, const RegEntry *reg, const uint32_t
         for (int v = beg; v < end; v++) c += (Q.cover_flags[v] != 0) != flip;
     int tot;
     int off = block_excl_scan(c, red, &tot);
+    int *out = Q.cover_out;
     if (emit)
         for (int v = beg; v < end; v++)
-            if ((Q.cover_flags[v] != 0) != flip) Q.cover_list[off++] = v;
+            if ((Q.cover_flags[v] != 0) != flip) {
+                Q.cover_list[off] = v;
+                if (out) out[off] = v;
+                off++;
+            }
     if (threadIdx.x == 0) Q.cover_len = emit ? tot : 0;
 }
 
+// mode 0: every query; 1: only those the root phase settled; 2: only the
+// searched ones (the others were finalised after the root phase)
 __global__ void __launch_bounds__(kRootThreads) finalize_kernel(QueryDesc *qs, const RegEntry *reg,
-                                                                 const uint32_t *reg_words, int wcap)
+                                                                 const uint32_t *reg_words, int wcap, int mode)
 {
     __shared__ int red[33];
     QueryDesc &Q = qs[blockIdx.x];
     if (Q.status != VC_OK) return;
+    if ((mode == 1 && !Q.answered) || (mode == 2 && Q.answered)) return;
     finalize_query(Q, reg, reg_words, wcap, red);
 }
 
@@ -1724,16 +1781,46 @@ int root_cluster_shift(int nq, int max_n, int max_deg)
     return cs;
 }
 
+// Host-side memo of the cluster launch set-up, per device: the function
+// attributes are set once, and the cluster shape found to fit for a graph
+// size is kept (each occupancy query costs host time on every solve).
+struct ClusterMemo {
+    std::mutex mu;
+    std::set<int> attrs_set;
+    std::map<std::pair<int, int>, int> shift;   // (device, max_n) -> cluster shift, -1: none fits
+};
+static ClusterMemo &cluster_memo()
+{
+    static ClusterMemo m;
+    return m;
+}
+
 cudaError_t root_run(QueryDesc *d_q, int nq, int max_n, int max_deg, cudaStream_t s)
 {
     if (nq <= 0) return cudaSuccess;
     int cs = root_cluster_shift(nq, max_n, max_deg);
+    int dev = 0;
+    bool memo_hit = false;
     if (cs >= 0) {
-        cudaError_t e = cudaFuncSetAttribute(root_cluster_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        cudaError_t e = cudaGetDevice(&dev);
         if (e != cudaSuccess) return e;
-        e = cudaFuncSetAttribute(root_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)kRootSmemMax);
-        if (e != cudaSuccess) return e;
+        ClusterMemo &M = cluster_memo();
+        std::lock_guard<std::mutex> lk(M.mu);
+        if (!M.attrs_set.count(dev)) {
+            e = cudaFuncSetAttribute(root_cluster_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+            if (e != cudaSuccess) return e;
+            e = cudaFuncSetAttribute(root_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)kRootSmemMax);
+            if (e != cudaSuccess) return e;
+            M.attrs_set.insert(dev);
+        }
+        auto it = M.shift.find({dev, max_n});
+        if (it != M.shift.end()) {
+            cs = it->second;
+            memo_hit = true;
+        }
+    }
+    if (cs >= 0 && !memo_hit) {
         int C = (int)((max_n + (1 << cs) - 1) >> cs);
         // a cluster wider than 8 is not guaranteed: shrink until one fits
         for (;;) {
@@ -1759,6 +1846,10 @@ cudaError_t root_run(QueryDesc *d_q, int nq, int max_n, int max_deg, cudaStream_
             cs++;
             C = (int)((max_n + (1 << cs) - 1) >> cs);
         }
+        ClusterMemo &M = cluster_memo();
+        std::lock_guard<std::mutex> lk(M.mu);
+        if (M.shift.size() >= 4096) M.shift.clear();   // many distinct sizes: start over
+        M.shift[{dev, max_n}] = cs;
     }
     if (cs >= 0) {
         const int C = (int)((max_n + (1 << cs) - 1) >> cs);
@@ -1792,10 +1883,10 @@ cudaError_t root_run(QueryDesc *d_q, int nq, int max_n, int max_deg, cudaStream_
 }
 
 cudaError_t finalize_run(QueryDesc *d_q, int nq, const RegEntry *reg, const uint32_t *reg_words, int wcap,
-                         cudaStream_t s)
+                         cudaStream_t s, int mode)
 {
     if (nq <= 0) return cudaSuccess;
-    finalize_kernel<<<nq, kRootThreads, 0, s>>>(d_q, reg, reg_words, wcap);
+    finalize_kernel<<<nq, kRootThreads, 0, s>>>(d_q, reg, reg_words, wcap, mode);
     return cudaGetLastError();
 }
 

@@ -186,7 +186,10 @@ __device__ inline bool query_is_done(const SearchParams &P, int q)
 
 // ---------------------------------------------------------------- worker
 
-template <typename T, int WT>
+// GA: the node arrays are in global memory (SearchParams::wglobal).  A
+// compile-time choice, so that in the shared-memory form every array access
+// is a shared-memory access rather than a generic one.
+template <typename T, int WT, bool GA = false>
 struct Worker {
     const SearchParams &P;
     Team<WT> tm;
@@ -228,12 +231,12 @@ struct Worker {
         : P(p), tm(t), wid(w), csr_s(csr)
     {
         const int ncap = P.ncap, wcap = P.wcap;
-        char *a = P.wglobal ? P.wglobal + (size_t)wid * (size_t)P.wglobal_stride : smem;
+        char *a = GA ? P.wglobal + (size_t)wid * (size_t)P.wglobal_stride : smem;
         d = (T *)a;                a += deg_region_bytes<T>(ncap);
         mark = (uint8_t *)a;       a += align_up(ncap, 16);
         lab = (int *)a;            a += ncap * 4;
         cov = (uint32_t *)a;       a += align_up(wcap * 4, 16);
-        char *s = P.wglobal ? smem : a;
+        char *s = GA ? smem : a;
         sc = (int *)s;             s += 128;
         ph = (unsigned long long *)(sc + 16);
         if constexpr (WT == 0) tm.red = (long long *)s;
@@ -1520,7 +1523,7 @@ struct Worker {
 // Register caps keep the occupancy the planner counts on: block workers fit
 // two 512-thread (four 256-thread) blocks per SM, warp workers three blocks
 // of eight warps.
-template <typename T, int WT>
+template <typename T, int WT, bool GA = false>
 __global__ void __launch_bounds__(WT ? 256 : 1024, WT ? 3 : 1) search_kernel(const __grid_constant__ SearchParams P)
 {
     extern __shared__ __align__(16) char smem_all[];
@@ -1544,7 +1547,8 @@ __global__ void __launch_bounds__(WT ? 256 : 1024, WT ? 3 : 1) search_kernel(con
         const int wid = blockIdx.x * wpb + warp;
         Team<1> t;
         t.rank = threadIdx.x & 31;
-        char *mine = smem + (size_t)warp * align_up(worker_smem_bytes<T>(P.ncap, P.wcap, P.wglobal != nullptr), 16);
+        static_assert(!GA, "warp workers keep their arrays in shared memory");
+        char *mine = smem + (size_t)warp * align_up(worker_smem_bytes<T>(P.ncap, P.wcap, false), 16);
         Worker<T, 1> w(P, t, wid, mine, csr);
         w.run();
     } else {
@@ -1552,7 +1556,7 @@ __global__ void __launch_bounds__(WT ? 256 : 1024, WT ? 3 : 1) search_kernel(con
         t.rank = threadIdx.x;
         t.nthreads = blockDim.x;
         t.red = nullptr;
-        Worker<T, 0> w(P, t, blockIdx.x, smem, csr);
+        Worker<T, 0, GA> w(P, t, blockIdx.x, smem, csr);
         w.run();
     }
 }
@@ -1706,13 +1710,25 @@ __global__ void serve_place_kernel(SearchParams P, const QueryDesc *staging, con
 
 namespace vcg {
 
-template <typename T, int WT>
+template <typename T, int WT, bool GA = false>
 static cudaError_t plan_one(int threads, size_t smem, int *blocks_per_sm)
 {
-    cudaError_t e = cudaFuncSetAttribute(search_kernel<T, WT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(search_kernel<T, WT, GA>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, search_kernel<T, WT>, threads, smem);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, search_kernel<T, WT, GA>, threads, smem);
+}
+
+// The search kernel instance of a plan.
+template <typename T>
+static void launch_search(const SearchPlan &pl, const SearchParams &P, cudaStream_t s)
+{
+    if (pl.warp_team)
+        search_kernel<T, 1><<<pl.blocks, pl.threads, pl.smem, s>>>(P);
+    else if (pl.wglobal_bytes > 0)
+        search_kernel<T, 0, true><<<pl.blocks, pl.threads, pl.smem, s>>>(P);
+    else
+        search_kernel<T, 0><<<pl.blocks, pl.threads, pl.smem, s>>>(P);
 }
 
 template <typename T>
@@ -1750,7 +1766,7 @@ static int plan_t(int team_req, int ncap, int wcap, int sms, int csr_bytes, Sear
             pl->wglobal_bytes = ((long long)worker_array_bytes<T>(ncap, wcap) + 255) / 256 * 256;
             pl->csr_bytes = 0;
             pl->smem = (size_t)align_up(worker_smem_bytes<T>(ncap, wcap, true), 16);
-            if (plan_one<T, 0>(pl->threads, pl->smem, &bps) != cudaSuccess) return VC_ECUDA;
+            if (plan_one<T, 0, true>(pl->threads, pl->smem, &bps) != cudaSuccess) return VC_ECUDA;
         }
     }
     if (bps < 1) return VC_ECAPACITY;
@@ -1771,7 +1787,7 @@ int search_plan(int dtype, int team_req, int ncap, int wcap, int sms, int csr_by
 
 template <typename T>
 static cudaError_t run_t(const SearchPlan &pl, SearchParams &P, const int *d_root_slot, int nq, int nroots,
-                         cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1)
+                         cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1, unsigned ev_flags)
 {
     search_init_kernel<T><<<256, 256, 0, s>>>(P, nq);
     cudaError_t e = cudaGetLastError();
@@ -1780,23 +1796,17 @@ static cudaError_t run_t(const SearchPlan &pl, SearchParams &P, const int *d_roo
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     search_roots_publish<<<1, 1, 0, s>>>(P, nroots);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    if (ev0) cudaEventRecord(ev0, s);
-    if (pl.warp_team)
-        search_kernel<T, 1><<<pl.blocks, pl.threads, pl.smem, s>>>(P);
-    else
-        search_kernel<T, 0><<<pl.blocks, pl.threads, pl.smem, s>>>(P);
+    if (ev0 && (e = cudaEventRecordWithFlags(ev0, s, ev_flags)) != cudaSuccess) return e;
+    launch_search<T>(pl, P, s);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    if (ev1) cudaEventRecord(ev1, s);
+    if (ev1 && (e = cudaEventRecordWithFlags(ev1, s, ev_flags)) != cudaSuccess) return e;
     return cudaSuccess;
 }
 
 template <typename T>
 static cudaError_t slice_t(const SearchPlan &pl, const SearchParams &P, cudaStream_t s)
 {
-    if (pl.warp_team)
-        search_kernel<T, 1><<<pl.blocks, pl.threads, pl.smem, s>>>(P);
-    else
-        search_kernel<T, 0><<<pl.blocks, pl.threads, pl.smem, s>>>(P);
+    launch_search<T>(pl, P, s);
     return cudaGetLastError();
 }
 
@@ -1828,12 +1838,12 @@ cudaError_t serve_place_run(const SearchPlan &pl, const SearchParams &P, const Q
 }
 
 cudaError_t search_run(const SearchPlan &pl, SearchParams &P, const int *d_root_slot, int nq, int nroots,
-                       cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1)
+                       cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1, unsigned ev_flags)
 {
     switch (pl.dtype) {
-    case 1: return run_t<uint8_t>(pl, P, d_root_slot, nq, nroots, s, ev0, ev1);
-    case 2: return run_t<uint16_t>(pl, P, d_root_slot, nq, nroots, s, ev0, ev1);
-    default: return run_t<uint32_t>(pl, P, d_root_slot, nq, nroots, s, ev0, ev1);
+    case 1: return run_t<uint8_t>(pl, P, d_root_slot, nq, nroots, s, ev0, ev1, ev_flags);
+    case 2: return run_t<uint16_t>(pl, P, d_root_slot, nq, nroots, s, ev0, ev1, ev_flags);
+    default: return run_t<uint32_t>(pl, P, d_root_slot, nq, nroots, s, ev0, ev1, ev_flags);
     }
 }
 

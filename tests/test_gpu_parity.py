@@ -134,6 +134,35 @@ def test_chung_lu_50k(vc):
     assert st["n_induced"] <= 64
 
 
+def test_chung_lu_50k_decision_and_independent_set(vc):
+    # the cluster root phase settles this graph and writes the cover list
+    # itself; the decision form and the complement go through finalisation
+    g = gg.chung_lu(50_000, 2.5, 6.0, 2000.0, 0)
+    opt = oracle.mvc(g.n, g.row_ptr, g.col)[0]
+    dg = vc.Graph.from_csr(g.row_ptr, g.col)
+    try:
+        for _ in range(2):
+            size, cover, _ = vc.solve_min(dg)
+            assert size == opt and np.all(np.diff(cover) > 0)
+            check_cover(g, cover, size)
+        yes, cover, _ = vc.solve_k(dg, opt)
+        assert yes and len(cover) <= opt and np.all(np.diff(cover) > 0)
+        check_cover(g, cover, len(cover))
+        assert not vc.solve_k(dg, opt - 1)[0]
+        alpha, iset, _ = vc.solve_mis(dg)
+        assert alpha == g.n - opt and len(iset) == alpha and np.all(np.diff(iset) > 0)
+        inside = np.zeros(g.n, bool)
+        inside[iset] = True
+        src = np.repeat(np.arange(g.n), np.diff(g.row_ptr))
+        assert not np.any(inside[src] & inside[g.col])
+        sizes, yes_b, status, covers, _ = vc.solve_batch([dg, dg], [-1, opt])
+        assert list(sizes[:1]) == [opt] and all(status == vc.VC_OK) and yes_b[1]
+        for c in covers:
+            check_cover(g, c, len(c))
+    finally:
+        dg.close()
+
+
 def test_options_same_answers(vc):
     for seed in range(6):
         g = gg.gnm(80, 200, 100 + seed)
