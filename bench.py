@@ -340,12 +340,13 @@ def extra_pvc_batch(vc, stream, count=4096, budget=200_000):
     sample = rng.choice(len(qg), size=min(512, len(qg)), replace=False)
     t0 = time.perf_counter()
     plain_ok = 0
+    plain_err = {}   # status -> count (VC_EBUDGET: the search order differs between launches)
     for j in sample:
         try:
             y, _, _ = vc.solve_k(qg[j], ks[j], node_budget=budget, want_cover=True)
             plain_ok += int(y == (int(j) < ns))
-        except vc.VcError:
-            pass
+        except vc.VcError as e:
+            plain_err[str(e.status)] = plain_err.get(str(e.status), 0) + 1
     plain_s = time.perf_counter() - t0
     for d in dms:
         d.close()
@@ -356,7 +357,7 @@ def extra_pvc_batch(vc, stream, count=4096, budget=200_000):
             "covers_failing_edge_check": bad_cover, "batched_nodes_per_s": round(bst["nodes"] / batch_s, 1),
             "batched_options": {f: getattr(tuned, f) for f in vc.TUNED_FIELDS},
             "plain_sample": len(sample), "plain_queries_per_s": round(len(sample) / plain_s, 1),
-            "plain_matching_answers": plain_ok}
+            "plain_matching_answers": plain_ok, "plain_errors": plain_err}
 
 
 def extra_component_heavy_full(vc, stream, peak, budget=100_000_000):
