@@ -92,12 +92,11 @@ __global__ void max_degree_kernel(int n, const int *rp, int *err)
 // ------------------------------------------------------------ root kernel
 
 constexpr int kRootThreads = 1024;
-constexpr int kHeavyRow = 32;    // rows longer than this are scanned by a whole warp
+// Rows longer than this are scanned by a whole warp: a thread scanning a row
+// alone takes one dependent L2 round trip per 8 entries, and after the first
+// rounds a round holds few vertices, so its slowest row sets its length.
+constexpr int kHeavyRow = 8;
 constexpr int kGiantRow = 512;   // rows longer than this are applied by the whole block
-// The cluster kernel hands rows to a warp from a shorter length: its rounds
-// are few vertices deep after the first, and a thread scanning a row alone
-// takes one dependent L2 round trip per 8 entries.
-constexpr int kClusterWarpRow = 8;
 
 struct RootShared {
     int cnt;        // marks in this round
@@ -309,18 +308,22 @@ struct Root {
         agg_append(&sh.fcnt, next, x, S.try_flag(x));
     }
 
-    // Is w in u's (sorted) row?  Short rows: batched linear scan; else binary search.
+    // Is u-w an edge?  The CSR is symmetric and its rows sorted: search the
+    // shorter of the two rows (batched linear scan, else binary search).
     __device__ bool row_has(int u, int w) const
     {
-        const int a = __ldg(rp + u), b = __ldg(rp + u + 1);
-        if (b - a > 16) return bsearch_row(col + a, b - a, w);
+        const int au = __ldg(rp + u), bu = __ldg(rp + u + 1);
+        const int aw = __ldg(rp + w), bw = __ldg(rp + w + 1);
+        const bool by_u = bu - au <= bw - aw;
+        const int a = by_u ? au : aw, b = by_u ? bu : bw, key = by_u ? w : u;
+        if (b - a > 16) return bsearch_row(col + a, b - a, key);
         for (int e0 = a; e0 < b; e0 += 8) {
             int xs[8];
 #pragma unroll
             for (int j = 0; j < 8; j++) xs[j] = e0 + j < b ? __ldg(col + e0 + j) : -1;
             bool hit = false;
 #pragma unroll
-            for (int j = 0; j < 8; j++) hit |= xs[j] == w;
+            for (int j = 0; j < 8; j++) hit |= xs[j] == key;
             if (hit) return true;
         }
         return false;
@@ -869,7 +872,7 @@ struct ClusterRoot {
         if (dv > bud) mark(v);
         if (dv > 2) return;
         const int a = __ldg(rp + v), b = __ldg(rp + v + 1);
-        if (b - a > kClusterWarpRow) {
+        if (b - a > kHeavyRow) {
             hv[atomicAdd(&sh.hcnt, 1)] = v;
             return;
         }
@@ -1097,7 +1100,7 @@ struct ClusterRoot {
                 const int u = ml[i];
                 const int len = __ldg(rp + u + 1) - __ldg(rp + u);
                 if (len > kGiantRow) hv[vcnt - 1 - atomicAdd(&sh.gcnt, 1)] = u;
-                else if (len > kClusterWarpRow) hv[atomicAdd(&sh.hcnt, 1)] = u;
+                else if (len > kHeavyRow) hv[atomicAdd(&sh.hcnt, 1)] = u;
                 else apply_row(u, 0, 1);
             }
             __syncthreads();
