@@ -83,6 +83,8 @@ def test_options_default_without_gpu(lib):
     import paper_2512_18334_gb300 as vc
     o = vc.options()
     assert o.use_components == 1 and o.load_balance == 1 and o.idle_timeout_ms == 60000
+    assert o.cuda_graph == 1   # the search phase is replayed from a CUDA graph by default
+    assert o.crown == 0 and o.disable_bounds == 0 and o.disable_root_rules == 0 and o.disable_dyn_bounds == 0
 
 
 def test_missing_library_fails_loudly(tmp_path, monkeypatch):
