@@ -181,6 +181,59 @@ def cpu_oracle_run(steps: int, warmup: int):
     return steps / dt, dt / steps * 1e3, size
 
 
+def host_cpu() -> dict:
+    """The host's core count and CPU model, for the CPU baselines."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    if model is None:
+        import platform
+        model = platform.processor() or platform.machine()
+    return {"nproc": os.cpu_count() or 1, "model": model}
+
+
+def cpu_oracle_all_cores(jobs, budget: int = 0, max_s: float = 15.0) -> dict:
+    """The oracle over independent graphs on every host core.  jobs: a list
+    of (graph, k) with k < 0 for a minimum cover.  Threads suffice: the
+    oracle is reentrant C and ctypes releases the GIL during the call.  Jobs
+    are taken in order, a core-count wave at a time, until max_s has passed
+    (a bounded sample); returns the rate over the jobs done."""
+    import concurrent.futures as cf
+    import oracle
+    oracle.build()
+    cores = os.cpu_count() or 1
+
+    def one(job):
+        g, k = job
+        try:
+            if k < 0:
+                oracle.mvc(g.n, g.row_ptr, g.col, node_budget=budget)
+            else:
+                oracle.pvc(g.n, g.row_ptr, g.col, k, node_budget=budget)
+            return 1
+        except oracle.OracleBudgetExceeded:
+            return 0
+
+    done = over = 0
+    t0 = time.perf_counter()
+    with cf.ThreadPoolExecutor(max_workers=cores) as ex:
+        for i in range(0, len(jobs), cores):
+            for r in ex.map(one, jobs[i:i + cores]):
+                done += 1
+                over += 1 - r
+            if time.perf_counter() - t0 > max_s:
+                break
+    dt = time.perf_counter() - t0
+    return {"per_s": round(done / dt, 1), "jobs": done, "of": len(jobs), "over_budget": over,
+            "cores": cores, "s": round(dt, 3)}
+
+
 def reference_main(args, rank, world):
     if rank != 0:
         return
@@ -244,7 +297,8 @@ def extra_workloads(vc, torch, stream, peak):
         "plain_nodes_per_s": round(nodes / (sum(lat) / 1e3), 1),
         "batched_graphs_per_s": round(len(dgs) / (bms / 1e3), 1), "batched_ms": round(bms, 3),
         "batched_nodes_per_s": round(bst["nodes"] / (bms / 1e3), 1),
-        "batched_options": {f: getattr(tuned, f) for f in vc.TUNED_FIELDS}}
+        "batched_options": {f: getattr(tuned, f) for f in vc.TUNED_FIELDS},
+        "cpu_oracle_all_cores": cpu_oracle_all_cores([(g, -1) for g in gs])}
     for d in dgs:
         d.close()
 
@@ -348,6 +402,8 @@ def extra_pvc_batch(vc, stream, count=4096, budget=200_000):
         except vc.VcError as e:
             plain_err[str(e.status)] = plain_err.get(str(e.status), 0) + 1
     plain_s = time.perf_counter() - t0
+    # the oracle on the same sample, over every host core
+    cpu_all = cpu_oracle_all_cores([(mix[solved[int(j) % ns]], ks[int(j)]) for j in sample], budget=budget)
     for d in dms:
         d.close()
     return {"graphs": count, "node_budget_per_query": budget, "mvc_launch_s": round(mvc_s, 3),
@@ -357,7 +413,7 @@ def extra_pvc_batch(vc, stream, count=4096, budget=200_000):
             "covers_failing_edge_check": bad_cover, "batched_nodes_per_s": round(bst["nodes"] / batch_s, 1),
             "batched_options": {f: getattr(tuned, f) for f in vc.TUNED_FIELDS},
             "plain_sample": len(sample), "plain_queries_per_s": round(len(sample) / plain_s, 1),
-            "plain_matching_answers": plain_ok, "plain_errors": plain_err}
+            "plain_matching_answers": plain_ok, "plain_errors": plain_err, "cpu_oracle_all_cores": cpu_all}
 
 
 def extra_component_heavy_full(vc, stream, peak, budget=100_000_000):
@@ -612,7 +668,7 @@ def ours_main(args, rank, world, local_rank):
         v, ms, osize = cpu_oracle_run(steps=2, warmup=0)
         assert osize == size, (osize, size)
         cpu = {"value": round(v, 6), "unit": "graphs/s", "cores": 1, "kind": "oracle",
-               "sample": "2 solves of the same workload graph, single thread"}
+               "sample": "2 solves of the same workload graph, single thread", "host": host_cpu()}
 
     also = None
     if rank == 0 and not args.no_extra:
@@ -624,7 +680,10 @@ def ours_main(args, rank, world, local_rank):
         also = {}
         for name, fn in legs:
             t0 = time.perf_counter()
-            r = fn()
+            try:
+                r = fn()
+            except Exception as e:   # a context leg never takes the headline line down with it
+                r = {"error": f"{type(e).__name__}: {e}"}
             r["wall_s"] = round(time.perf_counter() - t0, 2)
             if name == "small_graphs":
                 also.update(r)
