@@ -7,7 +7,7 @@
 //   reduce  - degree-one, degree-two-triangle and high-degree rules in
 //             synchronous rounds until a fixpoint (Section 2.2);
 //   prune   - |S| >= B or |E| > (B - |S| - 1)^2 with B the Best of the
-//             enclosing component (Algorithm 1, line 3);
+//             enclosing component (the stopping condition of Algorithms 1 and 2);
 //   leaf    - |E| = 0: a new best cover of the component (Algorithm 1, 5-7);
 //   split   - union-find over the live vertices finds the components
 //             (Section 3.2); cliques and chordless cycles are closed at once
@@ -15,7 +15,7 @@
 //             through the registry (Section 3.3);
 //   branch  - on the lowest-index vertex of maximum degree: the right child
 //             G - N(v) is stored (private stack or worklist), the left child
-//             G - v continues in shared memory (Algorithm 1, lines 9-11).
+//             G - v continues in shared memory (the vertex branch of Algorithm 1).
 // Completion decrements LiveNodes of the enclosing component entry; the last
 // descendant adds the component's Best into its parent's Sum and, when the
 // parent's LiveComps reaches zero, updates the ancestor's Best and continues
@@ -905,7 +905,7 @@ struct Worker {
             }
             r2 = tm.bcast(r2);
             if (r2 != 0) return;
-            // parent entry `par` is finished: Algorithm 2 line 20 for its ancestor
+            // parent entry `par` is finished: Algorithm 2's update of its ancestor's Best
             const int anc = vld(Pe.link);
             const int sum = vld(Pe.val);
             int go = 0;
@@ -943,7 +943,7 @@ struct Worker {
 
     // A child c of parent entry `par` finished in a parameterized query:
     // add its Best to Sum; when it was the last child, update the ancestor
-    // from S_P + the children's covers (Algorithm 2 line 20), push that up
+    // from S_P + the children's covers (Algorithm 2's ancestor update), push that up
     // (Section 3.5), free the children and the parent, and return true so the
     // caller continues with the ancestor's LiveNodes.
     __device__ bool complete_pvc_child(int c, int par, int bestc)
@@ -1199,7 +1199,7 @@ struct Worker {
             return kVertexBranch;
         }
 
-        // ---- branch on components (Algorithm 2 lines 14-20, Section 3.3)
+        // ---- branch on components (the component branch of Algorithm 2, Section 3.3)
         // parent entry: Sum = |S| (this node's cover, trivial components
         // included), LiveComps = number of components, witness = S
         int pidx = -1;
@@ -1390,7 +1390,7 @@ struct Worker {
                 }
                 lap(kPhComp);
             }
-            // ---- branch on v_max (Algorithm 1 lines 9-11)
+            // ---- branch on v_max (the vertex branch of Algorithm 1)
             if (vmax < lo || vmax > hi) {                         // cannot happen with edges left
                 if (tm.leader()) set_error(P.ctl, VC_ECAPACITY, 9);
                 tm.sync();
