@@ -88,6 +88,12 @@ typedef struct vc_options {
                                  captured once per launch shape into a CUDA graph
                                  kept with the workspace and replayed with one
                                  launch; 0: its kernels are launched one by one */
+    int32_t capacity_retries; /* when the search runs out of capacity (stack and
+                                 worklist full, registry exhausted), solve again up
+                                 to this many times, each time with the stack depth,
+                                 worklist capacity and registry capacity of the
+                                 failed attempt doubled (default 2; 0: report
+                                 VC_ECAPACITY at once).  vc_autotune does not retry */
 } vc_options;
 
 /* What a solve did.  All counters are totals over the launch. */
@@ -130,6 +136,10 @@ typedef struct vc_stats {
     int32_t cuda_graph;         /* search phase: 0 launched kernel by kernel (or no
                                    search), 1 captured into a graph by this call,
                                    2 replayed from the graph of an earlier call     */
+    int32_t retries;            /* solves repeated with larger capacities
+                                   (opt.capacity_retries); the other fields describe
+                                   the last attempt                                 */
+    int32_t reserved;
 } vc_stats;
 
 /* Fill *opt with the defaults. */

@@ -46,6 +46,7 @@ class Options(ctypes.Structure):
         ("disable_dyn_bounds", ctypes.c_int32),
         ("crown", ctypes.c_int32),
         ("cuda_graph", ctypes.c_int32),
+        ("capacity_retries", ctypes.c_int32),
     ]
 
 
@@ -83,6 +84,8 @@ class Stats(ctypes.Structure):
         ("crown_removed", ctypes.c_int32),
         ("crown_skipped", ctypes.c_int32),
         ("cuda_graph", ctypes.c_int32),
+        ("retries", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
     ]
 
     def to_dict(self) -> dict:

@@ -296,8 +296,16 @@ struct SearchGraphKey {
 
 // Run a set of queries in one root launch + one persistent search launch.
 // covers (nullable) / cover_lens receive the covers.
+// The capacities a solve's search ran with, and the search's status.
+struct SearchCaps {
+    int searched = 0;   // 1: a search ran
+    int depth = 0, wl_cap = 0, reg_cap = 0;   // reg_cap without the per-query root entries
+    int kstatus = 0;
+};
+
 int solve_queries(vc_graph *g0, const std::vector<QueryRef> &qs, const vc_options *opt_in,
-                  std::vector<QueryOut> &out, int32_t *const *covers, int32_t *cover_lens, vc_stats *stats)
+                  std::vector<QueryOut> &out, int32_t *const *covers, int32_t *cover_lens, vc_stats *stats,
+                  SearchCaps *caps = nullptr)
 {
     const auto t_start = std::chrono::steady_clock::now();
     vc_options opt;
@@ -436,6 +444,12 @@ int solve_queries(vc_graph *g0, const std::vector<QueryRef> &qs, const vc_option
             reg_cap = (int)std::min<size_t>((size_t)4 << 20, ((size_t)8 << 30) / per_entry);
             reg_cap = std::max(reg_cap, 64 * pl.workers);
         }
+        if (caps) {
+            caps->searched = 1;
+            caps->depth = depth;
+            caps->wl_cap = wl_cap;
+            caps->reg_cap = reg_cap;
+        }
         reg_cap += nq;
 
         if ((rc = ws.stack.ensure((size_t)pl.workers * depth * pl.slot_bytes)) != VC_OK) return rc;
@@ -524,6 +538,7 @@ int solve_queries(vc_graph *g0, const std::vector<QueryRef> &qs, const vc_option
     VC_CK(cudaEventElapsedTime(&ms_root, ws.ev[0], ws.ev[1]));
 
     const int kstatus = (int)(int64_t)ctlw(hctl_local, kStatus);
+    if (caps) caps->kstatus = kstatus;
     if (want_cov && kstatus == 0) {
         const int32_t *hc = (const int32_t *)ws.hcov.p;
         for (int i = 0; i < nq; i++)
@@ -646,6 +661,7 @@ int vc_options_default(vc_options *opt)
     opt->load_balance = 1;
     opt->idle_timeout_ms = 60000;
     opt->cuda_graph = 1;
+    opt->capacity_retries = 2;
     return VC_OK;
 }
 
@@ -660,6 +676,36 @@ int vc_load_csr_device(int32_t n, const int32_t *d_row_ptr, const int32_t *d_col
     return load_common(n, d_row_ptr, d_col, true, cuda_stream, out);
 }
 
+namespace {
+
+// solve_queries, repeated while the search ran out of capacity (stack and
+// worklist full, registry exhausted): each retry doubles the stack depth,
+// worklist capacity and registry capacity of the attempt that failed, up to
+// opt.capacity_retries times.  stats->retries counts the repeats.
+int solve_with_retries(vc_graph *g0, const std::vector<QueryRef> &qs, const vc_options *opt_in,
+                       std::vector<QueryOut> &out, int32_t *const *covers, int32_t *cover_lens, vc_stats *stats)
+{
+    vc_options o;
+    if (opt_in) o = *opt_in;
+    else vc_options_default(&o);
+    int rc = VC_OK;
+    for (int attempt = 0;; attempt++) {
+        SearchCaps c;
+        rc = solve_queries(g0, qs, &o, out, covers, cover_lens, stats, &c);
+        if (stats) stats->retries = attempt;
+        // (solve_queries returns the search's status, so rc is VC_ECAPACITY here too)
+        const bool out_of_capacity = c.searched && c.kstatus == VC_ECAPACITY;
+        if (!out_of_capacity || attempt >= o.capacity_retries) break;
+        const auto twice = [](int x) { return x > (1 << 29) ? (1 << 30) : 2 * std::max(x, 1); };
+        o.stack_depth = twice(c.depth);
+        o.worklist_capacity = twice(c.wl_cap);
+        o.registry_capacity = twice(c.reg_cap);
+    }
+    return rc;
+}
+
+}  // namespace
+
 int vc_solve_min(vc_graph *g, const vc_options *opt, int32_t *cover_size, int32_t *cover, int32_t *cover_len,
                  vc_stats *stats)
 {
@@ -668,7 +714,7 @@ int vc_solve_min(vc_graph *g, const vc_options *opt, int32_t *cover_size, int32_
     std::vector<QueryOut> out;
     int32_t *covers[1] = {cover};
     int32_t len = 0;
-    int rc = solve_queries(g, qs, opt, out, cover ? covers : nullptr, &len, stats);
+    int rc = solve_with_retries(g, qs, opt, out, cover ? covers : nullptr, &len, stats);
     if (rc != VC_OK) return rc;
     if (out[0].status != VC_OK) return out[0].status;
     *cover_size = out[0].size;
@@ -738,7 +784,7 @@ int vc_solve_mis(vc_graph *g, const vc_options *opt, int32_t *set_size, int32_t 
     std::vector<QueryOut> out;
     int32_t *sets[1] = {set};
     int32_t len = 0;
-    int rc = solve_queries(g, qs, opt, out, set ? sets : nullptr, &len, stats);
+    int rc = solve_with_retries(g, qs, opt, out, set ? sets : nullptr, &len, stats);
     if (rc != VC_OK) return rc;
     if (out[0].status != VC_OK) return out[0].status;
     *set_size = g->n - out[0].size;
@@ -754,7 +800,7 @@ int vc_solve_k(vc_graph *g, int32_t k, const vc_options *opt, int32_t *is_yes, i
     std::vector<QueryOut> out;
     int32_t *covers[1] = {cover};
     int32_t len = 0;
-    int rc = solve_queries(g, qs, opt, out, cover ? covers : nullptr, &len, stats);
+    int rc = solve_with_retries(g, qs, opt, out, cover ? covers : nullptr, &len, stats);
     if (rc != VC_OK) return rc;
     if (out[0].status != VC_OK) return out[0].status;
     *is_yes = out[0].yes;
@@ -774,7 +820,7 @@ int vc_solve_batch(int32_t count, vc_graph *const *graphs, const int32_t *ks, co
         qs[i] = {graphs[i], ks && ks[i] >= 0 ? ks[i] : -1};
     }
     std::vector<QueryOut> out;
-    int rc = solve_queries(graphs[0], qs, opt, out, covers, cover_lens, stats);
+    int rc = solve_with_retries(graphs[0], qs, opt, out, covers, cover_lens, stats);
     for (int i = 0; i < count; i++) {
         if (out_size) out_size[i] = out.empty() ? -1 : out[i].size;
         if (out_yes) out_yes[i] = out.empty() ? 0 : out[i].yes;

@@ -84,6 +84,7 @@ def test_options_default_without_gpu(lib):
     o = vc.options()
     assert o.use_components == 1 and o.load_balance == 1 and o.idle_timeout_ms == 60000
     assert o.cuda_graph == 1   # the search phase is replayed from a CUDA graph by default
+    assert o.capacity_retries == 2
     assert o.crown == 0 and o.disable_bounds == 0 and o.disable_root_rules == 0 and o.disable_dyn_bounds == 0
 
 

@@ -281,11 +281,32 @@ def test_registry_exhaustion_reports_cleanly(vc):
     g = gg.component_heavy(1, copies=8, copy_n=24, p=0.2, chain=3)
     dg = vc.Graph.from_csr(g.row_ptr, g.col)
     with pytest.raises(vc.VcError) as ei:
-        vc.solve_min(dg, registry_capacity=1)
+        vc.solve_min(dg, registry_capacity=1, capacity_retries=0)
     assert ei.value.status == vc.VC_ECAPACITY
     size, _, _ = vc.solve_min(dg)
     dg.close()
     assert size == oracle.mvc(g.n, g.row_ptr, g.col, node_budget=5_000_000)[0]
+
+
+def test_capacity_retries_grow_the_capacities(vc):
+    # a registry of one entry, a two-slot stack and a small worklist: the
+    # solve is repeated with doubled capacities until they suffice; the
+    # answer is exact
+    g = gg.component_heavy(1, copies=8, copy_n=24, p=0.2, chain=3)
+    want = oracle.mvc(g.n, g.row_ptr, g.col, node_budget=5_000_000)[0]
+    dg = vc.Graph.from_csr(g.row_ptr, g.col)
+    try:
+        size, cover, st = vc.solve_min(dg, registry_capacity=1, stack_depth=2, worklist_capacity=64,
+                                       capacity_retries=30)
+        assert size == want and st["retries"] >= 1
+        check_cover(g, cover, size)
+        sizes, _, status, covers, bst = vc.solve_batch([dg, dg], [-1, want], registry_capacity=1,
+                                                       capacity_retries=30)
+        assert list(status) == [vc.VC_OK, vc.VC_OK] and sizes[0] == want and bst["retries"] >= 1
+        for c in covers:
+            check_cover(g, c, len(c))
+    finally:
+        dg.close()
 
 
 @pytest.mark.parametrize("team", [64, 128, 256, 512, 1024])
