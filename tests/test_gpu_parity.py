@@ -307,6 +307,7 @@ def test_capacity_retries_grow_the_capacities(vc):
             check_cover(g, c, len(c))
     finally:
         dg.close()
+        vc.trim()   # hand the grown workspace back to the device
 
 
 @pytest.mark.parametrize("team", [64, 128, 256, 512, 1024])
