@@ -82,12 +82,12 @@ def _p(a):
     return a.ctypes.data_as(ctypes.c_void_p)
 
 
-def verify_cover(n, row_ptr, col, cover_flags) -> bool:
+def verify_cover(n, row_ptr, col, cover_flags, mutant: int = 0) -> bool:
     rp, c = _csr(row_ptr, col)
     f = np.ascontiguousarray(cover_flags, dtype=np.uint8)
     if f.size == 0:
         f = np.zeros(1, np.uint8)
-    return bool(_lib().orc_verify_cover(n, _p(rp), _p(c), _p(f)))
+    return bool(_lib(mutant).orc_verify_cover(n, _p(rp), _p(c), _p(f)))
 
 
 def brute_mvc(n, row_ptr, col, mutant: int = 0):

@@ -12,8 +12,8 @@
  *   orc_verify_cover   definition of a vertex cover            (Section 2.1)
  *   orc_brute_mvc      MVC by its definition: the smallest cover, found by
  *                      enumerating subsets in increasing size  (Section 2.1)
- *   orc_greedy         initial upper bound "computed by an approximate
- *                      algorithm such as a greedy one"         (Section 2.2)
+ *   orc_greedy         the initial upper bound: the size of some cover
+ *                      found quickly and without optimality    (Section 2.2)
  *   orc_mvc            Algorithm 2 (component-aware branch-and-reduce), with
  *                      the three reduction rules of Section 2.2, the stopping
  *                      condition of Algorithm 1/2, and the clique and
@@ -61,8 +61,12 @@ int orc_verify_cover(int n, const int32_t *rp, const int32_t *col, const uint8_t
 {
     for (int v = 0; v < n; v++) {
         if (cover[v]) continue;
-        for (int e = rp[v]; e < rp[v + 1]; e++)
+        for (int e = rp[v]; e < rp[v + 1]; e++) {
             if (!cover[col[e]]) return 0;
+#if ORC_MUTANT == 8
+            return 1;   /* planted: stops after the first edge it checks */
+#endif
+        }
     }
     return 1;
 }

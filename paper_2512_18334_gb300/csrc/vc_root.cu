@@ -664,8 +664,8 @@ struct Root {
             return;
         }
 
-        // initial upper bound (Algorithm 1: "an approximate minimum ... such
-        // as a greedy one")
+        // initial upper bound (Algorithm 1, Section 2.2): the size of a cover
+        // found fast with no optimality claim
         const int greedy_size = sh.forced + greedy();
         t0 = clock64();
         if (threadIdx.x == 0) { Q.greedy = greedy_size; Q.root_cycles[1] = t0 - t1; }

@@ -122,6 +122,77 @@ def test_mvc_all_labelled_graphs(n):
         assert oracle.verify_cover(g.n, g.row_ptr, g.col, cover) and cover.sum() == k
 
 
+def _covers_by_edges(g, flags):
+    """Definition of a cover (Section 2.1) restated with numpy over the edge list."""
+    u, v = gg.edges_of(g)
+    f = np.asarray(flags, dtype=bool)
+    return bool(np.all(f[u] | f[v])) if u.size else True
+
+
+@pytest.mark.parametrize("n", [2, 3, 4, 5])
+def test_verify_rejects_a_minimum_cover_minus_one_vertex(n):
+    # every labelled graph with an edge: drop each vertex of a minimum cover
+    # in turn; the edges to the dropped vertex's non-cover neighbours are bare
+    checked = 0
+    for g in _all_graphs(n):
+        if g.m == 0:
+            continue
+        _, cover = opt(g)
+        for v in np.flatnonzero(cover):
+            bad = cover.copy()
+            bad[v] = 0
+            assert not oracle.verify_cover(g.n, g.row_ptr, g.col, bad)
+            checked += 1
+    assert checked > 0
+
+
+def test_verify_rejects_the_empty_set():
+    for g in [gg.path(2), gg.cycle(5), gg.complete(4), gg.petersen(), gg.gnm(80, 200, 0)]:
+        assert not oracle.verify_cover(g.n, g.row_ptr, g.col, np.zeros(g.n, np.uint8))
+    g = gg.from_edges(4, [], [])
+    assert oracle.verify_cover(g.n, g.row_ptr, g.col, np.zeros(g.n, np.uint8))
+
+
+def test_verify_matches_edge_test_on_random_subsets():
+    rng = np.random.default_rng(11)
+    seen = {True: 0, False: 0}
+    for seed in range(200):
+        n = int(rng.integers(2, 40))
+        g = gg.gnp(n, [0.05, 0.1, 0.2, 0.4][seed % 4], seed)
+        for _ in range(10):
+            flags = (rng.random(n) < rng.uniform(0.3, 0.95)).astype(np.uint8)
+            want = _covers_by_edges(g, flags)
+            assert oracle.verify_cover(g.n, g.row_ptr, g.col, flags) == want
+            seen[want] += 1
+    assert seen[True] > 100 and seen[False] > 100
+
+
+def _verify_pins_fail(mutant):
+    """The negative pins above, run against a (possibly mutant) oracle build."""
+    for n in (3, 4):
+        for g in _all_graphs(n):
+            _, cover = opt(g)
+            for v in np.flatnonzero(cover):
+                bad = cover.copy()
+                bad[v] = 0
+                if oracle.verify_cover(g.n, g.row_ptr, g.col, bad, mutant=mutant):
+                    return True
+    rng = np.random.default_rng(5)
+    for seed in range(40):
+        g = gg.gnp(20, 0.2, seed)
+        flags = (rng.random(g.n) < 0.7).astype(np.uint8)
+        if oracle.verify_cover(g.n, g.row_ptr, g.col, flags, mutant=mutant) != _covers_by_edges(g, flags):
+            return True
+    return False
+
+
+def test_verify_mutant_is_caught():
+    # a planted early acceptance in the cover check (ORC_MUTANT 8) fails the
+    # negative pins; the normal build passes them
+    assert _verify_pins_fail(8)
+    assert not _verify_pins_fail(0)
+
+
 def test_mvc_random_vs_brute():
     rng = np.random.default_rng(7)
     for seed in range(300):
