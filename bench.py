@@ -61,13 +61,13 @@ def solve_options():
     return {}
 
 
-def kernel_traffic(kernel: str):
+def kernel_traffic(kernel: str, workload: str | None = None):
     """DRAM bytes per launch from the committed ncu summary, when it was taken
     on the current source of that kernel (else None)."""
     import hashlib
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
-        rec = json.load(open(path))[WORKLOAD["workload"]]
+        rec = json.load(open(path))[workload or WORKLOAD["workload"]]
     except Exception:
         return None
     if rec.get("kernel") != kernel:
@@ -367,20 +367,76 @@ def cover_ok(g, cover) -> bool:
     return bool(np.all(flags[src] | flags[g.col]))
 
 
-def extra_pvc_batch(vc, stream, count=4096, budget=200_000):
-    """4,096 graphs, n ~ U[40, 1500] (half G(n,p), half Chung-Lu 2.5), each
-    queried at k = opt (yes) and k = opt - 1 (no) in ONE persistent launch.
-    opt comes from a first batched MVC launch under the same per-query node
-    budget; graphs over budget there are dropped and counted."""
-    mix = gg.batch_pvc_mix(count, 11)
+def prepare_pvc_batch(vc, stream, count=4096, budget=200_000, seed=11):
+    """The batched PVC workload: 4,096 graphs, n ~ U[40, 1500] (half G(n,p)
+    with mean degree U[3, 8], half Chung-Lu 2.5), each queried at k = opt
+    (yes) and k = opt - 1 (no).  opt comes from a first batched MVC launch
+    under the same per-query node budget; graphs over budget there are
+    dropped and counted.  Launch options are autotuned on the queries."""
+    mix = gg.batch_pvc_mix(count, seed)
     dms = [vc.Graph.from_csr(h.row_ptr, h.col, stream=stream) for h in mix]
     t0 = time.perf_counter()
-    sizes, _, status, _, _ = vc.solve_batch(dms, node_budget=budget, want_covers=False, raise_on_error=False)
+    sizes, _, status, _, mst = vc.solve_batch(dms, node_budget=budget, want_covers=False, raise_on_error=False)
     mvc_s = time.perf_counter() - t0
     solved = [i for i in range(count) if status[i] == 0]
     qg = [dms[i] for i in solved] * 2
     ks = [int(sizes[i]) for i in solved] + [int(sizes[i]) - 1 for i in solved]
     tuned, _, _ = vc.autotune(qg, ks, repeats=1, node_budget=budget)
+    return {"mix": mix, "dms": dms, "sizes": sizes, "status": status, "solved": solved, "qg": qg, "ks": ks,
+            "tuned": tuned, "mvc_s": mvc_s, "mvc_stats": mst, "budget": budget, "count": count, "seed": seed}
+
+
+def search_block(vc, torch, prep, steps, hbm_peak, hbm_kind, l2_peak, flush):
+    """The persistent search measured on the batched PVC workload at full
+    size: `steps` launches of all its queries (each launch one root phase and
+    one persistent search), L2 flushed before each.  The search kernel's time
+    is its CUDA-event duration on the launching stream (recorded by the
+    library around the launch); nodes/s and algorithmic bytes per node come
+    from the kernel's own counters; the achieved rate is held against the
+    measured HBM copy peak and the L2 read peak measured in this run."""
+    qg, ks, tuned, budget = prep["qg"], prep["ks"], prep["tuned"], prep["budget"]
+    ns = len(prep["solved"])
+    for _ in range(2):   # the second call captures the search phase into a CUDA graph
+        vc.solve_batch(qg, ks, opts=tuned, want_covers=False, raise_on_error=False)
+    ms, wall, nodes, nbytes, wrong, over, launches = [], [], 0, 0, 0, 0, 0
+    for _ in range(steps):
+        flush.fill_(0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, pyes, pst, _, bst = vc.solve_batch(qg, ks, opts=tuned, want_covers=False, raise_on_error=False)
+        wall.append(time.perf_counter() - t0)
+        ok = pst == 0
+        wrong += int(np.sum(ok[:ns] & ~pyes[:ns])) + int(np.sum(ok[ns:] & pyes[ns:]))
+        over += int((pst == vc.VC_EBUDGET).sum())
+        ms.append(bst["ms_search"])
+        nodes += bst["nodes"]
+        nbytes += bst["search_bytes"]
+        launches += bst["launches"]
+    ksec = sum(ms) / 1e3
+    achieved = nbytes / ksec / 1e9
+    return {"workload": "pvc_batch_4096", "graphs": prep["count"], "seed": prep["seed"],
+            "node_budget_per_query": budget, "dropped_over_budget_in_mvc": prep["count"] - ns,
+            "queries": len(qg), "steps": steps, "l2": "256 MiB write before every step",
+            "kernel": "search_kernel", "ms_search_kernel": round(statistics.mean(ms), 3),
+            "nodes_per_launch": nodes // steps, "nodes_per_s": round(nodes / ksec, 1),
+            "queries_per_s": round(len(qg) * steps / sum(wall), 1),
+            "time_to_solution_ms": round(statistics.mean(wall) * 1e3, 3),
+            "over_budget_per_launch": over // steps, "wrong_answers": wrong,
+            "bytes_per_node": round(nbytes / max(1, nodes), 1), "achieved_gbs": round(achieved, 3),
+            "hbm_peak_gbs": hbm_peak, "hbm_peak_kind": hbm_kind, "frac_hbm": round(achieved / hbm_peak, 6),
+            "l2_peak_gbs": round(l2_peak, 1), "l2_peak_kind": "measured in this run (vc_measure_l2_read, 32 MiB)",
+            "frac_l2": round(achieved / l2_peak, 6) if l2_peak > 0 else None,
+            "traffic": kernel_traffic("search_kernel", "pvc_batch_4096"),
+            "options": {f: getattr(tuned, f) for f in vc.TUNED_FIELDS}, "gpu_launches": launches}
+
+
+def extra_pvc_batch(vc, stream, prep):
+    """Batched against plain on the batched PVC workload: one launch for all
+    queries against one launch per query (a 512-query sample), and the
+    oracle over every host core on the same sample."""
+    mix, dms, qg, ks, tuned, budget = prep["mix"], prep["dms"], prep["qg"], prep["ks"], prep["tuned"], prep["budget"]
+    solved = prep["solved"]
+    count = prep["count"]
     vc.solve_batch(qg[:64], ks[:64], opts=tuned, raise_on_error=False)
     t0 = time.perf_counter()
     psz, pyes, pst, covers, bst = vc.solve_batch(qg, ks, opts=tuned, raise_on_error=False)
@@ -404,9 +460,7 @@ def extra_pvc_batch(vc, stream, count=4096, budget=200_000):
     plain_s = time.perf_counter() - t0
     # the oracle on the same sample, over every host core
     cpu_all = cpu_oracle_all_cores([(mix[solved[int(j) % ns]], ks[int(j)]) for j in sample], budget=budget)
-    for d in dms:
-        d.close()
-    return {"graphs": count, "node_budget_per_query": budget, "mvc_launch_s": round(mvc_s, 3),
+    return {"graphs": count, "node_budget_per_query": budget, "mvc_launch_s": round(prep["mvc_s"], 3),
             "dropped_over_budget_in_mvc": count - ns, "queries": len(qg),
             "batched_queries_per_s": round(int(ok.sum()) / batch_s, 1), "batched_s": round(batch_s, 3),
             "batched_over_budget": int((pst == vc.VC_EBUDGET).sum()), "wrong_answers": wrong,
@@ -670,11 +724,19 @@ def ours_main(args, rank, world, local_rank):
         cpu = {"value": round(v, 6), "unit": "graphs/s", "cores": 1, "kind": "oracle",
                "sample": "2 solves of the same workload graph, single thread", "host": host_cpu()}
 
+    # ---- the persistent search on the batched PVC workload (rank 0)
+    search, prep = None, None
+    if rank == 0 and not args.no_search:
+        l2_peak = vc.measure_l2_read(32 << 20, 50, 5, stream=stream)
+        prep = prepare_pvc_batch(vc, stream)
+        search = search_block(vc, torch, prep, args.search_steps, peak, peak_kind, l2_peak, flush)
+        _log(f"search: {json.dumps(search, default=_json_default)}")
+
     also = None
     if rank == 0 and not args.no_extra:
         legs = [("small_graphs", lambda: extra_workloads(vc, torch, stream, peak)),
                 ("served_stream", lambda: extra_served_stream(vc, stream, count=args.stream_requests)),
-                ("pvc_batch_4096", lambda: extra_pvc_batch(vc, stream)),
+                ("pvc_batch_4096", lambda: extra_pvc_batch(vc, stream, prep or prepare_pvc_batch(vc, stream))),
                 ("component_heavy_256x48", lambda: extra_component_heavy_full(vc, stream, peak)),
                 ("ablation", lambda: extra_ablation(vc, stream))]
         also = {}
@@ -709,6 +771,7 @@ def ours_main(args, rank, world, local_rank):
             "e2e": {"value": round(e2e_value, 3), "unit": "graphs/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
             "roofline": roofline,
+            "search": search,
             "cpu_baseline": cpu,
             "clocks": clk,
             "gpu_launches": launches,
@@ -716,6 +779,9 @@ def ours_main(args, rank, world, local_rank):
         }
         print(json.dumps(line, default=_json_default), flush=True)
     dg.close()
+    if prep is not None:
+        for d in prep["dms"]:
+            d.close()
     if world > 1:
         torch.distributed.destroy_process_group()
 
@@ -728,6 +794,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the context workloads")
+    ap.add_argument("--no-search", action="store_true", help="skip the search block (batched PVC workload)")
+    ap.add_argument("--search-steps", type=int, default=3, help="timed launches of the search block")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="chung_lu_50k")
     ap.add_argument("--stream-requests", type=int, default=1000,
                     help="requests in the served-stream context measurement")

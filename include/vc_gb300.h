@@ -88,12 +88,16 @@ typedef struct vc_options {
                                  captured once per launch shape into a CUDA graph
                                  kept with the workspace and replayed with one
                                  launch; 0: its kernels are launched one by one */
-    int32_t capacity_retries; /* when the search runs out of capacity (stack and
-                                 worklist full, registry exhausted), solve again up
-                                 to this many times, each time with the stack depth,
-                                 worklist capacity and registry capacity of the
-                                 failed attempt doubled (default 2; 0: report
-                                 VC_ECAPACITY at once).  vc_autotune does not retry */
+    int32_t capacity_retries; /* when the search runs out of capacity, solve again
+                                 up to this many times (default 2; 0: report
+                                 VC_ECAPACITY at once), doubling only what ran out:
+                                 the stack depth and worklist capacity when both
+                                 were full, the registry capacity when it was
+                                 exhausted.  Growth stops at 24 GB of private
+                                 stacks, 8 GB of worklist and 16 GB of registry
+                                 (worst case about 48 GB for one solve); a solve
+                                 that retried frees its grown buffers before it
+                                 returns.  vc_autotune does not retry */
 } vc_options;
 
 /* What a solve did.  All counters are totals over the launch. */
@@ -399,6 +403,19 @@ int vc_server_get_stats(const vc_server *s, vc_server_stats *st);
 
 /* Release the server and all its memory.  NULL is a no-op. */
 void vc_server_free(vc_server *s);
+
+/* ------------------------------------------------------------------ measurement
+ *
+ * The L2 read bandwidth of the current device: the ceiling of the search
+ * kernel's roofline, since its working set (node slots, registry, induced
+ * CSR) stays in L2 (Section 5 reports throughput; the bandwidth ceiling is
+ * this library's).  Allocates a device buffer of `bytes` (>= 1 MiB; keep it
+ * well inside L2), reads it once to warm L2, then times `trials` launches
+ * of a read kernel (16-byte loads that bypass L1, one pass per rep, `reps`
+ * passes per launch) with CUDA events on `cuda_stream`, and writes the best
+ * rate in GB/s (10^9 bytes) to *gbs.  Frees the buffer before returning.
+ * VC_EINVAL (bad sizes, null gbs), VC_ENOMEM, VC_ECUDA. */
+int vc_measure_l2_read(int64_t bytes, int32_t reps, int32_t trials, void *cuda_stream, double *gbs);
 
 /* Name of the CUDA error behind the last VC_ECUDA / VC_ENOMEM returned on
  * this host thread ("no error" if none). */

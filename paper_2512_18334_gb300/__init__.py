@@ -104,6 +104,14 @@ def trim() -> int:
     return int(_L.lib().vc_trim())
 
 
+def measure_l2_read(bytes_: int = 32 << 20, reps: int = 50, trials: int = 5, stream=None) -> float:
+    """L2 read bandwidth of the current device in GB/s (vc_measure_l2_read)."""
+    out = ctypes.c_double(0.0)
+    _L.check(_L.lib().vc_measure_l2_read(int(bytes_), int(reps), int(trials), _stream_handle(stream),
+                                         ctypes.byref(out)))
+    return float(out.value)
+
+
 def _opts(opts, kw):
     if opts is None:
         return options(**kw)

@@ -197,6 +197,7 @@ SIGNATURES = {
     "vc_server_poll": (ctypes.c_int, [_P, _I, _P, _P, _P, ctypes.c_int64]),
     "vc_server_get_stats": (ctypes.c_int, [_P, _P]),
     "vc_server_free": (None, [_P]),
+    "vc_measure_l2_read": (ctypes.c_int, [ctypes.c_int64, _I, _I, _P, _P]),
 }
 
 

@@ -19,7 +19,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libvc_gb300.so")
-SOURCES = ["vc_root.cu", "vc_search.cu", "vc_api.cu", "vc_serve.cu"]
+SOURCES = ["vc_root.cu", "vc_search.cu", "vc_api.cu", "vc_serve.cu", "vc_peak.cu"]
 HEADERS = ["vc_common.cuh", "vc_internal.h"]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

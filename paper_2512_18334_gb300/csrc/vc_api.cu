@@ -301,6 +301,10 @@ struct SearchCaps {
     int searched = 0;   // 1: a search ran
     int depth = 0, wl_cap = 0, reg_cap = 0;   // reg_cap without the per-query root entries
     int kstatus = 0;
+    int err_where = 0;  // site code of the search's first error
+    int workers = 0, slot_bytes = 0, wcap = 0;
+    int dev = 0;
+    const void *ws = nullptr;   // the workspace the solve borrowed (back in the pool now)
 };
 
 int solve_queries(vc_graph *g0, const std::vector<QueryRef> &qs, const vc_options *opt_in,
@@ -322,6 +326,10 @@ int solve_queries(vc_graph *g0, const std::vector<QueryRef> &qs, const vc_option
     cudaStream_t s = g0->stream;
     WsLease lease(g0->device, s);
     Workspace &ws = *lease.ws;
+    if (caps) {
+        caps->dev = g0->device;
+        caps->ws = lease.ws;
+    }
     int rc;
     if ((rc = ws.init()) != VC_OK) return rc;
 
@@ -449,6 +457,9 @@ int solve_queries(vc_graph *g0, const std::vector<QueryRef> &qs, const vc_option
             caps->depth = depth;
             caps->wl_cap = wl_cap;
             caps->reg_cap = reg_cap;
+            caps->workers = pl.workers;
+            caps->slot_bytes = pl.slot_bytes;
+            caps->wcap = wcap;
         }
         reg_cap += nq;
 
@@ -538,7 +549,10 @@ int solve_queries(vc_graph *g0, const std::vector<QueryRef> &qs, const vc_option
     VC_CK(cudaEventElapsedTime(&ms_root, ws.ev[0], ws.ev[1]));
 
     const int kstatus = (int)(int64_t)ctlw(hctl_local, kStatus);
-    if (caps) caps->kstatus = kstatus;
+    if (caps) {
+        caps->kstatus = kstatus;
+        caps->err_where = (int)ctlw(hctl_local, kErrWhere);
+    }
     if (want_cov && kstatus == 0) {
         const int32_t *hc = (const int32_t *)ws.hcov.p;
         for (int i = 0; i < nq; i++)
@@ -678,10 +692,40 @@ int vc_load_csr_device(int32_t n, const int32_t *d_row_ptr, const int32_t *d_col
 
 namespace {
 
-// solve_queries, repeated while the search ran out of capacity (stack and
-// worklist full, registry exhausted): each retry doubles the stack depth,
-// worklist capacity and registry capacity of the attempt that failed, up to
-// opt.capacity_retries times.  stats->retries counts the repeats.
+// Growth ceilings of capacity retries, in bytes: the private stacks keep the
+// 24 GB clamp of solve_queries; the worklist and the registry stop at these.
+constexpr size_t kRetryWorklistBytes = (size_t)8 << 30;
+constexpr size_t kRetryRegistryBytes = (size_t)16 << 30;
+
+// Drop a workspace that a retried solve grew (it is idle in the pool again
+// unless another solve borrowed it meanwhile), so that its enlarged buffers
+// go back to the device instead of staying cached.
+void drop_workspace(int dev, const void *w)
+{
+    std::lock_guard<std::mutex> lk(pool_mutex());
+    auto &v = pool()[dev];
+    for (size_t i = 0; i < v.size(); i++) {
+        if (v[i] != w) continue;
+        Workspace *x = v[i];
+        v.erase(v.begin() + (long)i);
+        int cur = 0;
+        cudaGetDevice(&cur);
+        if (cur != dev) cudaSetDevice(dev);
+        x->release();
+        delete x;
+        if (cur != dev) cudaSetDevice(cur);
+        return;
+    }
+}
+
+// solve_queries, repeated while the search ran out of capacity, up to
+// opt.capacity_retries times.  Only the resource the kernel reported as
+// exhausted grows (doubled): node slots (site 5: private stack and worklist
+// both full) grow the stack depth and the worklist; registry exhaustion
+// (sites 7, 8) grows the registry; another site grows all three.  Growth
+// stops at the ceilings above; a retry that could grow nothing is not made.
+// After a retried solve its grown workspace is freed.  stats->retries counts
+// the repeats.
 int solve_with_retries(vc_graph *g0, const std::vector<QueryRef> &qs, const vc_options *opt_in,
                        std::vector<QueryOut> &out, int32_t *const *covers, int32_t *cover_lens, vc_stats *stats)
 {
@@ -689,18 +733,35 @@ int solve_with_retries(vc_graph *g0, const std::vector<QueryRef> &qs, const vc_o
     if (opt_in) o = *opt_in;
     else vc_options_default(&o);
     int rc = VC_OK;
-    for (int attempt = 0;; attempt++) {
-        SearchCaps c;
+    int attempt = 0;
+    SearchCaps c;
+    for (;; attempt++) {
+        c = SearchCaps();
         rc = solve_queries(g0, qs, &o, out, covers, cover_lens, stats, &c);
         if (stats) stats->retries = attempt;
         // (solve_queries returns the search's status, so rc is VC_ECAPACITY here too)
         const bool out_of_capacity = c.searched && c.kstatus == VC_ECAPACITY;
         if (!out_of_capacity || attempt >= o.capacity_retries) break;
+        const bool slots = c.err_where == 5, regs = c.err_where == 7 || c.err_where == 8;
+        const bool all = !slots && !regs;
         const auto twice = [](int x) { return x > (1 << 29) ? (1 << 30) : 2 * std::max(x, 1); };
-        o.stack_depth = twice(c.depth);
-        o.worklist_capacity = twice(c.wl_cap);
-        o.registry_capacity = twice(c.reg_cap);
+        bool grew = false;
+        if (slots || all) {
+            o.stack_depth = twice(c.depth);   // clamped to 24 GB by solve_queries
+            grew |= (size_t)o.stack_depth * c.workers * c.slot_bytes <= ((size_t)24 << 30);
+            const int w = twice(c.wl_cap);
+            if ((size_t)w * c.slot_bytes <= kRetryWorklistBytes) { o.worklist_capacity = w; grew = true; }
+        }
+        if (regs || all) {
+            const int r = twice(c.reg_cap);
+            if ((size_t)r * (sizeof(RegEntry) + 4ull * c.wcap) <= kRetryRegistryBytes) {
+                o.registry_capacity = r;
+                grew = true;
+            }
+        }
+        if (!grew) break;
     }
+    if (attempt > 0 && c.ws) drop_workspace(c.dev, c.ws);
     return rc;
 }
 

@@ -292,22 +292,32 @@ def test_capacity_retries_grow_the_capacities(vc):
     # a registry of one entry, a two-slot stack and a small worklist: the
     # solve is repeated with doubled capacities until they suffice; the
     # answer is exact
+    import torch
     g = gg.component_heavy(1, copies=8, copy_n=24, p=0.2, chain=3)
     want = oracle.mvc(g.n, g.row_ptr, g.col, node_budget=5_000_000)[0]
     dg = vc.Graph.from_csr(g.row_ptr, g.col)
     try:
+        vc.solve_min(dg)   # a pooled workspace at the default sizes
+        torch.cuda.synchronize()
+        free0 = torch.cuda.mem_get_info()[0]
         size, cover, st = vc.solve_min(dg, registry_capacity=1, stack_depth=2, worklist_capacity=64,
                                        capacity_retries=30)
         assert size == want and st["retries"] >= 1
         check_cover(g, cover, size)
+        # the retried solve freed the workspace it grew
+        torch.cuda.synchronize()
+        assert torch.cuda.mem_get_info()[0] >= free0 - (64 << 20)
         sizes, _, status, covers, bst = vc.solve_batch([dg, dg], [-1, want], registry_capacity=1,
                                                        capacity_retries=30)
         assert list(status) == [vc.VC_OK, vc.VC_OK] and sizes[0] == want and bst["retries"] >= 1
         for c in covers:
             check_cover(g, c, len(c))
+        # registry exhaustion grows only the registry: a one-entry registry
+        # with ample slots needs retries but reaches the answer
+        size, _, st = vc.solve_min(dg, registry_capacity=1, capacity_retries=30)
+        assert size == want and st["retries"] >= 1
     finally:
         dg.close()
-        vc.trim()   # hand the grown workspace back to the device
 
 
 @pytest.mark.parametrize("team", [64, 128, 256, 512, 1024])
