@@ -332,9 +332,46 @@ __device__ __forceinline__ bool aborted(unsigned long long *ctl)
 // ------------------------------------------------------------------ teams
 //
 // A worker is a "team" of threads that processes one search-tree node at a
-// time: one warp (Team<32>) for small induced graphs, or one thread block
-// (Team<0>, size = blockDim.x) for large ones.  Every team-wide operation
-// below must be reached by all threads of the team.
+// time: one warp (Team<1>) or one thread block (Team<0>, size = blockDim.x).
+// Every team-wide operation below must be reached by all threads of the team
+// in the same order.
+//
+// Block teams combine per-warp partials through shared memory with ONE
+// barrier per operation: the partials go to one of two buffers, alternating
+// from one operation to the next, so a buffer is rewritten only after the
+// barrier of the operation in between (which every thread passes after
+// reading it).  Each warp then combines the partials itself with its lanes.
+
+// Reduction scratch of a block team: 2 buffers x kRedVals values x 32 warps.
+constexpr int kRedVals = 8;
+constexpr int kRedInts = 2 * kRedVals * 32;
+
+// What one round of the reduction rules needs from the whole window.
+struct WinStats {
+    int e2;      // sum of live degrees (2 |E|)
+    int live;    // live vertices
+    int dmax;    // maximum degree (0: none live)
+    int vmax;    // lowest-index vertex of maximum degree (INT_MAX: none)
+    int lo, hi;  // live window (INT_MAX / -1: none)
+};
+
+__device__ __forceinline__ WinStats warp_stats(const WinStats &t)
+{
+    WinStats r;
+    r.e2 = __reduce_add_sync(kFull, t.e2);
+    r.live = __reduce_add_sync(kFull, t.live);
+    r.dmax = __reduce_max_sync(kFull, t.dmax);
+    r.vmax = __reduce_min_sync(kFull, t.dmax == r.dmax ? t.vmax : INT32_MAX);
+    r.lo = __reduce_min_sync(kFull, t.lo);
+    r.hi = __reduce_max_sync(kFull, t.hi);
+    return r;
+}
+
+__device__ __forceinline__ long long warp_lsum(long long x)
+{
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(kFull, x, o);
+    return x;
+}
 
 template <int WARP_TEAM>
 struct Team;
@@ -345,27 +382,25 @@ struct Team<1> {   // one warp per worker
     __device__ __forceinline__ int size() const { return 32; }
     __device__ __forceinline__ void sync() const { __syncwarp(); }
     __device__ __forceinline__ bool leader() const { return rank == 0; }
-    __device__ __forceinline__ int sum(int x) const { return __reduce_add_sync(kFull, x); }
-    __device__ __forceinline__ int max(int x) const { return __reduce_max_sync(kFull, x); }
-    __device__ __forceinline__ int min(int x) const { return __reduce_min_sync(kFull, x); }
-    __device__ __forceinline__ unsigned umax(unsigned x) const { return __reduce_max_sync(kFull, x); }
-    __device__ __forceinline__ long long lmax(long long x) const
+    // Each collective starts with __syncwarp(), so that it also orders the
+    // lanes' earlier shared-memory accesses (as the block barrier does for
+    // block teams).
+    __device__ __forceinline__ int sum(int x) { __syncwarp(); return __reduce_add_sync(kFull, x); }
+    __device__ __forceinline__ int max(int x) { __syncwarp(); return __reduce_max_sync(kFull, x); }
+    __device__ __forceinline__ int min(int x) { __syncwarp(); return __reduce_min_sync(kFull, x); }
+    __device__ __forceinline__ long long lsum(long long x) { __syncwarp(); return warp_lsum(x); }
+    __device__ __forceinline__ WinStats stats(const WinStats &t) { __syncwarp(); return warp_stats(t); }
+    __device__ __forceinline__ int bcast(int x) { __syncwarp(); return __shfl_sync(kFull, x, 0); }
+    __device__ __forceinline__ void bcast2(int &a, int &b)
     {
-        for (int o = 16; o > 0; o >>= 1) {
-            long long y = __shfl_xor_sync(kFull, x, o);
-            x = y > x ? y : x;
-        }
-        return x;
+        __syncwarp();
+        a = __shfl_sync(kFull, a, 0);
+        b = __shfl_sync(kFull, b, 0);
     }
-    __device__ __forceinline__ long long lsum(long long x) const
+    // exclusive prefix of x over the team; the team total in *tot
+    __device__ __forceinline__ int excl_scan(int x, int *tot)
     {
-        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(kFull, x, o);
-        return x;
-    }
-    __device__ __forceinline__ int bcast(int x) const { return __shfl_sync(kFull, x, 0); }
-    // exclusive prefix of flag over the team; returns the team total in *tot
-    __device__ __forceinline__ int excl_scan(int x, int *tot) const
-    {
+        __syncwarp();
         int inc = x;
         for (int o = 1; o < 32; o <<= 1) {
             int y = __shfl_up_sync(kFull, inc, o);
@@ -380,86 +415,117 @@ template <>
 struct Team<0> {   // one block per worker
     int rank;
     int nthreads;
-    long long *red;   // shared scratch, >= 34 long longs
+    int *red;      // kRedInts ints of shared scratch
+    int rb;        // buffer of the next operation (uniform over the team)
     __device__ __forceinline__ int size() const { return nthreads; }
     __device__ __forceinline__ void sync() const { __syncthreads(); }
     __device__ __forceinline__ bool leader() const { return rank == 0; }
-
-    template <class Op>
-    __device__ __forceinline__ long long reduce(long long x, long long ident, Op op) const
+    __device__ __forceinline__ int lane() const { return rank & 31; }
+    __device__ __forceinline__ int warp() const { return rank >> 5; }
+    __device__ __forceinline__ int nwarps() const { return (nthreads + 31) >> 5; }
+    // the next buffer: value k of warp w at [k * 32 + w]
+    __device__ __forceinline__ int *next_buf()
     {
-        for (int o = 16; o > 0; o >>= 1) x = op(x, (long long)__shfl_xor_sync(kFull, x, o));
-        const int w = rank >> 5, l = rank & 31, nw = (nthreads + 31) >> 5;
+        int *b = red + rb * (kRedVals * 32);
+        rb ^= 1;
+        return b;
+    }
+    // lane l of every warp reads value k of warp l (identity beyond the warps)
+    __device__ __forceinline__ int part(const int *b, int k, int ident) const
+    {
+        return lane() < nwarps() ? b[k * 32 + lane()] : ident;
+    }
+    __device__ __forceinline__ int sum(int x)
+    {
+        x = __reduce_add_sync(kFull, x);
+        int *b = next_buf();
+        if (lane() == 0) b[warp()] = x;
         __syncthreads();
-        if (l == 0) red[w] = x;
+        return __reduce_add_sync(kFull, part(b, 0, 0));
+    }
+    __device__ __forceinline__ int max(int x)
+    {
+        x = __reduce_max_sync(kFull, x);
+        int *b = next_buf();
+        if (lane() == 0) b[warp()] = x;
         __syncthreads();
-        if (w == 0) {
-            long long y = l < nw ? red[l] : ident;
-            for (int o = 16; o > 0; o >>= 1) y = op(y, (long long)__shfl_xor_sync(kFull, y, o));
-            if (l == 0) red[33] = y;
+        return __reduce_max_sync(kFull, part(b, 0, INT32_MIN));
+    }
+    __device__ __forceinline__ int min(int x)
+    {
+        x = __reduce_min_sync(kFull, x);
+        int *b = next_buf();
+        if (lane() == 0) b[warp()] = x;
+        __syncthreads();
+        return __reduce_min_sync(kFull, part(b, 0, INT32_MAX));
+    }
+    __device__ __forceinline__ long long lsum(long long x)
+    {
+        x = warp_lsum(x);
+        int *b = next_buf();
+        if (lane() == 0) {
+            b[warp()] = (int)(unsigned)(x & 0xffffffffll);
+            b[32 + warp()] = (int)(x >> 32);
         }
         __syncthreads();
-        return red[33];
+        long long y = 0;
+        if (lane() < nwarps()) y = ((long long)b[32 + lane()] << 32) | (unsigned)b[lane()];
+        return warp_lsum(y);
     }
-    __device__ __forceinline__ int sum(int x) const
+    __device__ __forceinline__ WinStats stats(const WinStats &t)
     {
-        return (int)reduce(x, 0, [](long long a, long long b) { return a + b; });
-    }
-    __device__ __forceinline__ long long lsum(long long x) const
-    {
-        return reduce(x, 0, [](long long a, long long b) { return a + b; });
-    }
-    __device__ __forceinline__ int max(int x) const
-    {
-        return (int)reduce(x, INT32_MIN, [](long long a, long long b) { return a > b ? a : b; });
-    }
-    __device__ __forceinline__ unsigned umax(unsigned x) const
-    {
-        return (unsigned)reduce((long long)x, 0, [](long long a, long long b) { return a > b ? a : b; });
-    }
-    __device__ __forceinline__ int min(int x) const
-    {
-        return (int)reduce(x, INT32_MAX, [](long long a, long long b) { return a < b ? a : b; });
-    }
-    __device__ __forceinline__ long long lmax(long long x) const
-    {
-        return reduce(x, LLONG_MIN, [](long long a, long long b) { return a > b ? a : b; });
-    }
-    __device__ __forceinline__ int bcast(int x) const
-    {
+        WinStats w = warp_stats(t);
+        int *b = next_buf();
+        if (lane() == 0) {
+            const int i = warp();
+            b[i] = w.e2; b[32 + i] = w.live; b[64 + i] = w.dmax;
+            b[96 + i] = w.vmax; b[128 + i] = w.lo; b[160 + i] = w.hi;
+        }
         __syncthreads();
-        if (rank == 0) red[32] = x;
-        __syncthreads();
-        int r = (int)red[32];
-        __syncthreads();
-        return r;
+        WinStats p;
+        p.e2 = part(b, 0, 0);
+        p.live = part(b, 1, 0);
+        p.dmax = part(b, 2, 0);
+        p.vmax = part(b, 3, INT32_MAX);
+        p.lo = part(b, 4, INT32_MAX);
+        p.hi = part(b, 5, -1);
+        return warp_stats(p);
     }
-    __device__ __forceinline__ int excl_scan(int x, int *tot) const
+    __device__ __forceinline__ int bcast(int x)
     {
-        const int w = rank >> 5, l = rank & 31, nw = (nthreads + 31) >> 5;
+        int *b = next_buf();
+        if (rank == 0) b[0] = x;
+        __syncthreads();
+        return b[0];
+    }
+    __device__ __forceinline__ void bcast2(int &x, int &y)
+    {
+        int *b = next_buf();
+        if (rank == 0) { b[0] = x; b[1] = y; }
+        __syncthreads();
+        x = b[0];
+        y = b[1];
+    }
+    __device__ __forceinline__ int excl_scan(int x, int *tot)
+    {
         int inc = x;
         for (int o = 1; o < 32; o <<= 1) {
             int y = __shfl_up_sync(kFull, inc, o);
-            if (l >= o) inc += y;
+            if (lane() >= o) inc += y;
         }
+        int *b = next_buf();
+        if (lane() == 31) b[warp()] = inc;
         __syncthreads();
-        if (l == 31) red[w] = inc;
-        __syncthreads();
-        if (w == 0) {
-            long long y = l < nw ? red[l] : 0;
-            long long s = y;
-            for (int o = 1; o < 32; o <<= 1) {
-                long long z = __shfl_up_sync(kFull, s, o);
-                if (l >= o) s += z;
-            }
-            if (l < nw) red[l] = s - y;   // exclusive warp offsets
-            if (l == 31) red[33] = s;
+        // inclusive scan of the warp totals, by every warp
+        const int y = part(b, 0, 0);
+        int s = y;
+        for (int o = 1; o < 32; o <<= 1) {
+            int z = __shfl_up_sync(kFull, s, o);
+            if (lane() >= o) s += z;
         }
-        __syncthreads();
-        int r = (int)red[w] + inc - x;
-        *tot = (int)red[33];
-        __syncthreads();
-        return r;
+        *tot = __shfl_sync(kFull, s, 31);
+        const int before = __shfl_sync(kFull, s - y, warp());   // exclusive offset of this warp
+        return before + inc - x;
     }
 };
 

@@ -79,13 +79,20 @@ __host__ __device__ inline int worker_array_bytes(int ncap, int wcap)
 {
     return deg_region_bytes<T>(ncap) + align_up(ncap, 16) + ncap * 4 + align_up(wcap * 4, 16);
 }
-constexpr int kWorkerScalarBytes = 128 + 34 * 8;
+// scalars: 16 general ints, the breakdown counters (7 x u64 at int 16), the
+// leader's registry free list and time-slice end (ints 32..36); then the
+// block team's reduction scratch
+constexpr int kWorkerScalarInts = 64;
+__host__ __device__ inline int worker_scalar_bytes(bool warp_team)
+{
+    return kWorkerScalarInts * 4 + (warp_team ? 0 : kRedInts * 4);
+}
 
 // shared-memory bytes of one worker (team)
 template <typename T>
-__host__ __device__ inline int worker_smem_bytes(int ncap, int wcap, bool arrays_global)
+__host__ __device__ inline int worker_smem_bytes(int ncap, int wcap, bool arrays_global, bool warp_team)
 {
-    return (arrays_global ? 0 : worker_array_bytes<T>(ncap, wcap)) + kWorkerScalarBytes;
+    return (arrays_global ? 0 : worker_array_bytes<T>(ncap, wcap)) + worker_scalar_bytes(warp_team);
 }
 
 // ---------------------------------------------------------------- registry
@@ -201,7 +208,8 @@ struct Worker {
     int *lab;         // union-find labels / mark list
     uint32_t *cov;    // cover bitmap of the context window
     int *sc;          // scalars (16 ints)
-    unsigned long long *ph;   // breakdown: cycles per activity [kPhases], last mark [kPhases]
+    // breakdown: cycles per activity [kPhases], last mark [kPhases] (scalars 16..29)
+    __device__ __forceinline__ unsigned long long *ph() const { return (unsigned long long *)(sc + 16); }
 
     const int *csr_s;   // staged CSR in shared memory (single-query launches) or null
 
@@ -212,20 +220,29 @@ struct Worker {
     int gen;          // generation of the node's query slot
     int dpar, danc, dlb;   // dynamic component bound of the context (dpar < 0: none)
     int cntbuf;       // double-buffer index of the mark counter
+    bool stop;        // the search was aborted (seen by process())
+    int qk;           // the node's query: k (< 0: minimum cover)
 
-    // private stack
-    char *stack;
+    // leader only: loads issued ahead for the next node (prefetch())
+    bool pf_ok, pf_dyn;
+    unsigned pf_ab;
+    unsigned long long pf_pk;
+    int pf_bv, pf_av;
+
+    // private stack depth
     int top;
 
-    // private registry free list (leader only)
-    int lf_head, lf_count;
-    long long nodes_local, last_flush;
-    long long qnodes;        // nodes of query qcur not yet added to its counter
+    // the leader's private registry free list and time-slice end live in
+    // shared memory (scalars 32..36), as does the deepest stack seen
+    __device__ __forceinline__ int &lf_head() const { return sc[32]; }
+    __device__ __forceinline__ int &lf_count() const { return sc[33]; }
+    __device__ __forceinline__ unsigned long long &t_end() const { return *(unsigned long long *)(sc + 34); }
+    __device__ __forceinline__ int &max_top() const { return sc[36]; }
+    int nflush;              // nodes since the counters were last flushed
+    int qnodes;              // nodes of query qcur not yet added to its counter
     int qcur;
     long long bytes_local;   // this thread's share of the algorithmic bytes
-    int max_top;
-    unsigned long long t_end;  // end of the time slice (leader; 0: none)
-    bool preempted;            // the slice ended: the node was stored, stop
+    bool preempted;          // the slice ended: the node was stored, stop
 
     __device__ Worker(const SearchParams &p, Team<WT> t, int w, char *smem, const int *csr)
         : P(p), tm(t), wid(w), csr_s(csr)
@@ -237,27 +254,38 @@ struct Worker {
         lab = (int *)a;            a += ncap * 4;
         cov = (uint32_t *)a;       a += align_up(wcap * 4, 16);
         char *s = GA ? smem : a;
-        sc = (int *)s;             s += 128;
-        ph = (unsigned long long *)(sc + 16);
-        if constexpr (WT == 0) tm.red = (long long *)s;
-        stack = P.stack_slots + (size_t)wid * P.stack_depth * P.slot_bytes;
+        sc = (int *)s;             s += kWorkerScalarInts * 4;
+        if constexpr (WT == 0) {
+            tm.red = (int *)s;
+            tm.rb = 0;
+        }
         top = P.stack_top ? P.stack_top[wid] : 0;
         gen = 0;
         dpar = -1;
         danc = -1;
         dlb = 0;
-        t_end = 0;
         preempted = false;
-        nodes_local = 0;
+        stop = false;
+        qk = -1;
+        pf_ok = false;
+        pf_dyn = false;
+        pf_ab = 0;
+        pf_pk = 0;
+        pf_bv = pf_av = 0;
+        nflush = 0;
         bytes_local = 0;
         qnodes = 0;
         qcur = -1;
-        last_flush = 0;
-        max_top = 0;
+
         cntbuf = 0;
-        lf_head = -1;
-        lf_count = 0;
-        if (tm.leader()) { sc[0] = 0; sc[1] = 0; }
+        if (tm.leader()) {
+            sc[0] = 0;
+            sc[1] = 0;
+            lf_head() = -1;
+            lf_count() = 0;
+            t_end() = 0;
+            max_top() = 0;
+        }
         tm.sync();
     }
 
@@ -288,7 +316,27 @@ struct Worker {
         }
     }
 
-    // queue u for the cover in this round (deduplicated); list in lab[]
+    // d[u] = 0 for a vertex that goes into the cover.  Sub-word entries are
+    // cleared with an atomic on their 32-bit word: other threads decrement
+    // the neighbouring entries of the same word with atomics meanwhile.
+    __device__ __forceinline__ void zero_deg(int u)
+    {
+        VC_GUARD(u >= wlo && u <= whi && u - wlo < P.ncap, 6)
+        const int off = u - wlo;
+        if constexpr (sizeof(T) == 1) {
+            atomicAnd((unsigned *)((char *)d + (off & ~3)), ~(0xffu << (8 * (off & 3))));
+        } else if constexpr (sizeof(T) == 2) {
+            atomicAnd((unsigned *)((char *)d + 2 * (off & ~1)), ~(0xffffu << (16 * (off & 1))));
+        } else {
+            d[off] = 0;   // a vertex going into the cover is never decremented
+        }
+    }
+
+    // queue u for the cover in this round (deduplicated); list in lab[].
+    // Mark bytes are cleared only when a node is loaded from a slot: every
+    // marked vertex goes into the cover (degree 0) and stays there for the
+    // rest of the node and its left descendants, so a stale mark is only
+    // ever seen on a vertex whose degree is already 0.
     __device__ __forceinline__ void mark_vertex(int u)
     {
         VC_GUARD(u >= wlo && u <= whi && u - wlo < P.ncap, 2)
@@ -324,6 +372,9 @@ struct Worker {
     // ------------------------------------------------------------ marks
 
     // Put every marked vertex (list lab[0..c)) in the cover: G - M, S + M.
+    // A marked vertex's own entry is cleared by its thread; neighbours that
+    // are marked too are skipped, so each edge between M and the rest is
+    // counted once.  One team barrier.
     __device__ void apply_marks(int c)
     {
         for (int i = tm.rank; i < c; i += tm.size()) {
@@ -334,14 +385,57 @@ struct Worker {
                 const int x = col[e];
                 if (dg(x) > 0 && !marked(x)) dec(x);
             }
+            zero_deg(u);
         }
+        S += c;
         tm.sync();
-        for (int i = tm.rank; i < c; i += tm.size()) {
-            const int u = lab[i];
-            VC_GUARD(u >= wlo && u <= whi && u - wlo < P.ncap, 5)
-            d[u - wlo] = 0;
-            mark[u - wlo] = 0;
+    }
+
+    // Put the single vertex v in the cover (the left child G - v of a vertex
+    // branch).  One team barrier.
+    __device__ void remove_vertex(int v)
+    {
+        for (int e = rp[v] + tm.rank; e < rp[v + 1]; e += tm.size()) {
+            const int x = col[e];
+            if (dg(x) > 0) dec(x);
         }
+        if (tm.leader()) {
+            cov_set(v);
+            zero_deg(v);
+            bytes_local += 8 + 4ll * (rp[v + 1] - rp[v]);
+        }
+        S += 1;
+        tm.sync();
+    }
+
+    // Put every live neighbour of v in the cover (the right child G - N(v)).
+    // The team's threads take the row in the same stripes in both passes:
+    // the first marks the live neighbours and counts them, the second applies
+    // them.  Two team barriers.
+    __device__ void remove_neighbourhood(int v)
+    {
+        int cnt = 0;
+        for (int e = rp[v] + tm.rank; e < rp[v + 1]; e += tm.size()) {
+            const int x = col[e];
+            if (dg(x) > 0) {
+                VC_GUARD(x >= wlo && x <= whi && x - wlo < P.ncap, 2)
+                mark[x - wlo] = 1;
+                cnt++;
+            }
+        }
+        const int c = tm.sum(cnt);
+        for (int e = rp[v] + tm.rank; e < rp[v + 1]; e += tm.size()) {
+            const int x = col[e];
+            if (!marked(x) || dg(x) == 0) continue;
+            cov_set(x);
+            bytes_local += 8 + 4ll * (rp[x + 1] - rp[x]);
+            for (int f = rp[x]; f < rp[x + 1]; f++) {
+                const int y = col[f];
+                if (dg(y) > 0 && !marked(y)) dec(y);
+            }
+            zero_deg(x);
+        }
+        if (tm.leader()) bytes_local += 8 + 4ll * (rp[v + 1] - rp[v]);
         S += c;
         tm.sync();
     }
@@ -352,19 +446,9 @@ struct Worker {
     {
         if (P.breakdown && tm.leader()) {
             const unsigned long long now = clock64();
-            ph[k] += now - ph[kPhases];
-            ph[kPhases] = now;
+            ph()[k] += now - ph()[kPhases];
+            ph()[kPhases] = now;
         }
-    }
-
-    __device__ int take_count()
-    {
-        tm.sync();
-        int c = sc[cntbuf];
-        if (tm.leader()) sc[cntbuf ^ 1] = 0;
-        cntbuf ^= 1;
-        tm.sync();
-        return c;
     }
 
     // ------------------------------------------------------------ reduce
@@ -379,6 +463,9 @@ struct Worker {
     };
 
     // Rules of Section 2.2 in synchronous rounds until no vertex is marked.
+    // Each round is one pass over the window (rules, and the window's
+    // statistics) and one team reduction; a round that marked vertices
+    // applies them (one more barrier) and is followed by another.
     __device__ Stats reduce(int B)
     {
         Stats st;
@@ -392,19 +479,16 @@ struct Worker {
         for (;;) {
             const int bud = B - S - 1;
             if (bud < 0) { st.pruned = 1; return st; }
-            long long e2 = 0;
-            int live = 0;
-            long long key = -1;
-            int nlo = INT_MAX, nhi = -1;
+            WinStats t;
+            t.e2 = 0; t.live = 0; t.dmax = 0; t.vmax = INT32_MAX; t.lo = INT32_MAX; t.hi = -1;
             for (int v = lo + tm.rank; v <= hi; v += tm.size()) {
                 const int dv = (int)d[v - wlo];
                 if (dv == 0) continue;
-                live++;
-                e2 += dv;
-                const long long k = ((long long)dv << 32) | (unsigned)(0x7fffffff - v);
-                key = k > key ? k : key;
-                nlo = min(nlo, v);
-                nhi = max(nhi, v);
+                t.live++;
+                t.e2 += dv;
+                if (dv > t.dmax) { t.dmax = dv; t.vmax = v; }   // ascending v: the lowest wins ties
+                t.lo = min(t.lo, v);
+                t.hi = v;
                 if (dv == 1) {
                     int u = -1;
                     int e = rp[v];
@@ -433,15 +517,20 @@ struct Worker {
                 }
                 if (dv > bud) mark_vertex(v);
             }
-            const int c = take_count();
+            // The reduction is also the barrier after which this round's mark
+            // count is final.  The other counter was last read before the
+            // previous barrier, so the leader may clear it for the next round.
+            const WinStats w = tm.stats(t);
+            const int c = sc[cntbuf];
+            if (tm.leader()) sc[cntbuf ^ 1] = 0;
+            cntbuf ^= 1;
             if (c == 0) {
-                st.e2 = tm.lsum(e2);
-                st.live = tm.sum(live);
-                long long kk = tm.lmax(key);
-                st.dmax = kk < 0 ? 0 : (int)(kk >> 32);
-                st.vmax = kk < 0 ? -1 : 0x7fffffff - (int)(kk & 0xffffffffll);
-                st.lo = tm.min(nlo);
-                st.hi = tm.max(nhi);
+                st.e2 = w.e2;
+                st.live = w.live;
+                st.dmax = w.dmax;
+                st.vmax = w.live > 0 ? w.vmax : -1;
+                st.lo = w.lo;
+                st.hi = w.hi;
                 st.pruned = 0;
                 return st;
             }
@@ -456,7 +545,7 @@ struct Worker {
 #ifdef VC_CHECKS
         if (i < 0 || i >= P.stack_depth) { set_error(P.ctl, VC_ECAPACITY, 107); i = 0; }
 #endif
-        return stack + (size_t)i * P.slot_bytes;
+        return P.stack_slots + ((size_t)wid * P.stack_depth + i) * P.slot_bytes;
     }
 
     // Write the current node (or a component child) into a slot.
@@ -522,26 +611,39 @@ struct Worker {
     __device__ bool read_slot(const char *slot)
     {
         constexpr int V = Vec<T>::kPer16;
-        const NodeHdr *h = (const NodeHdr *)slot;
-        // every thread reads the header (broadcast loads, L2 only: the slot
-        // may have been written by another SM)
-        q = __ldcg(&h->q);
-        gen = __ldcg(&h->gen);
-        int stale = 0;
-        if (tm.leader()) stale = query_is_done(P, q) || vld(P.queries[q].gen) != gen;
-        if (tm.bcast(stale)) return false;
-        S = __ldcg(&h->S); comp = __ldcg(&h->comp); wlo = __ldcg(&h->lo); whi = __ldcg(&h->hi);
-        clo = __ldcg(&h->clo); chi = __ldcg(&h->chi); depth = __ldcg(&h->depth);
-        dpar = __ldcg(&h->dpar); danc = __ldcg(&h->danc); dlb = __ldcg(&h->dlb);
-        const int op = __ldcg(&h->op), cov_empty = __ldcg(&h->cov_empty);
+        // Every thread reads the whole header: four 16-byte loads in flight
+        // at once (L2 only: the slot may have been written by another SM).
+        const int4 *h4 = (const int4 *)slot;
+        const int4 h0 = __ldcg(h4), h1 = __ldcg(h4 + 1), h2 = __ldcg(h4 + 2), h3 = __ldcg(h4 + 3);
+        S = h0.x; comp = h0.y; wlo = h0.z; whi = h0.w;      // NodeHdr field order
+        clo = h1.x; chi = h1.y;
+        const int op = h1.z;
+        q = h1.w;
+        const int cov_empty = h2.x;
+        depth = h2.y; gen = h2.z; dpar = h2.w;
+        danc = h3.x; dlb = h3.y;
         lo = wlo; hi = whi;
 #ifdef VC_CHECKS
         if (!(wlo >= 0 && whi >= wlo && align_up(whi + 1, V) - wlo <= P.ncap && clo <= chi &&
-              (chi >> 5) - (clo >> 5) < P.wcap && comp >= 0 && comp < P.reg_cap && q >= 0 && q < P.nq)) {
+              (chi >> 5) - (clo >> 5) < P.wcap && comp >= 0 && comp < P.reg_cap && q >= 0 && q < P.nq &&
+              (dpar < 0 || (dpar < P.reg_cap && danc >= 0 && danc < P.reg_cap)))) {
             if (tm.leader()) set_error(P.ctl, VC_ECAPACITY, 108);
-            whi = wlo = lo = hi = 0; clo = chi = 0; comp = 0; q = 0;
+            whi = wlo = lo = hi = 0; clo = chi = 0; comp = 0; q = 0; dpar = -1;
         }
 #endif
+        // The leader checks whether the node's request is still live while
+        // the team copies the payload: a stale node's copy is simply dropped
+        // (its window and bitmap were sized for this search's capacities,
+        // so the copy stays inside the worker's arrays either way).
+        int stale = 0;
+        const QueryDesc &Q = P.queries[q];
+        if (tm.leader()) {
+            stale = vld(Q.done) != 0 || vld(Q.gen) != gen;
+            prefetch();
+        }
+        const int qnp = Q.np;
+        qk = Q.k;
+        const int *qrp = Q.rp2, *qcol = Q.col2;
         const int nvec = (align_up(whi + 1, V) - wlo) / V;
         const uint4 *src = (const uint4 *)(slot + sizeof(NodeHdr));
         uint4 *dst = (uint4 *)d;
@@ -553,27 +655,19 @@ struct Worker {
         const int w0 = clo >> 5, nw = (chi >> 5) - w0 + 1;
         const uint32_t *csrc = (const uint32_t *)(slot + sizeof(NodeHdr) + deg_region_bytes<T>(P.ncap));
         for (int i = tm.rank; i < nw; i += tm.size()) cov[i] = cov_empty ? 0u : __ldcg(csrc + i);
+        // (the broadcast is also the barrier after the copies)
+        if (tm.bcast(stale)) return false;
         if (tm.leader()) bytes_local += (long long)sizeof(NodeHdr) + 16ll * nvec + (cov_empty ? 0 : 4ll * nw);
-        const QueryDesc &Q = P.queries[q];
         if (csr_s && q == P.csr_query) {
             rp = csr_s;
-            col = csr_s + Q.np + 1;
+            col = csr_s + qnp + 1;
         } else {
-            rp = Q.rp2;
-            col = Q.col2;
+            rp = qrp;
+            col = qcol;
         }
-        np = Q.np;
-        tm.sync();
-        if (op >= 0) {
-            // right child of a vertex branch: G - N(op), S + N(op)
-            for (int e = rp[op] + tm.rank; e < rp[op + 1]; e += tm.size()) {
-                const int x = col[e];
-                if (dg(x) > 0) mark_vertex(x);
-                bytes_local += 4;
-            }
-            const int c = take_count();
-            apply_marks(c);
-        }
+        np = qnp;
+        // right child of a vertex branch: G - N(op), S + N(op)
+        if (op >= 0) remove_neighbourhood(op);
         return true;
     }
 
@@ -676,16 +770,17 @@ struct Worker {
     __device__ bool push_child(int kind, int op, int root, int clo_c, int chi_c, int comp_c, int S_c, int hi_c,
                                int dpar_c = -1, int danc_c = -1, int dlb_c = 0)
     {
+        // The worklist's level is read at the push itself: a reading taken
+        // when the node started (one node earlier) measurably starved idle
+        // workers (component-heavy 8 x 48: 23% -> 45% idle).
         int to_wl = 0;
-        if (P.load_balance && tm.leader()) {
-            const long long cnt = (long long)*(volatile unsigned long long *)&ctlw(P.ctl, kWlCount);
-            to_wl = cnt < P.wl_low;
-        }
+        if (P.load_balance && tm.leader())
+            to_wl = (long long)*(volatile unsigned long long *)&ctlw(P.ctl, kWlCount) < P.wl_low;
         to_wl = tm.bcast(to_wl);   // uniform decision: the team must take one path
         if (!to_wl && top < P.stack_depth) {
             write_slot(stack_slot(top), kind, op, root, clo_c, chi_c, comp_c, S_c, hi_c, dpar_c, danc_c, dlb_c);
             top++;
-            max_top = max(max_top, top);
+            if (tm.leader()) max_top() = max(max_top(), top);
             tm.sync();
             return true;
         }
@@ -694,7 +789,7 @@ struct Worker {
             if (top < P.stack_depth) {
                 write_slot(stack_slot(top), kind, op, root, clo_c, chi_c, comp_c, S_c, hi_c, dpar_c, danc_c, dlb_c);
                 top++;
-                max_top = max(max_top, top);
+                if (tm.leader()) max_top() = max(max_top(), top);
                 tm.sync();
                 return true;
             }
@@ -712,14 +807,14 @@ struct Worker {
 
     __device__ int reg_alloc()
     {
-        if (lf_head < 0) {
+        if (lf_head() < 0) {
             const int c = reg_chunk_pop(P);
-            if (c >= 0) { lf_head = c; lf_count = *(volatile int *)&P.reg[c].pad[1]; }
+            if (c >= 0) { lf_head() = c; lf_count() = *(volatile int *)&P.reg[c].pad[1]; }
         }
-        if (lf_head >= 0) {
-            const int e = lf_head;
-            lf_head = *(volatile int *)&P.reg[e].next;
-            lf_count--;
+        if (lf_head() >= 0) {
+            const int e = lf_head();
+            lf_head() = *(volatile int *)&P.reg[e].next;
+            lf_count()--;
             return e;
         }
         const int e = (int)atomicAdd(&ctlw(P.ctl, kRegBump), 1ull);
@@ -728,17 +823,17 @@ struct Worker {
 
     __device__ void reg_free(int e)
     {
-        *(volatile int *)&P.reg[e].next = lf_head;
-        lf_head = e;
-        lf_count++;
-        if (lf_count >= 2 * kChunk) {
+        *(volatile int *)&P.reg[e].next = lf_head();
+        lf_head() = e;
+        lf_count()++;
+        if (lf_count() >= 2 * kChunk) {
             // detach the first kChunk entries as one chunk
-            int last = lf_head;
+            int last = lf_head();
             for (int i = 1; i < kChunk; i++) last = *(volatile int *)&P.reg[last].next;
-            const int chunk = lf_head;
-            lf_head = *(volatile int *)&P.reg[last].next;
+            const int chunk = lf_head();
+            lf_head() = *(volatile int *)&P.reg[last].next;
             *(volatile int *)&P.reg[last].next = -1;
-            lf_count -= kChunk;
+            lf_count() -= kChunk;
             reg_chunk_push(P, chunk, kChunk);
         }
     }
@@ -774,13 +869,13 @@ struct Worker {
             E.cur = S;
             atomicExch(&E.val, S);
             reg_unlock(P, comp);
-            if (vld(E.link) < 0 && P.queries[q].k >= 0) query_done(P, q);   // PVC: a cover <= k exists
+            if (vld(E.link) < 0 && qk >= 0) query_done(P, q);   // PVC: a cover <= k exists
         }
         oldcur = tm.bcast(oldcur);
         if (pvc()) pvc_propagate(comp, oldcur, S);
     }
 
-    __device__ __forceinline__ bool pvc() const { return P.queries[q].k >= 0; }
+    __device__ __forceinline__ bool pvc() const { return qk >= 0; }
 
     // Entry a's witness := the parent entry's own cover S_P (its bitmap) plus
     // every child's current cover.  Caller holds a's lock; children are
@@ -931,7 +1026,7 @@ struct Worker {
                     Aw.has_w = 1;
                     atomicExch(&Aw.val, sum);
                     reg_unlock(P, anc);
-                    if (vld(Aw.link) < 0 && P.queries[q].k >= 0) query_done(P, q);
+                    if (vld(Aw.link) < 0 && qk >= 0) query_done(P, q);
                 }
             }
             tm.sync();
@@ -1023,10 +1118,13 @@ struct Worker {
         }
     }
 
-    // Connected components of the live vertices in [lo, hi]; afterwards
-    // lab[i] (i = v - lo) is the smallest relative index of v's component.
-    // Returns the number of components.
-    __device__ int find_components()
+    // Connected components of the live vertices in [lo, hi] (union-find with
+    // hooking to the smaller root, one pass over the live edges).  Returns
+    // the number of components.  With two or more, or when need_labels is
+    // set, lab[i] (i = v - lo) is afterwards the smallest relative index of
+    // v's component (-1 for dead vertices); with one, the labels are left
+    // unfinished (nothing reads them).
+    __device__ int find_components(bool need_labels)
     {
         const int W = hi - lo + 1;
         for (int i = tm.rank; i < W; i += tm.size()) lab[i] = d[lo + i - wlo] > 0 ? i : -1;
@@ -1041,21 +1139,24 @@ struct Worker {
             }
         }
         tm.sync();
-        // Final labels.  Every root is final here, and the walk to it is
-        // read-only: with path halving, a thread still passing through i
-        // could store a stale ancestor into lab[i] after i's final label was
-        // written (seen with block workers as vertices left outside their
-        // component).  Readers of lab[i] now see its old parent or its root.
+        // the roots are final here: one per component
         int roots = 0;
+        for (int i = tm.rank; i < W; i += tm.size()) roots += lab[i] == i;
+        const int nc = tm.sum(roots);
+        if (nc < 2 && !need_labels) return nc;
+        // Final labels.  The walk to the root is read-only: with path
+        // halving, a thread still passing through i could store a stale
+        // ancestor into lab[i] after i's final label was written (seen with
+        // block workers as vertices left outside their component).  Readers
+        // of lab[i] now see its old parent or its root.
         for (int i = tm.rank; i < W; i += tm.size()) {
             if (lab[i] < 0) continue;
             int r = i;
             for (int p = ((volatile int *)lab)[r]; p != r; p = ((volatile int *)lab)[r]) r = p;
             ((volatile int *)lab)[i] = r;
-            roots += (r == i);
         }
         tm.sync();
-        return tm.sum(roots);
+        return nc;
     }
 
     // Cover of a chordless cycle component starting at vertex s: every other
@@ -1077,30 +1178,22 @@ struct Worker {
         }
     }
 
-    // Vertex of maximum degree (lowest index) among live vertices.
-    __device__ int find_vmax()
+    // Statistics of the live vertices in [lo, hi]: degree sum, count,
+    // lowest-index vertex of maximum degree, live window.  One reduction.
+    __device__ WinStats window_stats()
     {
-        long long key = -1;
+        WinStats t;
+        t.e2 = 0; t.live = 0; t.dmax = 0; t.vmax = INT32_MAX; t.lo = INT32_MAX; t.hi = -1;
         for (int v = lo + tm.rank; v <= hi; v += tm.size()) {
             const int dv = (int)d[v - wlo];
             if (dv == 0) continue;
-            const long long k = ((long long)dv << 32) | (unsigned)(0x7fffffff - v);
-            key = k > key ? k : key;
+            t.live++;
+            t.e2 += dv;
+            if (dv > t.dmax) { t.dmax = dv; t.vmax = v; }
+            t.lo = min(t.lo, v);
+            t.hi = v;
         }
-        long long kk = tm.lmax(key);
-        return kk < 0 ? -1 : 0x7fffffff - (int)(kk & 0xffffffffll);
-    }
-
-    // Narrow [lo, hi] to the live vertices.
-    __device__ void shrink_window()
-    {
-        if (P.no_bounds) return;
-        int nlo = INT_MAX, nhi = -1;
-        for (int v = lo + tm.rank; v <= hi; v += tm.size())
-            if (d[v - wlo] > 0) { nlo = min(nlo, v); nhi = max(nhi, v); }
-        nlo = tm.min(nlo);
-        nhi = tm.max(nhi);
-        if (nhi >= 0) { lo = nlo; hi = nhi; }
+        return tm.stats(t);
     }
 
     enum { kComplete = 0, kVertexBranch = 1, kHandedOff = 2, kError = 3 };
@@ -1194,10 +1287,7 @@ struct Worker {
             improve();
             return kComplete;
         }
-        if (nontriv == 1) {
-            shrink_window();
-            return kVertexBranch;
-        }
+        if (nontriv == 1) return kVertexBranch;
 
         // ---- branch on components (the component branch of Algorithm 2, Section 3.3)
         // parent entry: Sum = |S| (this node's cover, trivial components
@@ -1314,32 +1404,52 @@ struct Worker {
     // ------------------------------------------------------------ node
 
     // Process the node now in shared memory and all its left descendants.
+    // The leader's loads for the next node of this context, issued at once
+    // and consumed by process(): the abort flag, the context's Best and the
+    // two words of the dynamic bound.  They are
+    // issued early (when a node is loaded, or before the left child's
+    // vertex is removed) so that their latency overlaps the team's work.
+    // A stale value is safe: Best only decreases, so a stale bound prunes
+    // less, and a late abort costs one more node.
+    __device__ __forceinline__ void prefetch()
+    {
+        // (the low word of the abort flag)
+        pf_ab = *(volatile unsigned *)&ctlw(P.ctl, kAbort);
+        pf_bv = ld_relaxed(&P.reg[comp].val);
+        pf_dyn = dpar >= 0 && !P.no_dyn_bounds;
+        if (pf_dyn) {
+            pf_pk = ld_relaxed_u64((const unsigned long long *)&P.reg[dpar].pad[0]);
+            pf_av = ld_relaxed(&P.reg[danc].val);
+        }
+        pf_ok = true;
+    }
+
+    // Process the node now in shared memory and all its left descendants.
     __device__ void process()
     {
         for (int iter = 0;; iter++) {
             int B = 0;
             if (tm.leader()) {
-                if (aborted(P.ctl)) B = INT_MIN;
-                else if (iter > 0 && t_end && globaltimer() > t_end) B = kPreempt;
+                if (!pf_ok) prefetch();
+                pf_ok = false;
+                if (pf_ab) B = INT_MIN;
+                else if (iter > 0 && P.quantum_ns > 0 && globaltimer() > t_end()) B = kPreempt;
                 else {
-                    B = ld_relaxed(&P.reg[comp].val);
-                    if (dpar >= 0 && !P.no_dyn_bounds && !pvc()) {
+                    B = pf_bv;
+                    if (pf_dyn && qk < 0) {
                         // Best of the enclosing context minus what the parent
                         // and its other children already need: if this
                         // component cannot beat it, the parent's sum cannot
                         // beat the ancestor (every running sibling needs at
                         // least its LB), so no cover is lost
-                        const unsigned long long pk =
-                            ld_relaxed_u64((const unsigned long long *)&P.reg[dpar].pad[0]);
-                        const long long bd = (long long)ld_relaxed(&P.reg[danc].val) -
-                                             (long long)(unsigned)(pk & 0xffffffffull) -
-                                             ((long long)(pk >> 32) - dlb);
+                        const long long bd = (long long)pf_av - (long long)(unsigned)(pf_pk & 0xffffffffull) -
+                                             ((long long)(pf_pk >> 32) - dlb);
                         if (bd < B) B = bd < 0 ? 0 : (int)bd;
                     }
                 }
             }
             B = tm.bcast(B);
-            if (B == INT_MIN) return;   // aborted (decided by the leader for the whole team)
+            if (B == INT_MIN) { stop = true; return; }   // aborted (decided by the leader for the whole team)
             if (B == kPreempt) {
                 // the slice is over: store this node (no pending operation) so
                 // that the next slice resumes it; it stays live in its context
@@ -1348,7 +1458,7 @@ struct Worker {
                 preempted = true;
                 return;
             }
-            nodes_local++;
+            nflush++;
             qnodes++;
             Stats st = reduce(B);
             lap(kPhReduce);
@@ -1378,15 +1488,18 @@ struct Worker {
             }
             int vmax = st.vmax;
             if (P.use_components) {
-                const int ncomp = find_components();
                 const bool clique = (long long)st.live * (st.live - 1) == st.e2;
                 const bool cycle = st.dmax == 2 && st.e2 == 2ll * st.live;
+                const int ncomp = find_components(clique || cycle);
                 if (ncomp >= 2 || clique || cycle) {
                     const int r = handle_components(B);
                     lap(kPhComp);
                     if (r == kComplete) { complete(comp); lap(kPhDone); return; }
                     if (r != kVertexBranch) return;
-                    vmax = find_vmax();
+                    // one non-trivial component is left: its window and v_max
+                    const WinStats w = window_stats();
+                    vmax = w.live > 0 ? w.vmax : -1;
+                    if (!P.no_bounds && w.live > 0) { lo = w.lo; hi = w.hi; }
                 }
                 lap(kPhComp);
             }
@@ -1396,12 +1509,12 @@ struct Worker {
                 tm.sync();
                 return;
             }
-            if (tm.leader()) atomicAdd(&P.reg[comp].live, 1);    // two children replace one node
-            tm.sync();
+            // two children replace one node; the leader's increment precedes
+            // its own publication of the right child (fence, then release)
+            if (tm.leader()) atomicAdd(&P.reg[comp].live, 1);
             if (!push_child(0, vmax, -1, clo, chi, comp, S, hi)) return;
-            if (tm.rank == 0) mark_vertex(vmax);
-            const int c = take_count();
-            apply_marks(c);
+            if (tm.leader()) prefetch();   // for the left child, overlapping its update
+            remove_vertex(vmax);
             depth++;
             lap(kPhBranch);
         }
@@ -1431,19 +1544,19 @@ struct Worker {
         bytes_local = 0;
         if (tm.leader()) {
             atomicAdd(&ctlw(P.ctl, kBytes), (unsigned long long)b);
-            atomicAdd(&ctlw(P.ctl, kNodes), (unsigned long long)(nodes_local - last_flush));
+            atomicAdd(&ctlw(P.ctl, kNodes), (unsigned long long)nflush);
             atomicAdd(&ctlw(P.ctl, kProgress), 1ull);
-            atomicMax(&ctlw(P.ctl, kMaxStack), (unsigned long long)max_top);
+            atomicMax(&ctlw(P.ctl, kMaxStack), (unsigned long long)max_top());
         }
-        last_flush = nodes_local;
+        nflush = 0;
     }
 
     __device__ void run()
     {
-        if (P.quantum_ns > 0 && tm.leader()) t_end = globaltimer() + (unsigned long long)P.quantum_ns;
+        if (P.quantum_ns > 0 && tm.leader()) t_end() = globaltimer() + (unsigned long long)P.quantum_ns;
         if (P.breakdown && tm.leader()) {
-            for (int k = 0; k < kPhases; k++) ph[k] = 0;
-            ph[kPhases] = clock64();
+            for (int k = 0; k < kPhases; k++) ph()[k] = 0;
+            ph()[kPhases] = clock64();
         }
         unsigned long long idle_since = 0, seen_progress = ~0ull;
         int backoff = 32;
@@ -1451,9 +1564,14 @@ struct Worker {
         long long flush_every = 64;
         if (P.node_budget > 0) flush_every = max(1ll, min(64ll, P.node_budget / 64));
         for (;;) {
-            int ab = 0;
-            if (tm.leader()) ab = aborted(P.ctl) || (t_end && globaltimer() > t_end);
-            if (tm.bcast(ab)) break;
+            // process() sees an abort with its first loads; the time slice's
+            // end is read from the SM's clock (no memory access)
+            if (stop) break;
+            if (P.quantum_ns > 0) {
+                int ab = 0;
+                if (tm.leader()) ab = globaltimer() > t_end();
+                if (tm.bcast(ab)) break;
+            }
             // 0 nothing, 1 node loaded, 2 node of a finished request (or of an
             // earlier request of a recycled slot) dropped unexpanded
             int got = 0;
@@ -1484,14 +1602,18 @@ struct Worker {
                     const unsigned long long dt = globaltimer() - tp;
                     if (dt > 100000ull) atomicMax(&ctlw(P.ctl, kMaxProcNs), dt);
                 }
-                if (preempted) break;
-                if (nodes_local - last_flush >= flush_every) flush_counters();
+                if (preempted || stop) break;
+                if (nflush >= flush_every) flush_counters();
                 tm.sync();
                 continue;
             }
             // idle
             int stop = 0;
-            if (tm.leader() && *(volatile unsigned long long *)&ctlw(P.ctl, kRemaining) == 0ull) stop = 2;
+            if (tm.leader()) {
+                const unsigned long long rem = *(volatile unsigned long long *)&ctlw(P.ctl, kRemaining);
+                if (aborted(P.ctl)) stop = 3;
+                else if (rem == 0ull) stop = 2;
+            }
             if (tm.leader() && !stop) {
                 const unsigned long long prog = *(volatile unsigned long long *)&ctlw(P.ctl, kProgress);
                 const unsigned long long now = globaltimer();
@@ -1507,13 +1629,13 @@ struct Worker {
         const unsigned long long tx = tm.leader() ? globaltimer() : 0ull;
         flush_counters();
         if (tm.leader()) {
-            if (lf_count > 0) reg_chunk_push(P, lf_head, lf_count);
-            lf_head = -1;
-            lf_count = 0;
+            if (lf_count() > 0) reg_chunk_push(P, lf_head(), lf_count());
+            lf_head() = -1;
+            lf_count() = 0;
             if (P.stack_top) P.stack_top[wid] = top;
             atomicMax(&ctlw(P.ctl, kMaxExitNs), globaltimer() - tx);
             if (P.breakdown)
-                for (int k = 0; k < kPhases; k++) atomicAdd(&ctlw(P.ctl, kPhase + k), ph[k]);
+                for (int k = 0; k < kPhases; k++) atomicAdd(&ctlw(P.ctl, kPhase + k), ph()[k]);
         }
     }
 };
@@ -1548,7 +1670,7 @@ __global__ void __launch_bounds__(WT ? 256 : 1024, WT ? 3 : 1) search_kernel(con
         Team<1> t;
         t.rank = threadIdx.x & 31;
         static_assert(!GA, "warp workers keep their arrays in shared memory");
-        char *mine = smem + (size_t)warp * align_up(worker_smem_bytes<T>(P.ncap, P.wcap, false), 16);
+        char *mine = smem + (size_t)warp * align_up(worker_smem_bytes<T>(P.ncap, P.wcap, false, true), 16);
         Worker<T, 1> w(P, t, wid, mine, csr);
         w.run();
     } else {
@@ -1734,7 +1856,8 @@ static void launch_search(const SearchPlan &pl, const SearchParams &P, cudaStrea
 template <typename T>
 static int plan_t(int team_req, int ncap, int wcap, int sms, int csr_bytes, SearchPlan *pl)
 {
-    const int wsm = align_up(worker_smem_bytes<T>(ncap, wcap, false), 16);
+    const bool warp = team_req == 32;
+    const int wsm = align_up(worker_smem_bytes<T>(ncap, wcap, false, warp), 16);
     const int kMaxSmem = 227 * 1024 - csr_bytes;
     pl->dtype = sizeof(T);
     pl->slot_bytes = slot_bytes_for<T>(ncap, wcap);
@@ -1742,7 +1865,6 @@ static int plan_t(int team_req, int ncap, int wcap, int sms, int csr_bytes, Sear
     // automatic: 128-thread block workers for induced graphs up to 4,096
     // vertices, 256-thread ones above (measured faster on GB300 than warp
     // workers or 512-thread blocks); warp workers on request
-    bool warp = team_req == 32;
     int bps = 0;
     if (warp) {
         int wpb = kMaxSmem / wsm;
@@ -1765,7 +1887,7 @@ static int plan_t(int team_req, int ncap, int wcap, int sms, int csr_bytes, Sear
             // memory (no staged CSR either)
             pl->wglobal_bytes = ((long long)worker_array_bytes<T>(ncap, wcap) + 255) / 256 * 256;
             pl->csr_bytes = 0;
-            pl->smem = (size_t)align_up(worker_smem_bytes<T>(ncap, wcap, true), 16);
+            pl->smem = (size_t)align_up(worker_smem_bytes<T>(ncap, wcap, true, false), 16);
             if (plan_one<T, 0, true>(pl->threads, pl->smem, &bps) != cudaSuccess) return VC_ECUDA;
         }
     }
