@@ -75,7 +75,7 @@ typedef struct vc_options {
     int32_t breakdown;        /* 1: count SM cycles per activity (vc_stats.phase_cycles) */
     int32_t offload_below;    /* load balancing: a new right child goes to the shared
                                  worklist while it holds fewer items than this;
-                                 0 = half the number of workers */
+                                 0 = four per worker, at most half the worklist */
     int32_t disable_dyn_bounds; /* 1: a component's bound stays the one fixed when it
                                  was registered (no dynamic tightening from the
                                  enclosing Best and the finished siblings) */

@@ -125,7 +125,9 @@ struct NodeHdr {            // 64 bytes; the payload after it stays 16-aligned
     // node's component context, that parent's ancestor, and the context's
     // lower bound (dpar = -1: the context is a root entry)
     int32_t dpar, danc, dlb;
-    int32_t pad[2];
+    int32_t fix;            // 1: the degree array is at a fixpoint of the degree-one
+                            // and degree-two-triangle rules (pending op aside)
+    int32_t pad;
 };
 static_assert(sizeof(NodeHdr) == 64, "node header must stay 64 bytes");
 

@@ -74,10 +74,19 @@ __host__ __device__ inline int slot_bytes_for(int ncap, int wcap)
 // region of global memory (Section 4.1: the degree array is staged in shared
 // memory if it fits); the scalars and the team's reduction scratch always
 // live in shared memory.
+// Capacity of a worker's list of vertices whose degree dropped to 1 or 2
+// since the rules last examined them (more in one round: the next round
+// examines the whole window instead).  Small arrays get one entry per
+// vertex (never full); large ones a fixed 256, so that the list does not
+// cost a block of occupancy (11.7k vertices: three blocks per SM fit with
+// 1 KB, two with 4 KB).
+__host__ __device__ inline int dirty_cap(int ncap) { return ncap <= 1024 ? ncap : 256; }
+
 template <typename T>
 __host__ __device__ inline int worker_array_bytes(int ncap, int wcap)
 {
-    return deg_region_bytes<T>(ncap) + align_up(ncap, 16) + ncap * 4 + align_up(wcap * 4, 16);
+    return deg_region_bytes<T>(ncap) + align_up(ncap, 16) + ncap * 4 + align_up(wcap * 4, 16) +
+           align_up(dirty_cap(ncap) * 4, 16);
 }
 // scalars: 16 general ints, the breakdown counters (7 x u64 at int 16), the
 // leader's registry free list and time-slice end (ints 32..36); then the
@@ -204,9 +213,10 @@ struct Worker {
 
     // shared-memory arrays of this worker
     T *d;             // degrees of vertices [wlo, wlo + ncap)
-    uint8_t *mark;    // mark bytes, same indexing
+    uint8_t *mark;    // per vertex: bit 0 marked for the cover, bit 1 on the dirty list
     int *lab;         // union-find labels / mark list
     uint32_t *cov;    // cover bitmap of the context window
+    int *dl;          // dirty list (dirty_cap(ncap) entries)
     int *sc;          // scalars (16 ints)
     // breakdown: cycles per activity [kPhases], last mark [kPhases] (scalars 16..29)
     __device__ __forceinline__ unsigned long long *ph() const { return (unsigned long long *)(sc + 16); }
@@ -220,6 +230,8 @@ struct Worker {
     int gen;          // generation of the node's query slot
     int dpar, danc, dlb;   // dynamic component bound of the context (dpar < 0: none)
     int cntbuf;       // double-buffer index of the mark counter
+    int dc;           // double-buffer index of the dirty-list counter (scalars 2, 3)
+    bool full;        // the next rule round examines every vertex of the window
     bool stop;        // the search was aborted (seen by process())
     int qk;           // the node's query: k (< 0: minimum cover)
 
@@ -253,6 +265,7 @@ struct Worker {
         mark = (uint8_t *)a;       a += align_up(ncap, 16);
         lab = (int *)a;            a += ncap * 4;
         cov = (uint32_t *)a;       a += align_up(wcap * 4, 16);
+        dl = (int *)a;             a += align_up(dirty_cap(ncap) * 4, 16);
         char *s = GA ? smem : a;
         sc = (int *)s;             s += kWorkerScalarInts * 4;
         if constexpr (WT == 0) {
@@ -278,9 +291,13 @@ struct Worker {
         qcur = -1;
 
         cntbuf = 0;
+        dc = 0;
+        full = true;
         if (tm.leader()) {
             sc[0] = 0;
             sc[1] = 0;
+            sc[2] = 0;
+            sc[3] = 0;
             lf_head() = -1;
             lf_count() = 0;
             t_end() = 0;
@@ -298,21 +315,47 @@ struct Worker {
 
     __device__ __forceinline__ bool marked(int u) const
     {
-        return u >= wlo && u <= whi && mark[u - wlo] != 0;
+        return u >= wlo && u <= whi && (mark[u - wlo] & 1) != 0;
     }
 
-    __device__ __forceinline__ void dec(int u)
+    // Decrement u's degree; returns the new degree.
+    __device__ __forceinline__ int dec(int u)
     {
-        VC_GUARD(u >= wlo && u <= whi && u - wlo < P.ncap, 1)
+        VC_GUARD_R(u >= wlo && u <= whi && u - wlo < P.ncap, 1, 0)
         const int off = u - wlo;
         if constexpr (sizeof(T) == 1) {
             unsigned *w = (unsigned *)((char *)d + (off & ~3));
-            atomicSub(w, 1u << (8 * (off & 3)));
+            const int sh = 8 * (off & 3);
+            return (int)((atomicSub(w, 1u << sh) >> sh) & 0xffu) - 1;
         } else if constexpr (sizeof(T) == 2) {
             unsigned *w = (unsigned *)((char *)d + 2 * (off & ~1));
-            atomicSub(w, 1u << (16 * (off & 1)));
+            const int sh = 16 * (off & 1);
+            return (int)((atomicSub(w, 1u << sh) >> sh) & 0xffffu) - 1;
         } else {
-            atomicSub((unsigned *)&d[off], 1u);
+            return (int)atomicSub((unsigned *)&d[off], 1u) - 1;
+        }
+    }
+
+    // Degree-one and degree-two-triangle candidates.  After a round of the
+    // rules reaches its fixpoint, only a vertex whose degree has dropped to
+    // 1 or 2 since can start to satisfy either rule (edges are never added,
+    // so a degree-two vertex with unchanged degree keeps its neighbours), so
+    // each decrement that leaves 1 or 2 puts the vertex on the dirty list
+    // (once: bit 1 of its mark byte), and a round examines only the list.
+    // A list that overflows makes the next round examine the whole window.
+    // Missing a candidate would cost nodes, never correctness: the rules
+    // only shrink the graph; the high-degree rule, on which the stopping
+    // condition's soundness rests, is checked for every vertex every round.
+    __device__ __forceinline__ void dec_dirty(int u)
+    {
+        const int nd = dec(u);
+        if (nd == 1 || nd == 2) {
+            const int off = u - wlo;
+            const unsigned bit = 2u << (8 * (off & 3));
+            if (!(atomicOr((unsigned *)(mark + (off & ~3)), bit) & bit)) {
+                const int pos = atomicAdd(&sc[2 + dc], 1);
+                if (pos < dirty_cap(P.ncap)) dl[pos] = u;
+            }
         }
     }
 
@@ -371,22 +414,37 @@ struct Worker {
 
     // ------------------------------------------------------------ marks
 
+    // Rows are walked by groups of kGroup lanes: item i of a list goes to
+    // group i mod (team / kGroup), whose lanes take every kGroup-th entry of
+    // its row.  Rows here are a handful of entries long, so one vertex's row
+    // costs about one dependent step instead of one per entry.
+    static constexpr int kGroup = 8;
+    __device__ __forceinline__ int ngroups() const { return tm.size() / kGroup; }
+    __device__ __forceinline__ int group() const { return tm.rank / kGroup; }
+    __device__ __forceinline__ int glane() const { return tm.rank % kGroup; }
+
+    // Put the live vertex u in the cover: decrement its live unmarked
+    // neighbours (the group's lanes share the row) and clear its entry.
+    __device__ __forceinline__ void remove_marked(int u)
+    {
+        for (int e = rp[u] + glane(); e < rp[u + 1]; e += kGroup) {
+            const int x = col[e];
+            if (dg(x) > 0 && !marked(x)) dec_dirty(x);
+        }
+        if (glane() == 0) {
+            cov_set(u);
+            zero_deg(u);
+            bytes_local += 8 + 4ll * (rp[u + 1] - rp[u]);
+        }
+    }
+
     // Put every marked vertex (list lab[0..c)) in the cover: G - M, S + M.
-    // A marked vertex's own entry is cleared by its thread; neighbours that
+    // A marked vertex's own entry is cleared by its group; neighbours that
     // are marked too are skipped, so each edge between M and the rest is
     // counted once.  One team barrier.
     __device__ void apply_marks(int c)
     {
-        for (int i = tm.rank; i < c; i += tm.size()) {
-            const int u = lab[i];
-            cov_set(u);
-            bytes_local += 8 + 4ll * (rp[u + 1] - rp[u]);
-            for (int e = rp[u]; e < rp[u + 1]; e++) {
-                const int x = col[e];
-                if (dg(x) > 0 && !marked(x)) dec(x);
-            }
-            zero_deg(u);
-        }
+        for (int i = group(); i < c; i += ngroups()) remove_marked(lab[i]);
         S += c;
         tm.sync();
     }
@@ -397,7 +455,7 @@ struct Worker {
     {
         for (int e = rp[v] + tm.rank; e < rp[v + 1]; e += tm.size()) {
             const int x = col[e];
-            if (dg(x) > 0) dec(x);
+            if (dg(x) > 0) dec_dirty(x);
         }
         if (tm.leader()) {
             cov_set(v);
@@ -424,16 +482,12 @@ struct Worker {
             }
         }
         const int c = tm.sum(cnt);
-        for (int e = rp[v] + tm.rank; e < rp[v + 1]; e += tm.size()) {
+        for (int e = rp[v] + group(); e < rp[v + 1]; e += ngroups()) {
             const int x = col[e];
-            if (!marked(x) || dg(x) == 0) continue;
-            cov_set(x);
-            bytes_local += 8 + 4ll * (rp[x + 1] - rp[x]);
-            for (int f = rp[x]; f < rp[x + 1]; f++) {
-                const int y = col[f];
-                if (dg(y) > 0 && !marked(y)) dec(y);
-            }
-            zero_deg(x);
+            // marked in the first pass exactly when it was live; only its
+            // own group clears its entry, so the mark alone decides (a
+            // degree test could race with the group's own lane 0)
+            if (marked(x)) remove_marked(x);
         }
         if (tm.leader()) bytes_local += 8 + 4ll * (rp[v + 1] - rp[v]);
         S += c;
@@ -462,10 +516,100 @@ struct Worker {
         int pruned;      // budget exhausted during reduction
     };
 
+    // The degree-one and degree-two-triangle rules at a live vertex v of
+    // degree dv (1 or 2), against the current snapshot; ties are broken
+    // towards the lower vertex so that two rules never put both ends of an
+    // edge (or all of a triangle) in the cover.
+    __device__ __forceinline__ void low_degree_rules(int v, int dv)
+    {
+        if (dv == 1) {
+            int u = -1;
+            int e = rp[v];
+            for (; e < rp[v + 1]; e++) {
+                int x = col[e];
+                if (dg(x) > 0) { u = x; break; }
+            }
+            bytes_local += 8 + 4ll * (e - rp[v] + 1);
+            if (u >= 0 && !(dg(u) == 1 && u < v)) mark_vertex(u);
+        } else {
+            int u = -1, w = -1;
+            int e = rp[v];
+            for (; e < rp[v + 1]; e++) {
+                int x = col[e];
+                if (dg(x) > 0) {
+                    if (u < 0) u = x; else { w = x; break; }
+                }
+            }
+            if (w < 0) return;   // (only while the snapshot is inconsistent; never at a round's start)
+            bytes_local += 16 + 4ll * (e - rp[v] + 1) + 4ll * (32 - __clz(max(1, rp[u + 1] - rp[u])));
+            if (adjacent(u, w) && !((dg(u) == 2 && u < v) || (dg(w) == 2 && w < v))) {
+                mark_vertex(u);
+                mark_vertex(w);
+            }
+        }
+    }
+
+    // low_degree_rules for the dirty vertex v (-1: none) by a group of
+    // kGroup lanes: they read its row in parallel and a ballot finds the
+    // first one or two live neighbours.  Called by every lane of the warp
+    // (the loop below is uniform over the warp: the ballots need it).
+    __device__ void low_degree_group(int v)
+    {
+        int dv = 0, r0 = 0, r1 = 0;
+        if (v >= 0) {
+            const int off = v - wlo;
+            if (glane() == 0) atomicAnd((unsigned *)(mark + (off & ~3)), ~(2u << (8 * (off & 3))));
+            dv = (int)d[off];
+            if (dv == 1 || dv == 2) { r0 = rp[v]; r1 = rp[v + 1]; }
+            else dv = 0;
+        }
+        const int lane = tm.rank & 31, gbase = lane & ~(kGroup - 1);
+        const int nch = dv ? (r1 - r0 + kGroup - 1) / kGroup : 0;
+        const int wmax = __reduce_max_sync(kFull, nch);
+        int u = -1, w = -1, found = 0, scanned = 0;
+        for (int ch = 0; ch < wmax; ch++) {
+            const int e = r0 + ch * kGroup + glane();
+            int x = -1;
+            bool live = false;
+            if (found < dv && e < r1) {
+                x = col[e];
+                live = dg(x) > 0;
+            }
+            const unsigned b = (__ballot_sync(kFull, live) >> gbase) & ((1u << kGroup) - 1);
+            // the first two live entries of this chunk, as lanes of the group
+            const int f1 = b ? __ffs(b) - 1 : 0;
+            const unsigned b2 = b & (b - 1);
+            const int f2 = b2 ? __ffs(b2) - 1 : 0;
+            const int x1 = __shfl_sync(kFull, x, gbase + f1);
+            const int x2 = __shfl_sync(kFull, x, gbase + f2);
+            if (found < dv) {
+                scanned = min(r1 - r0, (ch + 1) * kGroup);
+                if (b) {
+                    if (found == 0) { u = x1; found = 1; if (b2 && dv == 2) { w = x2; found = 2; } }
+                    else if (found == 1) { w = x1; found = 2; }
+                }
+            }
+        }
+        if (dv == 0 || glane() != 0) return;
+        bytes_local += 8 + 4ll * scanned;
+        if (dv == 1) {
+            if (u >= 0 && !(dg(u) == 1 && u < v)) mark_vertex(u);
+        } else if (w >= 0) {
+            bytes_local += 8 + 4ll * (32 - __clz(max(1, rp[u + 1] - rp[u])));
+            if (adjacent(u, w) && !((dg(u) == 2 && u < v) || (dg(w) == 2 && w < v))) {
+                mark_vertex(u);
+                mark_vertex(w);
+            }
+        }
+    }
+
     // Rules of Section 2.2 in synchronous rounds until no vertex is marked.
-    // Each round is one pass over the window (rules, and the window's
-    // statistics) and one team reduction; a round that marked vertices
-    // applies them (one more barrier) and is followed by another.
+    // Each round is one pass over the window (statistics, high-degree rule,
+    // and, in a full round, the low-degree rules at every vertex), a pass
+    // over the dirty list (low-degree rules at the vertices whose degree
+    // dropped to 1 or 2 since the last round) and one team reduction; a
+    // round that marked vertices applies them (one more barrier) and is
+    // followed by another.
     __device__ Stats reduce(int B)
     {
         Stats st;
@@ -479,6 +623,14 @@ struct Worker {
         for (;;) {
             const int bud = B - S - 1;
             if (bud < 0) { st.pruned = 1; return st; }
+            // The dirty list filled since the last round (its counter is
+            // final: a barrier separates every push from this point); the
+            // other counter takes the pushes of this round's application.
+            const int nd = sc[2 + dc];
+            const bool all = full || nd > dirty_cap(P.ncap);
+            full = false;
+            if (tm.leader()) sc[2 + (dc ^ 1)] = 0;
+            dc ^= 1;
             WinStats t;
             t.e2 = 0; t.live = 0; t.dmax = 0; t.vmax = INT32_MAX; t.lo = INT32_MAX; t.hi = -1;
             for (int v = lo + tm.rank; v <= hi; v += tm.size()) {
@@ -489,33 +641,17 @@ struct Worker {
                 if (dv > t.dmax) { t.dmax = dv; t.vmax = v; }   // ascending v: the lowest wins ties
                 t.lo = min(t.lo, v);
                 t.hi = v;
-                if (dv == 1) {
-                    int u = -1;
-                    int e = rp[v];
-                    for (; e < rp[v + 1]; e++) {
-                        int x = col[e];
-                        if (dg(x) > 0) { u = x; break; }
-                    }
-                    bytes_local += 8 + 4ll * (e - rp[v] + 1);
-                    if (u >= 0 && !(dg(u) == 1 && u < v)) mark_vertex(u);
-                } else if (dv == 2) {
-                    int u = -1, w = -1;
-                    int e = rp[v];
-                    for (; e < rp[v + 1]; e++) {
-                        int x = col[e];
-                        if (dg(x) > 0) {
-                            if (u < 0) u = x; else { w = x; break; }
-                        }
-                    }
-                    bytes_local += 16 + 4ll * (e - rp[v] + 1) + 4ll * (32 - __clz(max(1, rp[u + 1] - rp[u])));
-                    if (w >= 0 && adjacent(u, w)) {
-                        if (!((dg(u) == 2 && u < v) || (dg(w) == 2 && w < v))) {
-                            mark_vertex(u);
-                            mark_vertex(w);
-                        }
-                    }
-                }
+                if (all && dv <= 2) low_degree_rules(v, dv);
                 if (dv > bud) mark_vertex(v);
+            }
+            if (!all) {
+                for (int base = 0; base < nd; base += ngroups()) low_degree_group(base + group() < nd ? dl[base + group()] : -1);
+            } else if (nd > 0) {
+                // a full round: every dirty flag goes (the list is dropped)
+                for (int v = lo + tm.rank; v <= hi; v += tm.size()) {
+                    const int off = v - wlo;
+                    if (mark[off] & 2) atomicAnd((unsigned *)(mark + (off & ~3)), ~(2u << (8 * (off & 3))));
+                }
             }
             // The reduction is also the barrier after which this round's mark
             // count is final.  The other counter was last read before the
@@ -576,6 +712,11 @@ struct Worker {
             h->dpar = kind == 0 ? dpar : dpar_c;
             h->danc = kind == 0 ? danc : danc_c;
             h->dlb = kind == 0 ? dlb : dlb_c;
+            // a vertex branch's right child and a component child are stored
+            // from an array the rules brought to their fixpoint; a preempted
+            // node is stored after a vertex removal, before the next rules
+            h->fix = (kind == 1 || op >= 0) ? 1 : 0;
+            h->pad = 0;
         }
         uint4 *dst = (uint4 *)(slot + sizeof(NodeHdr));
         if (tm.leader())
@@ -622,6 +763,7 @@ struct Worker {
         const int cov_empty = h2.x;
         depth = h2.y; gen = h2.z; dpar = h2.w;
         danc = h3.x; dlb = h3.y;
+        const int fix = h3.z;
         lo = wlo; hi = whi;
 #ifdef VC_CHECKS
         if (!(wlo >= 0 && whi >= wlo && align_up(whi + 1, V) - wlo <= P.ncap && clo <= chi &&
@@ -640,7 +782,10 @@ struct Worker {
         if (tm.leader()) {
             stale = vld(Q.done) != 0 || vld(Q.gen) != gen;
             prefetch();
+            sc[2] = 0;   // empty dirty list (the mark bytes are cleared below)
+            sc[3] = 0;
         }
+        full = fix == 0;
         const int qnp = Q.np;
         qk = Q.k;
         const int *qrp = Q.rp2, *qcol = Q.col2;
@@ -1730,7 +1875,7 @@ __global__ void search_roots_kernel(SearchParams P, const int *root_slot)
     if (threadIdx.x == 0) {
         h->S = 0; h->comp = qi; h->lo = 0; h->hi = np - 1; h->clo = 0; h->chi = np - 1;
         h->op = -1; h->q = qi; h->cov_empty = 1; h->depth = 0; h->gen = Q.gen;
-        h->dpar = -1; h->danc = -1; h->dlb = 0;
+        h->dpar = -1; h->danc = -1; h->dlb = 0; h->fix = 0; h->pad = 0;
     }
     T *dd = (T *)(s + sizeof(NodeHdr));
     const int lim = align_up(np, V);
@@ -1809,7 +1954,7 @@ __global__ void serve_place_kernel(SearchParams P, const QueryDesc *staging, con
         NodeHdr *h = (NodeHdr *)s;
         h->S = 0; h->comp = qi; h->lo = 0; h->hi = np - 1; h->clo = 0; h->chi = np - 1;
         h->op = -1; h->q = qi; h->cov_empty = 1; h->depth = 0; h->gen = Q.gen;
-        h->dpar = -1; h->danc = -1; h->dlb = 0;
+        h->dpar = -1; h->danc = -1; h->dlb = 0; h->fix = 0; h->pad = 0;
     }
     T *dd = (T *)(s + sizeof(NodeHdr));
     const int lim = align_up(np, V);
