@@ -765,8 +765,12 @@ struct ClusterRoot {
     const int *rp, *col;
     int ftot;                // cluster-wide forced count (same in every CTA)
     int xround;              // exchange buffer selector
+    // rows of the vertices owned here, staged in shared memory when they fit
+    // (lrp: offsets into lcol, relative to this CTA's first entry); null:
+    // the rows are read from the global CSR
+    const int *lrp, *lcol;
 
-    __device__ ClusterRoot(QueryDesc &q, ClusterShared &s, char *smem, int cs_)
+    __device__ ClusterRoot(QueryDesc &q, ClusterShared &s, char *smem, int cs_, int smem_bytes)
         : Q(q), sh(s), cl(cgx::this_cluster())
     {
         n = Q.n;
@@ -786,6 +790,37 @@ struct ClusterRoot {
         }
         uint32_t *bits = (uint32_t *)(smem + 2 * (size_t)chunk);
         for (int i = threadIdx.x; i < 3 * (chunk / 32); i += blockDim.x) bits[i] = 0;
+        // Stage this CTA's rows: every examination and application of the
+        // rules, the greedy bound and the induced graph read only rows of
+        // vertices owned here (a shared-memory load instead of an L2 round
+        // trip); the triangle test's rows of other vertices stay global.
+        lrp = nullptr;
+        lcol = nullptr;
+        const size_t off = (cluster_smem_bytes(chunk) + 15) & ~(size_t)15;
+        const int e0 = vcnt > 0 ? __ldg(rp + vbeg) : 0, e1 = vcnt > 0 ? __ldg(rp + vbeg + vcnt) : 0;
+        const long long need = 4ll * (chunk + 1) + 4ll * (e1 - e0);
+        if (vcnt > 0 && (long long)off + need <= (long long)smem_bytes) {
+            int *r = (int *)(smem + off), *c = r + chunk + 1;
+            for (int i = threadIdx.x; i <= vcnt; i += blockDim.x) r[i] = __ldg(rp + vbeg + i) - e0;
+            for (int e = threadIdx.x; e < e1 - e0; e += blockDim.x) c[e] = __ldg(col + e0 + e);
+            lrp = r;
+            lcol = c;
+        }
+    }
+
+    // Row of a vertex owned here: entries [a, b) of *cp.
+    __device__ __forceinline__ void own_row(int v, int &a, int &b, const int *&cp) const
+    {
+        if (lcol) {
+            const int i = v - vbeg;
+            a = lrp[i];
+            b = lrp[i + 1];
+            cp = lcol;
+        } else {
+            a = __ldg(rp + v);
+            b = __ldg(rp + v + 1);
+            cp = col;
+        }
     }
 
     // ---- distributed state
@@ -871,7 +906,9 @@ struct ClusterRoot {
         if (dv == 0) return;
         if (dv > bud) mark(v);
         if (dv > 2) return;
-        const int a = __ldg(rp + v), b = __ldg(rp + v + 1);
+        int a, b;
+        const int *cp;
+        own_row(v, a, b, cp);
         if (b - a > kHeavyRow) {
             hv[atomicAdd(&sh.hcnt, 1)] = v;
             return;
@@ -881,7 +918,7 @@ struct ClusterRoot {
             int xs[8];
             bool lv[8];
 #pragma unroll
-            for (int j = 0; j < 8; j++) xs[j] = e0 + j < b ? __ldg(col + e0 + j) : -1;
+            for (int j = 0; j < 8; j++) xs[j] = e0 + j < b ? cp[e0 + j] : -1;
 #pragma unroll
             for (int j = 0; j < 8; j++) lv[j] = xs[j] >= 0 && live(xs[j]);
 #pragma unroll
@@ -898,13 +935,15 @@ struct ClusterRoot {
     __device__ void warp_live_nbrs(int v, int need, int &u, int &w) const
     {
         const int lane = threadIdx.x & 31;
-        const int a = __ldg(rp + v), b = __ldg(rp + v + 1);
+        int a, b;
+        const int *cp;
+        own_row(v, a, b, cp);
         u = -1;
         w = -1;
         int found = 0;
         for (int base0 = a; base0 < b && found < need; base0 += 32) {
             const int e = base0 + lane;
-            const int x = e < b ? __ldg(col + e) : -1;
+            const int x = e < b ? cp[e] : -1;
             unsigned m = __ballot_sync(kFull, x >= 0 && live(x));
             while (m && found < need) {
                 const int pos = __ffs(m) - 1;
@@ -920,13 +959,15 @@ struct ClusterRoot {
     // next frontier (forced bits already include this round's marks)
     __device__ void apply_row(int u, int lane, int stride)
     {
-        const int a = __ldg(rp + u), b = __ldg(rp + u + 1);
+        int a, b;
+        const int *cp;
+        own_row(u, a, b, cp);
         if (stride == 1) {
             for (int e0 = a; e0 < b; e0 += 8) {
                 int xs[8];
                 bool lv[8];
 #pragma unroll
-                for (int j = 0; j < 8; j++) xs[j] = e0 + j < b ? __ldg(col + e0 + j) : -1;
+                for (int j = 0; j < 8; j++) xs[j] = e0 + j < b ? cp[e0 + j] : -1;
 #pragma unroll
                 for (int j = 0; j < 8; j++) lv[j] = xs[j] >= 0 && live(xs[j]);
 #pragma unroll
@@ -936,7 +977,7 @@ struct ClusterRoot {
             return;
         }
         for (int e = a + lane; e < b; e += stride) {
-            const int x = __ldg(col + e);
+            const int x = cp[e];
             if (live(x)) { dec(x); push_frontier(x); }
         }
     }
@@ -1009,6 +1050,39 @@ struct ClusterRoot {
         __syncthreads();
     }
 
+    // The same exchange in two halves around a barrier the caller passes
+    // anyway: publish() writes this CTA's four numbers, collect() (after the
+    // next cluster barrier) reduces every CTA's into sh.tot.
+    __device__ void publish(long long a0, long long a1, long long a2, long long a3)
+    {
+        const int buf = xround & 1;
+        xround++;
+        if (threadIdx.x == 0) {
+            int *sl = shp(0)->slot[buf][rank];
+            sl[0] = (int)a0; sl[1] = (int)a1; sl[2] = (int)a2; sl[3] = (int)a3;
+        }
+    }
+    __device__ void collect()
+    {
+        const int buf = (xround - 1) & 1;
+        if (threadIdx.x < 32) {
+            const int l = threadIdx.x;
+            long long v0 = 0, v1 = 0, v2 = 0, v3 = INT_MIN;
+            if (l < C) {
+                const volatile int *sl = shp(0)->slot[buf][l];
+                v0 = sl[0]; v1 = sl[1]; v2 = sl[2]; v3 = sl[3];
+            }
+            for (int o = 16; o > 0; o >>= 1) {
+                v0 += __shfl_xor_sync(kFull, v0, o);
+                v1 += __shfl_xor_sync(kFull, v1, o);
+                v2 += __shfl_xor_sync(kFull, v2, o);
+                v3 = max(v3, (long long)__shfl_xor_sync(kFull, v3, o));
+            }
+            if (l == 0) { sh.tot[0] = v0; sh.tot[1] = v1; sh.tot[2] = v2; sh.tot[3] = v3; }
+        }
+        __syncthreads();
+    }
+
     // Prefix over ranks of two per-CTA values (exclusive) and their totals.
     __device__ void exchange_prefix(int mine, int mine2, int &off, int &tot, int &off2, int &tot2)
     {
@@ -1035,24 +1109,34 @@ struct ClusterRoot {
         __syncthreads();
     }
 
-    // Synchronous rounds, three cluster barriers each:
-    //   B1  last round's decrements and frontier bits have landed
-    //   B2  this round's marks and partner bits have landed (inside exchange)
-    //   B3  totals known, forced bits include this round's marks
+    // Synchronous rounds, two cluster barriers each:
+    //   B1  last round's decrements and frontier bits have landed, and its
+    //       totals (published before B1) are read: stop when it marked
+    //       nothing and left no frontier
+    //   B2  this round's marks and partner bits have landed
     __device__ bool reduce_rounds(bool hd, int bound)
     {
         int *fl = Q.fr0 + vbeg;        // my frontier list
         int *ml = Q.heavy + vbeg;      // my marks of this round
         int *hv = Q.aux + vbeg;        // heavy rows (front) / giant rows (back)
         const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
-        bool first = true;
+        bool first = true, last_full = false;
         long long delta = INT_MAX;
         for (;;) {
+            cl.sync();                                                    // B1
+            if (!first) {
+                collect();
+                const long long tcnt = sh.tot[0], tpend = sh.tot[1];
+                if (last_full) delta = sh.tot[3];
+                ftot += (int)tcnt;
+                if (rank == 0 && threadIdx.x == 0) Q.forced = ftot;
+                if (tcnt == 0 && tpend == 0) return true;
+            }
             const int bud = hd ? bound - ftot - 1 : INT_MAX;
             if (hd && bud < 0) return false;
             const bool full = first || (hd && delta > bud);
             first = false;
-            cl.sync();                                                    // B1
+            last_full = full;
             if (threadIdx.x == 0) { sh.hcnt = 0; sh.gcnt = 0; }
             const int fsize = bits_to_list(flagp(rank), fl, false);       // my frontier
             int dmax = 0;
@@ -1084,21 +1168,20 @@ struct ClusterRoot {
                 for (int i = threadIdx.x; i < chunk / 32; i += blockDim.x) pend += __popc(fw[i]);
                 pend = block_sum(pend, sh.red);
             }
-            exchange(cnt, pend, 0, dm);                                   // B3
-            const long long tcnt = sh.tot[0], tpend = sh.tot[1];
-            if (full) delta = sh.tot[3];
+            publish(cnt, pend, 0, dm);   // read by every CTA after the next B1
             if (rank == 0 && threadIdx.x == 0) Q.rounds++;
-            if (tcnt == 0 && tpend == 0) return true;
-            // append my marks to the forced list
-            __shared__ int fbase;
-            if (threadIdx.x == 0) fbase = cnt ? atomicAdd(&Q.forced, cnt) : 0;
+            if (cnt == 0) continue;
+            // (the forced set is the forced bitmap here; Q.forced gets its
+            // size when the rounds end)
             if (threadIdx.x == 0) { sh.hcnt = 0; sh.gcnt = 0; }
             __syncthreads();
-            for (int i = threadIdx.x; i < cnt; i += blockDim.x) Q.forced_list[fbase + i] = ml[i];
             // apply: short rows by one thread, long by a warp, giant by the block
             for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
                 const int u = ml[i];
-                const int len = __ldg(rp + u + 1) - __ldg(rp + u);
+                int a, b;
+                const int *cp;
+                own_row(u, a, b, cp);
+                const int len = b - a;
                 if (len > kGiantRow) hv[vcnt - 1 - atomicAdd(&sh.gcnt, 1)] = u;
                 else if (len > kHeavyRow) hv[atomicAdd(&sh.hcnt, 1)] = u;
                 else apply_row(u, 0, 1);
@@ -1107,7 +1190,6 @@ struct ClusterRoot {
             const int hc2 = sh.hcnt, gc = sh.gcnt;
             for (int i = warp; i < hc2; i += nwarps) apply_row(hv[i], lane, 32);
             for (int i = 0; i < gc; i++) apply_row(hv[vcnt - 1 - i], threadIdx.x, blockDim.x);
-            ftot += (int)tcnt;
             __syncthreads();
         }
     }
@@ -1135,8 +1217,11 @@ struct ClusterRoot {
                 if (__ldcg(aux + v) != 0) continue;
                 const unsigned long long pv = ((unsigned long long)d(v) << 32) | mix32((unsigned)v);
                 bool j = true;
-                for (int e = __ldg(rp + v); e < __ldg(rp + v + 1) && j; e++) {
-                    const int x = __ldg(col + e);
+                int a, b;
+                const int *cp;
+                own_row(v, a, b, cp);
+                for (int e = a; e < b && j; e++) {
+                    const int x = cp[e];
                     const int ax = ((volatile int *)aux)[x];
                     if (ax == 1) j = false;
                     else if (ax == 0) {
@@ -1157,7 +1242,10 @@ struct ClusterRoot {
             for (int i = threadIdx.x; i < vcnt; i += blockDim.x) {
                 const int v = vbeg + i;
                 if (__ldcg(aux + v) != 4) continue;
-                for (int e = __ldg(rp + v); e < __ldg(rp + v + 1); e++) atomicCAS(&aux[__ldg(col + e)], 0, 2);
+                int a, b;
+                const int *cp;
+                own_row(v, a, b, cp);
+                for (int e = a; e < b; e++) atomicCAS(&aux[cp[e]], 0, 2);
             }
             cl.sync();
             for (int i = threadIdx.x; i < vcnt; i += blockDim.x)
@@ -1219,8 +1307,11 @@ struct ClusterRoot {
         for (int i = coff + threadIdx.x; i < coff + lnp; i += T) {
             const int v = Q.orig[i];
             int o = Q.rp2[i];
-            for (int e = __ldg(rp + v); e < __ldg(rp + v + 1); e++) {
-                const int nx = ((volatile int *)nid)[__ldg(col + e)];
+            int a, b;
+            const int *cp;
+            own_row(v, a, b, cp);
+            for (int e = a; e < b; e++) {
+                const int nx = ((volatile int *)nid)[cp[e]];
                 if (nx >= 0) Q.col2[o++] = nx;
             }
         }
@@ -1349,13 +1440,13 @@ struct ClusterRoot {
     }
 };
 
-__global__ void __launch_bounds__(kRootThreads, 1) root_cluster_kernel(QueryDesc *qs, int cs)
+__global__ void __launch_bounds__(kRootThreads, 1) root_cluster_kernel(QueryDesc *qs, int cs, int smem_bytes)
 {
     extern __shared__ __align__(16) char root_smem[];
     __shared__ ClusterShared sh;
     QueryDesc &Q = qs[0];
     if (Q.status != VC_OK) return;   // uniform across the cluster
-    ClusterRoot r(Q, sh, root_smem, cs);
+    ClusterRoot r(Q, sh, root_smem, cs, smem_bytes);
     cgx::this_cluster().sync();      // remote addresses and zeroed bitmaps everywhere
     r.run();
     cgx::this_cluster().sync();      // nobody leaves while others may touch its shared memory
@@ -1839,7 +1930,7 @@ cudaError_t root_run(QueryDesc *d_q, int nq, int max_n, int max_deg, cudaStream_
             cudaLaunchConfig_t probe = {};
             probe.gridDim = dim3(C, 1, 1);
             probe.blockDim = dim3(kRootThreads, 1, 1);
-            probe.dynamicSmemBytes = cluster_smem_bytes(1 << cs);
+            probe.dynamicSmemBytes = kRootSmemMax;   // (the rows are staged in what is left)
             cudaLaunchAttribute pa[1];
             pa[0].id = cudaLaunchAttributeClusterDimension;
             pa[0].val.clusterDim.x = C;
@@ -1865,7 +1956,7 @@ cudaError_t root_run(QueryDesc *d_q, int nq, int max_n, int max_deg, cudaStream_
     }
     if (cs >= 0) {
         const int C = (int)((max_n + (1 << cs) - 1) >> cs);
-        const size_t smem = cluster_smem_bytes(1 << cs);
+        const size_t smem = kRootSmemMax;   // one CTA per SM in any case: room for staged rows
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3(C, 1, 1);
         cfg.blockDim = dim3(kRootThreads, 1, 1);
@@ -1878,7 +1969,7 @@ cudaError_t root_run(QueryDesc *d_q, int nq, int max_n, int max_deg, cudaStream_
         attr[0].val.clusterDim.z = 1;
         cfg.attrs = attr;
         cfg.numAttrs = 1;
-        return cudaLaunchKernelEx(&cfg, root_cluster_kernel, d_q, cs);
+        return cudaLaunchKernelEx(&cfg, root_cluster_kernel, d_q, cs, (int)smem);
     }
     const size_t smem = SmemStore::smem_bytes(max_n);
     if (max_deg <= 65535 && smem <= kRootSmemMax) {
