@@ -297,9 +297,13 @@ int vc_trim(void);
  *      on the device and written to mapped host memory, and their slots and
  *      arena space are freed.
  * The answer of a request does not depend on what else is in flight; it is
- * the answer vc_solve_min / vc_solve_k give for the same graph.  The
- * resident search accepts induced subgraphs of up to max_induced vertices
- * (after the root reduction); a larger one finishes with VC_ECAPACITY.
+ * the answer vc_solve_min / vc_solve_k give for the same graph.  Requests
+ * are served in size classes by the size of their induced subgraph (after
+ * the root reduction): up to max_induced vertices, and up to
+ * max_induced_large; each class has a resident search of its own (node
+ * slots sized for it), and every step runs one time slice of each class
+ * that has work.  An induced subgraph above the largest class finishes with
+ * VC_ECAPACITY.
  *
  * Threading: a server is not thread-safe; one host thread drives it.
  */
@@ -317,7 +321,10 @@ typedef struct vc_server_config {
     int32_t use_components;    /* default 1 */
     int32_t load_balance;      /* default 1 */
     int32_t idle_timeout_ms;   /* default 60000 */
-    int32_t reserved;
+    int32_t max_induced_large; /* a second size class: induced graphs larger than
+                                  max_induced and up to this many vertices go to a
+                                  resident search of their own, sized for them
+                                  (default 20000; 0 or <= max_induced: none) */
     int64_t arena_bytes;       /* device memory for admitted requests (default 2 GiB) */
     int64_t node_budget;       /* per request (0: none); VC_EBUDGET when exceeded */
     int64_t cover_buffer;      /* int32 entries of the mapped cover buffer (default 16M) */
@@ -350,7 +357,8 @@ typedef struct vc_server_stats {
     double ms_admit;           /* device time: validation, root phase, placement */
     double ms_search;          /* device time of the search slices */
     double ms_retire;          /* device time of finalisation */
-    int32_t workers, team, dtype_bytes, max_induced;
+    int32_t workers, team, dtype_bytes, max_induced;   /* (of the small class; max_induced:
+                                                           the largest class's capacity) */
     int32_t slot_bytes, max_stack;
     int64_t device_bytes;      /* device memory held by the server */
     int64_t wait_polls;        /* polls of worklist sequence words (contention) */
@@ -378,12 +386,14 @@ int vc_server_create(const vc_server_config *cfg, void *cuda_stream, vc_server *
 int vc_server_submit(vc_server *s, int32_t n, const int32_t *row_ptr, const int32_t *col, int32_t k,
                      int64_t tag);
 
-/* One scheduling iteration (admit, one search slice, retire); blocks until
- * the device finished it.  *completed (nullable) receives the number of
- * requests retired by this step.  A device-side failure (a bounded wait
- * expired, stack / worklist / registry full) ends every request in flight
- * with that status and empties the resident state; the server stays usable
- * and the step returns VC_OK.  VC_ECUDA / VC_ENOMEM are returned as such. */
+/* One scheduling iteration (admit, one search slice per size class with
+ * work, retire); blocks until the device finished it.  *completed (nullable)
+ * receives the number of requests retired by this step.  A request whose
+ * search runs out of node slots or registry entries finishes alone with
+ * VC_ECAPACITY; the others continue.  A bounded wait that expires
+ * (VC_ETIMEOUT) ends every request in flight in that size class and empties
+ * its resident state.  The server stays usable and the step returns VC_OK.
+ * VC_ECUDA / VC_ENOMEM are returned as such. */
 int vc_server_step(vc_server *s, int32_t *completed);
 
 /* Counts of queued (not yet admitted), in-flight and retired-but-not-polled

@@ -116,7 +116,7 @@ class ServerConfig(ctypes.Structure):
         ("use_components", ctypes.c_int32),
         ("load_balance", ctypes.c_int32),
         ("idle_timeout_ms", ctypes.c_int32),
-        ("reserved", ctypes.c_int32),
+        ("max_induced_large", ctypes.c_int32),
         ("arena_bytes", ctypes.c_int64),
         ("node_budget", ctypes.c_int64),
         ("cover_buffer", ctypes.c_int64),

@@ -92,6 +92,7 @@ struct QueryDesc {
     int *cover_list;     // ascending original ids (device, >= n)
     int *cover_out;      // non-null: finalisation writes the same list here too
                          // (mapped host memory, >= n entries)
+    int lane;            // served requests: the size class whose resident search holds it
 };
 
 // One served request as seen after a time slice, written by the device into
@@ -106,7 +107,7 @@ struct RetireRec {
     long long cover_off;   // offset in the cover buffer, -1: buffer full (retry)
     long long nodes;
     int np;
-    int pad;
+    int lane;              // size class of the request (its resident search)
 };
 
 // ------------------------------------------------------------------ nodes

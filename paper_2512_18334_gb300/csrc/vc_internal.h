@@ -121,8 +121,11 @@ cudaError_t search_slice_run(const SearchPlan &pl, const SearchParams &P, cudaSt
 cudaError_t search_reset_run(const SearchParams &P, int first, cudaStream_t s);
 // Place na root-reduced descriptors (device staging array) into their slots
 // and push the root nodes of those that need a search.
+// (lane: the size class placing; it takes the requests with min_np < np <=
+// max_np, lane 0 also the settled ones, the last lane also the larger ones)
 cudaError_t serve_place_run(const SearchPlan &pl, const SearchParams &P, const QueryDesc *d_staging,
-                            const int *d_slot_idx, int na, int max_np, cudaStream_t s);
+                            const int *d_slot_idx, int na, int max_np, int lane, int min_np, int last,
+                            cudaStream_t s);
 
 // ---- served requests (vc_root.cu)
 // Validate na staged CSR graphs (one block each); a malformed one gets
@@ -132,10 +135,13 @@ cudaError_t serve_validate_run(QueryDesc *d_staging, int na, cudaStream_t s);
 // For each active slot: if its request is finished, finalise the answer and
 // cover (as finalize_run) and copy the cover to cover_out at an offset taken
 // from *cover_ctr (device counter, zeroed by the caller).  Block 0 also
-// copies the control block's first words to ctl_out (mapped).
+// copies the control block's first words to ctl_out (mapped).  Only the
+// slots of size class `lane` are handled (reg / reg_words / wcap / ctl are
+// that class's); the others keep their records for their own class.
 cudaError_t serve_retire_run(QueryDesc *d_slots, const int *active, int nactive, const RegEntry *reg,
                              const uint32_t *reg_words, int wcap, RetireRec *rec, int *cover_out,
                              long long cover_cap, unsigned long long *cover_ctr,
-                             const unsigned long long *ctl, unsigned long long *ctl_out, cudaStream_t s);
+                             const unsigned long long *ctl, unsigned long long *ctl_out, int lane,
+                             cudaStream_t s);
 
 }  // namespace vcg

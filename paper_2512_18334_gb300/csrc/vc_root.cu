@@ -1805,7 +1805,7 @@ __global__ void __launch_bounds__(kRootThreads) serve_validate_kernel(QueryDesc 
 __global__ void __launch_bounds__(kRootThreads) serve_retire_kernel(
     QueryDesc *slots, const int *active, int nactive, const RegEntry *reg, const uint32_t *reg_words, int wcap,
     RetireRec *rec, int *cover_out, long long cover_cap, unsigned long long *cover_ctr,
-    const unsigned long long *ctl, unsigned long long *ctl_out)
+    const unsigned long long *ctl, unsigned long long *ctl_out, int lane)
 {
     __shared__ int red[33];
     __shared__ long long s_off;
@@ -1814,9 +1814,10 @@ __global__ void __launch_bounds__(kRootThreads) serve_retire_kernel(
     if ((int)blockIdx.x >= nactive) return;
     const int qi = active[blockIdx.x];
     QueryDesc &Q = slots[qi];
+    if (Q.lane != lane) return;   // another size class retires it (uniform over the block)
     RetireRec &R = rec[blockIdx.x];
     if (!Q.done) {
-        if (threadIdx.x == 0) { R.slot = qi; R.state = 0; }
+        if (threadIdx.x == 0) { R.slot = qi; R.state = 0; R.lane = lane; }
         return;
     }
     const bool ok = Q.status == VC_OK;
@@ -1839,6 +1840,7 @@ __global__ void __launch_bounds__(kRootThreads) serve_retire_kernel(
         R.cover_off = fits ? off : -1;
         R.nodes = Q.nodes;
         R.np = Q.np;
+        R.lane = lane;
     }
 }
 
@@ -2010,10 +2012,10 @@ cudaError_t serve_validate_run(QueryDesc *d_staging, int na, cudaStream_t s)
 cudaError_t serve_retire_run(QueryDesc *d_slots, const int *active, int nactive, const RegEntry *reg,
                              const uint32_t *reg_words, int wcap, RetireRec *rec, int *cover_out,
                              long long cover_cap, unsigned long long *cover_ctr,
-                             const unsigned long long *ctl, unsigned long long *ctl_out, cudaStream_t s)
+                             const unsigned long long *ctl, unsigned long long *ctl_out, int lane, cudaStream_t s)
 {
     serve_retire_kernel<<<nactive > 0 ? nactive : 1, kRootThreads, 0, s>>>(
-        d_slots, active, nactive, reg, reg_words, wcap, rec, cover_out, cover_cap, cover_ctr, ctl, ctl_out);
+        d_slots, active, nactive, reg, reg_words, wcap, rec, cover_out, cover_cap, cover_ctr, ctl, ctl_out, lane);
     return cudaGetLastError();
 }
 

@@ -909,6 +909,21 @@ struct Worker {
         return loaded ? 1 : 2;
     }
 
+    // The search ran out of node slots or registry entries (leader only).
+    // A single solve stops as a whole (the caller may retry with larger
+    // capacities).  A resident search of served requests ends only the
+    // request that needed the room: it finishes with VC_ECAPACITY, its
+    // remaining nodes are dropped when taken, and the others continue.
+    __device__ void capacity_error(int site)
+    {
+        if (P.stack_top) {
+            atomicCAS(&P.queries[q].status, VC_OK, VC_ECAPACITY);
+            query_done(P, q);
+        } else {
+            set_error(P.ctl, VC_ECAPACITY, site);
+        }
+    }
+
     // Store a child: the worklist when it is hungry (load balancing,
     // Section 2.3), else the private stack, else the worklist.  Returns false
     // on overflow (error already recorded).
@@ -938,7 +953,7 @@ struct Worker {
                 tm.sync();
                 return true;
             }
-            if (tm.leader()) set_error(P.ctl, VC_ECAPACITY, 5);
+            if (tm.leader()) capacity_error(5);
             tm.sync();
             return false;
         }
@@ -1440,7 +1455,7 @@ struct Worker {
         int pidx = -1;
         if (tm.leader()) {
             pidx = reg_alloc();
-            if (pidx < 0) set_error(P.ctl, VC_ECAPACITY, 7);
+            if (pidx < 0) capacity_error(7);
         }
         pidx = tm.bcast(pidx);
         if (pidx < 0) return kError;
@@ -1494,7 +1509,7 @@ struct Worker {
                     int cidx = -1;
                     if (tm.leader()) {
                         cidx = reg_alloc();
-                        if (cidx < 0) set_error(P.ctl, VC_ECAPACITY, 8);
+                        if (cidx < 0) capacity_error(8);
                     }
                     cidx = tm.bcast(cidx);
                     if (cidx < 0) return kError;
@@ -1901,16 +1916,28 @@ __global__ void search_roots_publish(SearchParams P, int nroots)
 // worklist tickets are taken without contention.  A request whose induced
 // graph exceeds the resident node capacity or the degree type finishes with
 // VC_ECAPACITY; one settled by the root phase (or rejected) is done at once.
+//
+// Size classes: every class has a resident search of its own (its own node
+// capacity, worklist and registry) and runs this kernel over all admitted
+// requests; a class places the requests whose induced graph has more than
+// min_np and at most max_np vertices, class 0 also those the root phase
+// settled or rejected, and the last class rejects what exceeds it.
 template <typename T>
-__global__ void serve_place_kernel(SearchParams P, const QueryDesc *staging, const int *slot_idx, int max_np)
+__global__ void serve_place_kernel(SearchParams P, const QueryDesc *staging, const int *slot_idx, int max_np,
+                                   int lane, int min_np, int last)
 {
     __shared__ long long s_t;
     __shared__ int s_ok;
     constexpr int V = Vec<T>::kPer16;
+    const QueryDesc &Sg = staging[blockIdx.x];
+    const bool settled = Sg.status != VC_OK || Sg.answered || Sg.np <= 0;
+    const bool mine = settled ? lane == 0 : ((Sg.np > min_np && Sg.np <= max_np) || (last && Sg.np > max_np));
+    if (!mine) return;   // (uniform over the block)
     const int qi = slot_idx[blockIdx.x];
     QueryDesc &Q = P.queries[qi];
     if (threadIdx.x == 0) {
         Q = staging[blockIdx.x];
+        Q.lane = lane;
         int ok = Q.status == VC_OK && !Q.answered && Q.np > 0;
         const bool fits_t = sizeof(T) >= 4 || Q.maxdeg <= (int)((1u << (8 * sizeof(T))) - 1u);
         if (ok && (Q.np > max_np || !fits_t)) {
@@ -2093,13 +2120,14 @@ cudaError_t search_reset_run(const SearchParams &P, int first, cudaStream_t s)
 }
 
 cudaError_t serve_place_run(const SearchPlan &pl, const SearchParams &P, const QueryDesc *d_staging,
-                            const int *d_slot_idx, int na, int max_np, cudaStream_t s)
+                            const int *d_slot_idx, int na, int max_np, int lane, int min_np, int last,
+                            cudaStream_t s)
 {
     if (na <= 0) return cudaSuccess;
     switch (pl.dtype) {
-    case 1: serve_place_kernel<uint8_t><<<na, 256, 0, s>>>(P, d_staging, d_slot_idx, max_np); break;
-    case 2: serve_place_kernel<uint16_t><<<na, 256, 0, s>>>(P, d_staging, d_slot_idx, max_np); break;
-    default: serve_place_kernel<uint32_t><<<na, 256, 0, s>>>(P, d_staging, d_slot_idx, max_np); break;
+    case 1: serve_place_kernel<uint8_t><<<na, 256, 0, s>>>(P, d_staging, d_slot_idx, max_np, lane, min_np, last); break;
+    case 2: serve_place_kernel<uint16_t><<<na, 256, 0, s>>>(P, d_staging, d_slot_idx, max_np, lane, min_np, last); break;
+    default: serve_place_kernel<uint32_t><<<na, 256, 0, s>>>(P, d_staging, d_slot_idx, max_np, lane, min_np, last); break;
     }
     return cudaGetLastError();
 }

@@ -17,6 +17,7 @@
 // id map, state and cover arrays) lives in the arena until it retires.
 #include <algorithm>
 #include <chrono>
+#include <climits>
 #include <cstring>
 #include <deque>
 #include <map>
@@ -110,6 +111,7 @@ struct Request {
 
 struct Slot {
     bool busy = false;
+    int lane = 0;          // size class holding the request (known after its first step)
     int gen = 0;
     int64_t tag = 0;
     int n = 0;
@@ -124,16 +126,37 @@ struct Done {
 
 }  // namespace
 
+// One size class: a resident search of its own, for induced graphs of more
+// than the previous class's capacity and at most max_np vertices.
+struct Lane {
+    int max_np = 0, min_np = 0;
+    SearchPlan pl{};
+    SearchParams P{};
+    int ncap = 0, wcap = 0;
+    DevBuf stack, wl, wl_seq, reg, reg_words, comp_scratch, ctl, stack_top, wglobal;
+    HostBuf m_ctl;                               // mapped: control words after a step
+    unsigned long long snap[kCtlEntries] = {};   // control words after the last step
+    long long base_nodes = 0, base_bytes = 0;    // counters accumulated before resets
+    long long base_waits = 0, base_preempts = 0;
+    bool dirty = false;                          // resident state holds work of earlier requests
+    void release()
+    {
+        for (DevBuf *b : {&stack, &wl, &wl_seq, &reg, &reg_words, &comp_scratch, &ctl, &stack_top, &wglobal})
+            b->release();
+        m_ctl.release();
+    }
+};
+constexpr int kMaxLanes = 2;
+
 struct vc_server {
     int device = 0, sms = 0;
     cudaStream_t stream = nullptr;
     vc_server_config cfg{};
-    SearchPlan pl{};
-    SearchParams P{};
-    int ncap = 0, wcap = 0;
-    DevBuf stack, wl, wl_seq, reg, reg_words, comp_scratch, ctl, stack_top, slots, admit, arena, cover_ctr, wglobal;
-    HostBuf h_up;                          // pinned: the packed admission upload
-    HostBuf m_rec, m_cover, m_ctl, m_act;  // mapped: retire records, covers, control words, active slots
+    Lane lane[kMaxLanes];
+    int nlanes = 0;
+    DevBuf slots, admit, arena, cover_ctr;
+    HostBuf h_up;                   // pinned: the packed admission upload
+    HostBuf m_rec, m_cover, m_act;  // mapped: retire records, covers, active slots
     cudaEvent_t ev[6] = {};
     std::deque<Request> queue;
     std::vector<Slot> slot;
@@ -142,10 +165,6 @@ struct vc_server {
     Arena arena_alloc;
     std::deque<Done> ready;
     vc_server_stats st{};
-    unsigned long long snap[kCtlEntries] = {};   // control words after the last step
-    long long base_nodes = 0, base_bytes = 0;    // counters accumulated before resets
-    long long base_waits = 0, base_preempts = 0;
-    bool dirty = false;                          // resident state holds work of earlier requests
     std::chrono::steady_clock::time_point t0;
 
     double now_ms() const
@@ -155,10 +174,9 @@ struct vc_server {
 
     void release()
     {
-        for (DevBuf *b : {&stack, &wl, &wl_seq, &reg, &reg_words, &comp_scratch, &ctl, &stack_top, &slots, &admit,
-                          &arena, &cover_ctr, &wglobal})
-            b->release();
-        for (HostBuf *b : {&h_up, &m_rec, &m_cover, &m_ctl, &m_act}) b->release();
+        for (Lane &L : lane) L.release();
+        for (DevBuf *b : {&slots, &admit, &arena, &cover_ctr}) b->release();
+        for (HostBuf *b : {&h_up, &m_rec, &m_cover, &m_act}) b->release();
         for (auto &e : ev)
             if (e) { cudaEventDestroy(e); e = nullptr; }
     }
@@ -166,19 +184,19 @@ struct vc_server {
 
 namespace {
 
-// Empty the resident search state (worklist, counters, registry allocator,
-// stack depths); registry entries [0, max_inflight) stay reserved as the
-// slots' root entries.
-int reset_state(vc_server *s)
+// Empty a class's resident search state (worklist, counters, registry
+// allocator, stack depths); registry entries [0, max_inflight) stay reserved
+// as the slots' root entries.
+int reset_state(vc_server *s, Lane &L)
 {
-    s->base_nodes += (long long)s->snap[kNodes];
-    s->base_bytes += (long long)s->snap[kBytes];
-    s->base_waits += (long long)s->snap[kWaitIters];
-    s->base_preempts += (long long)s->snap[kPreempts];
-    SV_CK(search_reset_run(s->P, s->cfg.max_inflight, s->stream));
-    SV_CK(cudaMemsetAsync(s->stack_top.p, 0, s->stack_top.bytes, s->stream));
-    memset(s->snap, 0, sizeof(s->snap));
-    s->dirty = false;
+    L.base_nodes += (long long)L.snap[kNodes];
+    L.base_bytes += (long long)L.snap[kBytes];
+    L.base_waits += (long long)L.snap[kWaitIters];
+    L.base_preempts += (long long)L.snap[kPreempts];
+    SV_CK(search_reset_run(L.P, s->cfg.max_inflight, s->stream));
+    SV_CK(cudaMemsetAsync(L.stack_top.p, 0, L.stack_top.bytes, s->stream));
+    memset(L.snap, 0, sizeof(L.snap));
+    L.dirty = false;
     s->st.resets++;
     return VC_OK;
 }
@@ -205,9 +223,12 @@ int admit(vc_server *s, int *n_admitted)
 {
     *n_admitted = 0;
     if (s->queue.empty() || s->free_slots.empty()) return VC_OK;
-    // worklist room: one root node per admitted request, half the ring at most
-    const long long wl_used = (long long)s->snap[kWlCount];
-    long long room = (long long)s->P.wl_cap / 2 - wl_used;
+    // worklist room: one root node per admitted request, half the ring at
+    // most (in every class: which class takes a request is known only after
+    // its root phase)
+    long long room = LLONG_MAX;
+    for (int l = 0; l < s->nlanes; l++)
+        room = std::min(room, (long long)s->lane[l].P.wl_cap / 2 - (long long)s->lane[l].snap[kWlCount]);
     std::vector<Request> adm;
     std::vector<int> qidx;
     std::vector<long long> aoff;
@@ -220,6 +241,7 @@ int admit(vc_server *s, int *n_admitted)
         s->free_slots.pop_back();
         Slot &sl = s->slot[qi];
         sl.busy = true;
+        sl.lane = 0;
         sl.gen++;
         sl.tag = r.tag;
         sl.n = r.n;
@@ -304,11 +326,15 @@ int admit(vc_server *s, int *n_admitted)
     QueryDesc *dq = (QueryDesc *)d;
     SV_CK(serve_validate_run(dq, na, st));
     SV_CK(root_run(dq, na, max_n, max_deg, st));
-    SV_CK(serve_place_run(s->pl, s->P, dq, (const int *)(d + off_idx), na, s->ncap, st));
+    for (int l = 0; l < s->nlanes; l++) {
+        Lane &L = s->lane[l];
+        SV_CK(serve_place_run(L.pl, L.P, dq, (const int *)(d + off_idx), na, L.max_np, l, L.min_np,
+                              l == s->nlanes - 1 ? 1 : 0, st));
+        L.dirty = true;
+    }
     SV_CK(cudaEventRecord(s->ev[1], st));
     s->st.h2d_bytes += (long long)up;
     s->st.admitted += na;
-    s->dirty = true;
     *n_admitted = na;
     return VC_OK;
 }
@@ -319,7 +345,13 @@ int step(vc_server *s, int *completed)
     cudaStream_t st = s->stream;
     int rc;
     s->st.steps++;
-    if (s->active.empty() && s->dirty && (rc = reset_state(s)) != VC_OK) return rc;
+    // a class with nothing in flight is emptied before new requests come in
+    for (int l = 0; l < s->nlanes; l++) {
+        Lane &L = s->lane[l];
+        bool busy = false;
+        for (int qi : s->active) busy |= s->slot[qi].lane == l;
+        if (!busy && L.dirty && (rc = reset_state(s, L)) != VC_OK) return rc;
+    }
     int na = 0;
     if ((rc = admit(s, &na)) != VC_OK) return rc;
     s->active.clear();
@@ -327,39 +359,54 @@ int step(vc_server *s, int *completed)
         if (s->slot[i].busy) s->active.push_back(i);
     const int nact = (int)s->active.size();
     if (nact == 0) return VC_OK;
-    const bool slice = na > 0 || s->snap[kRemaining] > 0;
-    if (slice) {
-        SV_CK(cudaMemsetAsync(&ctlw(s->P.ctl, kMaxProcNs), 0, 8, st));
-        SV_CK(cudaMemsetAsync(&ctlw(s->P.ctl, kMaxExitNs), 0, 8, st));
-        SV_CK(cudaEventRecord(s->ev[2], st));
-        SV_CK(search_slice_run(s->pl, s->P, st));
-        SV_CK(cudaEventRecord(s->ev[3], st));
+    // one time slice per class with work (each class's kernel ends at once
+    // when none of its requests is unfinished)
+    bool sliced = false;
+    SV_CK(cudaEventRecord(s->ev[2], st));
+    for (int l = 0; l < s->nlanes; l++) {
+        Lane &L = s->lane[l];
+        if (!(na > 0 || L.snap[kRemaining] > 0)) continue;
+        SV_CK(cudaMemsetAsync(&ctlw(L.P.ctl, kMaxProcNs), 0, 8, st));
+        SV_CK(cudaMemsetAsync(&ctlw(L.P.ctl, kMaxExitNs), 0, 8, st));
+        SV_CK(search_slice_run(L.pl, L.P, st));
         s->st.slices++;
+        sliced = true;
     }
+    SV_CK(cudaEventRecord(s->ev[3], st));
     memcpy(s->m_act.p, s->active.data(), sizeof(int) * nact);
     SV_CK(cudaMemsetAsync(s->cover_ctr.p, 0, sizeof(unsigned long long), st));
     SV_CK(cudaEventRecord(s->ev[4], st));
-    SV_CK(serve_retire_run(s->slots.as<QueryDesc>(), s->m_act.dev_as<int>(), nact, s->P.reg, s->P.reg_words,
-                           s->wcap, s->m_rec.dev_as<RetireRec>(), s->m_cover.dev_as<int>(), s->cfg.cover_buffer,
-                           s->cover_ctr.as<unsigned long long>(), s->P.ctl, s->m_ctl.dev_as<unsigned long long>(),
-                           st));
+    for (int l = 0; l < s->nlanes; l++) {
+        Lane &L = s->lane[l];
+        SV_CK(serve_retire_run(s->slots.as<QueryDesc>(), s->m_act.dev_as<int>(), nact, L.P.reg, L.P.reg_words,
+                               L.wcap, s->m_rec.dev_as<RetireRec>(), s->m_cover.dev_as<int>(), s->cfg.cover_buffer,
+                               s->cover_ctr.as<unsigned long long>(), L.P.ctl,
+                               L.m_ctl.dev_as<unsigned long long>(), l, st));
+    }
     SV_CK(cudaEventRecord(s->ev[5], st));
     SV_CK(cudaStreamSynchronize(st));
     float ms = 0.f;
     if (na > 0 && cudaEventElapsedTime(&ms, s->ev[0], s->ev[1]) == cudaSuccess) s->st.ms_admit += ms;
-    if (slice && cudaEventElapsedTime(&ms, s->ev[2], s->ev[3]) == cudaSuccess) s->st.ms_search += ms;
+    if (sliced && cudaEventElapsedTime(&ms, s->ev[2], s->ev[3]) == cudaSuccess) s->st.ms_search += ms;
     if (cudaEventElapsedTime(&ms, s->ev[4], s->ev[5]) == cudaSuccess) s->st.ms_retire += ms;
-    memcpy(s->snap, s->m_ctl.p, sizeof(s->snap));
-    s->st.max_stack = std::max(s->st.max_stack, (int32_t)s->snap[kMaxStack]);
-    s->st.d2h_bytes += (long long)sizeof(RetireRec) * nact + (long long)sizeof(s->snap);
+    int kstatus[kMaxLanes] = {};
+    for (int l = 0; l < s->nlanes; l++) {
+        Lane &L = s->lane[l];
+        memcpy(L.snap, L.m_ctl.p, sizeof(L.snap));
+        s->st.max_stack = std::max(s->st.max_stack, (int32_t)L.snap[kMaxStack]);
+        s->st.d2h_bytes += (long long)sizeof(L.snap);
+        kstatus[l] = (int)(int64_t)L.snap[kStatus];
+    }
+    s->st.d2h_bytes += (long long)sizeof(RetireRec) * nact;
 
-    const int kstatus = (int)(int64_t)s->snap[kStatus];
     const RetireRec *rec = s->m_rec.as<RetireRec>();
     const int32_t *cov = s->m_cover.as<int32_t>();
     int done = 0;
     for (int i = 0; i < nact; i++) {
         const RetireRec &R = rec[i];
         const int qi = s->active[i];
+        const int l = R.lane >= 0 && R.lane < s->nlanes ? R.lane : 0;
+        s->slot[qi].lane = l;
         vc_server_result r{};
         if (R.state == 1 && R.cover_off >= 0) {
             r.status = R.status;
@@ -371,9 +418,10 @@ int step(vc_server *s, int *completed)
             s->st.d2h_bytes += 4ll * R.cover_len;
             finish_slot(s, qi, r, cov + R.cover_off);
             done++;
-        } else if (kstatus != 0) {
-            // the slice failed as a whole: every unfinished request ends with its status
-            r.status = kstatus;
+        } else if (kstatus[l] != 0) {
+            // the class's slice failed as a whole: each of its unfinished
+            // requests ends with that status
+            r.status = kstatus[l];
             r.size = -1;
             r.n_induced = R.np;
             r.nodes = R.state == 1 ? R.nodes : 0;
@@ -381,7 +429,8 @@ int step(vc_server *s, int *completed)
             done++;
         }
     }
-    if (kstatus != 0) s->dirty = true;   // emptied before the next admission
+    for (int l = 0; l < s->nlanes; l++)
+        if (kstatus[l] != 0) s->lane[l].dirty = true;   // emptied before the next admission
     s->active.clear();
     for (int i = 0; i < s->cfg.max_inflight; i++)
         if (s->slot[i].busy) s->active.push_back(i);
@@ -407,6 +456,7 @@ int vc_server_config_default(vc_server_config *cfg)
     cfg->idle_timeout_ms = 60000;
     cfg->arena_bytes = (int64_t)2 << 30;
     cfg->cover_buffer = (int64_t)16 << 20;
+    cfg->max_induced_large = 20000;
     return VC_OK;
 }
 
@@ -427,9 +477,12 @@ int vc_server_create(const vc_server_config *cfg_in, void *cuda_stream, vc_serve
         if (cfg.idle_timeout_ms <= 0) cfg.idle_timeout_ms = d.idle_timeout_ms;
         if (cfg.arena_bytes <= 0) cfg.arena_bytes = d.arena_bytes;
         if (cfg.cover_buffer <= 0) cfg.cover_buffer = d.cover_buffer;
+        if (cfg.max_induced_large < 0) cfg.max_induced_large = 0;
     }
     if (cfg.dtype_bytes != 1 && cfg.dtype_bytes != 2 && cfg.dtype_bytes != 4) return VC_EINVAL;
-    if (cfg.max_inflight > (1 << 20) || cfg.max_induced > (1 << 24) || cfg.node_budget < 0) return VC_EINVAL;
+    if (cfg.max_inflight > (1 << 20) || cfg.max_induced > (1 << 24) || cfg.max_induced_large > (1 << 24) ||
+        cfg.node_budget < 0)
+        return VC_EINVAL;
     if (cfg.team != 32 && cfg.team < 64) return VC_EINVAL;
 
     vc_server *s = new vc_server();
@@ -443,95 +496,111 @@ int vc_server_create(const vc_server_config *cfg_in, void *cuda_stream, vc_serve
     for (auto &e : s->ev)
         if (cudaEventCreate(&e) != cudaSuccess) return fail(VC_ECUDA);
 
-    s->ncap = (cfg.max_induced + 16 + 15) / 16 * 16;
-    s->wcap = cfg.max_induced / 32 + 2;
-    int rc = search_plan(cfg.dtype_bytes, cfg.team, s->ncap, s->wcap, s->sms, 0, &s->pl);
-    if (rc != VC_OK) return fail(rc);
-    const SearchPlan &pl = s->pl;
-    int depth = cfg.stack_depth > 0 ? cfg.stack_depth : std::min(s->ncap + 2, 1024);
-    const size_t per_level = (size_t)pl.workers * pl.slot_bytes;
-    const size_t stack_budget = (size_t)8 << 30;
-    if (cfg.stack_depth <= 0 && (size_t)depth * per_level > stack_budget)
-        depth = (int)std::max<size_t>(16, stack_budget / per_level);
-    int wl_cap = 1;
-    const int wl_want = cfg.worklist_capacity > 0 ? cfg.worklist_capacity
-                                                  : std::max(std::max(4 * pl.workers, 1024), 4 * cfg.max_inflight);
-    while (wl_cap < wl_want) wl_cap <<= 1;
-    int reg_cap = cfg.registry_capacity;
-    if (reg_cap <= 0) {
-        const size_t per_entry = sizeof(RegEntry) + (size_t)s->wcap * 4;
-        reg_cap = (int)std::min<size_t>((size_t)4 << 20, ((size_t)4 << 30) / per_entry);
-        reg_cap = std::max(reg_cap, 64 * pl.workers);
+    // size classes: induced graphs of up to max_induced vertices, then (when
+    // max_induced_large is larger) up to max_induced_large
+    const int caps[kMaxLanes] = {cfg.max_induced, cfg.max_induced_large};
+    s->nlanes = cfg.max_induced_large > cfg.max_induced ? 2 : 1;
+    int rc;
+    for (int l = 0; l < s->nlanes; l++) {
+        Lane &L = s->lane[l];
+        L.ncap = (caps[l] + 16 + 15) / 16 * 16;
+        L.wcap = caps[l] / 32 + 2;
+        L.min_np = l == 0 ? 0 : s->lane[l - 1].max_np;
+        L.max_np = L.ncap;
+        // the large class uses the default worker shape for its size (the
+        // configured team is for the small class)
+        rc = search_plan(cfg.dtype_bytes, l == 0 ? cfg.team : 0, L.ncap, L.wcap, s->sms, 0, &L.pl);
+        if (rc != VC_OK) return fail(rc);
+        const SearchPlan &pl = L.pl;
+        int depth = cfg.stack_depth > 0 ? cfg.stack_depth : std::min(L.ncap + 2, l == 0 ? 1024 : 2048);
+        const size_t per_level = (size_t)pl.workers * pl.slot_bytes;
+        const size_t stack_budget = (size_t)8 << 30;
+        if (cfg.stack_depth <= 0 && (size_t)depth * per_level > stack_budget)
+            depth = (int)std::max<size_t>(16, stack_budget / per_level);
+        int wl_cap = 1;
+        const int wl_want = cfg.worklist_capacity > 0
+                                ? cfg.worklist_capacity
+                                : std::max(std::max(4 * pl.workers, 1024), (l == 0 ? 4 : 16) * cfg.max_inflight);
+        while (wl_cap < wl_want) wl_cap <<= 1;
+        int reg_cap = cfg.registry_capacity;
+        if (reg_cap <= 0) {
+            const size_t per_entry = sizeof(RegEntry) + (size_t)L.wcap * 4;
+            reg_cap = (int)std::min<size_t>((size_t)4 << 20, (((size_t)4 << 30) >> l) / per_entry);
+            reg_cap = std::max(reg_cap, 64 * pl.workers);
+        }
+        reg_cap += cfg.max_inflight;
+        if ((rc = L.stack.ensure((size_t)pl.workers * depth * pl.slot_bytes)) != VC_OK ||
+            (rc = L.wl.ensure((size_t)wl_cap * pl.slot_bytes)) != VC_OK ||
+            (rc = L.wl_seq.ensure((size_t)wl_cap * 4)) != VC_OK ||
+            (rc = L.reg.ensure((size_t)reg_cap * sizeof(RegEntry))) != VC_OK ||
+            (rc = L.reg_words.ensure((size_t)reg_cap * L.wcap * 4)) != VC_OK ||
+            (rc = L.comp_scratch.ensure((size_t)pl.workers * 5 * L.ncap * 4)) != VC_OK ||
+            (rc = L.ctl.ensure(kCtlWords * 8)) != VC_OK ||
+            (rc = L.stack_top.ensure((size_t)pl.workers * 4)) != VC_OK ||
+            (rc = L.m_ctl.ensure(kCtlEntries * 8, true)) != VC_OK ||
+            (pl.wglobal_bytes > 0 && (rc = L.wglobal.ensure((size_t)pl.workers * (size_t)pl.wglobal_bytes)) != VC_OK))
+            return fail(rc);
+        SearchParams &P = L.P;
+        P.queries = nullptr;   // set below, once the slot array exists
+        P.nq = cfg.max_inflight;
+        P.team = pl.warp_team ? 32 : pl.threads;
+        P.workers = pl.workers;
+        P.ncap = L.ncap;
+        P.wcap = L.wcap;
+        P.slot_bytes = pl.slot_bytes;
+        P.stack_depth = depth;
+        P.stack_slots = L.stack.as<char>();
+        P.wl_slots = L.wl.as<char>();
+        P.wl_seq = L.wl_seq.as<unsigned>();
+        P.wl_cap = wl_cap;
+        P.wl_low = cfg.load_balance ? std::max(8, std::min(wl_cap / 2, 4 * pl.workers)) : 0;
+        P.reg = L.reg.as<RegEntry>();
+        P.reg_words = L.reg_words.as<uint32_t>();
+        P.reg_cap = reg_cap;
+        P.comp_scratch = L.comp_scratch.as<int>();
+        P.ctl = L.ctl.as<unsigned long long>();
+        P.node_budget = cfg.node_budget;
+        P.idle_timeout_ns = (long long)cfg.idle_timeout_ms * 1000000ll;
+        P.use_components = cfg.use_components;
+        P.load_balance = cfg.load_balance;
+        P.csr_smem = 0;
+        P.csr_query = 0;
+        P.quantum_ns = (long long)cfg.quantum_us * 1000ll;
+        P.stack_top = L.stack_top.as<int>();
+        P.no_bounds = 0;
+        P.breakdown = 0;
+        P.no_dyn_bounds = 0;
+        P.wglobal = pl.wglobal_bytes > 0 ? L.wglobal.as<char>() : nullptr;
+        P.wglobal_stride = pl.wglobal_bytes;
+        for (DevBuf *b : {&L.stack, &L.wl, &L.wl_seq, &L.reg, &L.reg_words, &L.comp_scratch, &L.ctl, &L.stack_top,
+                          &L.wglobal})
+            s->st.device_bytes += (int64_t)b->bytes;
     }
-    reg_cap += cfg.max_inflight;
-
-    if ((rc = s->stack.ensure((size_t)pl.workers * depth * pl.slot_bytes)) != VC_OK ||
-        (rc = s->wl.ensure((size_t)wl_cap * pl.slot_bytes)) != VC_OK ||
-        (rc = s->wl_seq.ensure((size_t)wl_cap * 4)) != VC_OK ||
-        (rc = s->reg.ensure((size_t)reg_cap * sizeof(RegEntry))) != VC_OK ||
-        (rc = s->reg_words.ensure((size_t)reg_cap * s->wcap * 4)) != VC_OK ||
-        (rc = s->comp_scratch.ensure((size_t)pl.workers * 5 * s->ncap * 4)) != VC_OK ||
-        (rc = s->ctl.ensure(kCtlWords * 8)) != VC_OK ||
-        (rc = s->stack_top.ensure((size_t)pl.workers * 4)) != VC_OK ||
-        (rc = s->slots.ensure(sizeof(QueryDesc) * cfg.max_inflight)) != VC_OK ||
+    if ((rc = s->slots.ensure(sizeof(QueryDesc) * cfg.max_inflight)) != VC_OK ||
         (rc = s->arena.ensure((size_t)cfg.arena_bytes)) != VC_OK ||
         (rc = s->cover_ctr.ensure(256)) != VC_OK ||
         (rc = s->m_rec.ensure(sizeof(RetireRec) * cfg.max_inflight, true)) != VC_OK ||
         (rc = s->m_cover.ensure((size_t)cfg.cover_buffer * 4, true)) != VC_OK ||
-        (rc = s->m_ctl.ensure(kCtlEntries * 8, true)) != VC_OK ||
-        (rc = s->m_act.ensure(sizeof(int) * cfg.max_inflight, true)) != VC_OK ||
-        (pl.wglobal_bytes > 0 && (rc = s->wglobal.ensure((size_t)pl.workers * (size_t)pl.wglobal_bytes)) != VC_OK))
+        (rc = s->m_act.ensure(sizeof(int) * cfg.max_inflight, true)) != VC_OK)
         return fail(rc);
     s->arena_alloc.init((size_t)cfg.arena_bytes);
-
-    SearchParams &P = s->P;
-    P.queries = s->slots.as<QueryDesc>();
-    P.nq = cfg.max_inflight;
-    P.team = pl.warp_team ? 32 : pl.threads;
-    P.workers = pl.workers;
-    P.ncap = s->ncap;
-    P.wcap = s->wcap;
-    P.slot_bytes = pl.slot_bytes;
-    P.stack_depth = depth;
-    P.stack_slots = s->stack.as<char>();
-    P.wl_slots = s->wl.as<char>();
-    P.wl_seq = s->wl_seq.as<unsigned>();
-    P.wl_cap = wl_cap;
-    P.wl_low = cfg.load_balance ? std::max(8, pl.workers / 2) : 0;
-    P.reg = s->reg.as<RegEntry>();
-    P.reg_words = s->reg_words.as<uint32_t>();
-    P.reg_cap = reg_cap;
-    P.comp_scratch = s->comp_scratch.as<int>();
-    P.ctl = s->ctl.as<unsigned long long>();
-    P.node_budget = cfg.node_budget;
-    P.idle_timeout_ns = (long long)cfg.idle_timeout_ms * 1000000ll;
-    P.use_components = cfg.use_components;
-    P.load_balance = cfg.load_balance;
-    P.csr_smem = 0;
-    P.csr_query = 0;
-    P.quantum_ns = (long long)cfg.quantum_us * 1000ll;
-    P.stack_top = s->stack_top.as<int>();
-    P.no_bounds = 0;
-    P.breakdown = 0;
-    P.no_dyn_bounds = 0;
-    P.wglobal = pl.wglobal_bytes > 0 ? s->wglobal.as<char>() : nullptr;
-    P.wglobal_stride = pl.wglobal_bytes;
+    for (int l = 0; l < s->nlanes; l++) s->lane[l].P.queries = s->slots.as<QueryDesc>();
 
     s->slot.assign(cfg.max_inflight, Slot{});
     for (int i = cfg.max_inflight - 1; i >= 0; i--) s->free_slots.push_back(i);
     if (cudaMemsetAsync(s->slots.p, 0, s->slots.bytes, s->stream) != cudaSuccess) return fail(VC_ECUDA);
-    if ((rc = reset_state(s)) != VC_OK) return fail(rc);
+    for (int l = 0; l < s->nlanes; l++)
+        if ((rc = reset_state(s, s->lane[l])) != VC_OK) return fail(rc);
     s->st.resets = 0;
     if (cudaStreamSynchronize(s->stream) != cudaSuccess) return fail(VC_ECUDA);
 
-    s->st.workers = pl.workers;
-    s->st.team = P.team;
-    s->st.dtype_bytes = pl.dtype;
-    s->st.max_induced = cfg.max_induced;
-    s->st.slot_bytes = pl.slot_bytes;
-    for (DevBuf *b : {&s->stack, &s->wl, &s->wl_seq, &s->reg, &s->reg_words, &s->comp_scratch, &s->ctl,
-                      &s->stack_top, &s->slots, &s->arena, &s->cover_ctr})
-        s->st.device_bytes += (int64_t)b->bytes;
+    const Lane &L0 = s->lane[0];
+    s->st.workers = L0.pl.workers;
+    s->st.team = L0.P.team;
+    s->st.dtype_bytes = L0.pl.dtype;
+    s->st.max_induced = s->nlanes > 1 ? cfg.max_induced_large : cfg.max_induced;
+    s->st.slot_bytes = L0.pl.slot_bytes;
+    for (DevBuf *b : {&s->slots, &s->arena, &s->cover_ctr}) s->st.device_bytes += (int64_t)b->bytes;
     *out = s;
     return VC_OK;
 }
@@ -602,12 +671,16 @@ int vc_server_get_stats(const vc_server *s, vc_server_stats *st)
 {
     if (!s || !st) return VC_EINVAL;
     *st = s->st;
-    st->nodes = s->base_nodes + (long long)s->snap[kNodes];
-    st->search_bytes = s->base_bytes + (long long)s->snap[kBytes];
-    st->wait_polls = s->base_waits + (long long)s->snap[kWaitIters];
-    st->preemptions = s->base_preempts + (long long)s->snap[kPreempts];
-    st->max_node_ns = (long long)s->snap[kMaxProcNs];
-    st->max_exit_ns = (long long)s->snap[kMaxExitNs];
+    st->nodes = st->search_bytes = st->wait_polls = st->preemptions = st->max_node_ns = st->max_exit_ns = 0;
+    for (int l = 0; l < s->nlanes; l++) {
+        const Lane &L = s->lane[l];
+        st->nodes += L.base_nodes + (long long)L.snap[kNodes];
+        st->search_bytes += L.base_bytes + (long long)L.snap[kBytes];
+        st->wait_polls += L.base_waits + (long long)L.snap[kWaitIters];
+        st->preemptions += L.base_preempts + (long long)L.snap[kPreempts];
+        st->max_node_ns = std::max(st->max_node_ns, (int64_t)L.snap[kMaxProcNs]);
+        st->max_exit_ns = std::max(st->max_exit_ns, (int64_t)L.snap[kMaxExitNs]);
+    }
     return VC_OK;
 }
 

@@ -146,7 +146,7 @@ def test_admission_waits_for_device_memory(vc):
 
 
 def test_malformed_oversized_and_over_budget_requests(vc):
-    srv = vc.Server(max_induced=64, node_budget=50, quantum_us=300)
+    srv = vc.Server(max_induced=64, max_induced_large=0, node_budget=50, quantum_us=300)
     good = gg.random_forest(40, 3, 1)           # settled by the root phase
     bad_rp = np.array([0, 1, 2, 2], np.int32)   # 0-1 and 1-2 listed once each: not mirrored
     bad_col = np.array([1, 2], np.int32)
@@ -162,6 +162,67 @@ def test_malformed_oversized_and_over_budget_requests(vc):
     assert res[t_hard]["status"] == vc.VC_EBUDGET and res[t_hard]["nodes"] > 50
     assert res[t_good]["status"] == vc.VC_OK and res[t_good]["size"] == opt_of(good)
     verify(good, res[t_good])
+    srv.close()
+
+
+def test_size_classes_serve_small_and_large_induced_graphs_together(vc):
+    # two classes: induced graphs of up to 64 vertices, and up to 512; the
+    # small and large requests are in flight together and each answer equals
+    # the oracle's and the plain call's; one above 512 is refused
+    srv = vc.Server(max_induced=64, max_induced_large=512, quantum_us=300)
+    small = [gg.gnm(40, 90, s) for s in range(6)]
+    large = [gg.disjoint_union([gg.gnm(40, 90, 10 * s + j) for j in range(4)]) for s in range(4)]
+    too_big = gg.disjoint_union([gg.gnm(40, 90, 100 + j) for j in range(40)])
+    graphs = []
+    for i in range(6):
+        graphs.append(small[i])
+        if i < 4:
+            graphs.append(large[i])
+    tags = {srv.submit(g.row_ptr, g.col): g for g in graphs}
+    t_big = srv.submit(too_big.row_ptr, too_big.col)
+    res = {r["tag"]: r for r in srv.drain()}
+    sizes = []
+    for t, g in tags.items():
+        r = res[t]
+        dg = vc.Graph.from_csr(g.row_ptr, g.col)
+        want, _, st = vc.solve_min(dg)
+        dg.close()
+        assert r["status"] == vc.VC_OK and r["size"] == want == opt_of(g)
+        assert r["n_induced"] == st["n_induced"]
+        verify(g, r)
+        sizes.append(r["n_induced"])
+    assert max(sizes) > 64 and min(sizes) <= 64    # both classes were used
+    assert res[t_big]["status"] == vc.VC_ECAPACITY and res[t_big]["n_induced"] > 512
+    st = srv.stats()
+    assert st["max_induced"] == 512
+    srv.close()
+
+
+def test_running_out_of_room_ends_only_that_request(vc):
+    # a one-slot stack and a 16-slot worklist: requests whose search needs
+    # more room finish with VC_ECAPACITY on their own; every answer given is
+    # exact, and the server keeps serving afterwards
+    srv = vc.Server(stack_depth=1, worklist_capacity=16, max_inflight=8, quantum_us=300)
+    hard = [gg.component_heavy(s, copies=6, copy_n=24, p=0.2, chain=3) for s in range(1, 4)]
+    easy = [gg.random_forest(200, 3, s) for s in range(3)] + [gg.cycle(41), gg.complete(9)]
+    graphs = hard + easy
+    tags = {srv.submit(g.row_ptr, g.col): g for g in graphs}
+    res = {r["tag"]: r for r in srv.drain()}
+    statuses = {r["status"] for r in res.values()}
+    assert statuses <= {vc.VC_OK, vc.VC_ECAPACITY}
+    for t, g in tags.items():
+        if res[t]["status"] == vc.VC_OK:
+            assert res[t]["size"] == opt_of(g)
+            verify(g, res[t])
+    for g in easy:   # settled at the root or closed at once: never short of room
+        t = [k for k, v in tags.items() if v is g][0]
+        assert res[t]["status"] == vc.VC_OK
+    g = gg.gnm(80, 200, 3)
+    t = srv.submit(g.row_ptr, g.col)
+    r = {x["tag"]: x for x in srv.drain()}[t]
+    assert r["status"] in (vc.VC_OK, vc.VC_ECAPACITY)
+    if r["status"] == vc.VC_OK:
+        assert r["size"] == opt_of(g)
     srv.close()
 
 
