@@ -96,6 +96,45 @@ def combine_over_ranks(local_ms: float, steps: int, world: int):
     return local_ms, world * steps / (local_ms / 1e3)
 
 
+def shard_by_cost(costs, world: int):
+    """Split independent graphs over `world` ranks: longest first, each to
+    the rank with the least cost so far (LPT).  Returns one ascending index
+    list per rank; every index appears exactly once."""
+    load = [0.0] * world
+    parts = [[] for _ in range(world)]
+    for i in sorted(range(len(costs)), key=lambda j: (-costs[j], j)):
+        r = min(range(world), key=lambda k: (load[k], k))
+        parts[r].append(i)
+        load[r] += costs[i]
+    return [sorted(p) for p in parts]
+
+
+def host_group():
+    """A gloo process group over every rank, for the host-side gathers of
+    the sharded batch (no device collective on the data path)."""
+    import torch.distributed as dist
+    return dist.new_group(backend="gloo")
+
+
+def combine_search(local: dict, world: int, group=None) -> dict:
+    """Sharded batch: every rank solved its share; the job's time is the
+    slowest rank's, its queries and nodes those of every rank."""
+    if world == 1:
+        return local
+    import torch.distributed as dist
+    parts = [None] * world
+    dist.all_gather_object(parts, {k: local[k] for k in ("queries", "nodes", "ms_wall", "ms_kernel", "wrong",
+                                                          "over", "bytes")}, group=group)
+    ms_wall = max(p["ms_wall"] for p in parts)
+    ms_kernel = max(p["ms_kernel"] for p in parts)
+    out = dict(local)
+    for k in ("queries", "nodes", "wrong", "over", "bytes"):
+        out[k] = sum(p[k] for p in parts)
+    out["ms_wall"], out["ms_kernel"] = ms_wall, ms_kernel
+    out["per_rank_queries"] = [p["queries"] for p in parts]
+    return out
+
+
 def load_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -367,26 +406,29 @@ def cover_ok(g, cover) -> bool:
     return bool(np.all(flags[src] | flags[g.col]))
 
 
-def prepare_pvc_batch(vc, stream, count=4096, budget=200_000, seed=11):
+def prepare_pvc_batch(vc, stream, count=4096, budget=200_000, seed=11, rank=0, world=1):
     """The batched PVC workload: 4,096 graphs, n ~ U[40, 1500] (half G(n,p)
     with mean degree U[3, 8], half Chung-Lu 2.5), each queried at k = opt
     (yes) and k = opt - 1 (no).  opt comes from a first batched MVC launch
     under the same per-query node budget; graphs over budget there are
     dropped and counted.  Launch options are autotuned on the queries."""
     mix = gg.batch_pvc_mix(count, seed)
+    if world > 1:   # this rank's share of the graphs, balanced by size
+        mix = [mix[i] for i in shard_by_cost([g.n + g.m for g in mix], world)[rank]]
     dms = [vc.Graph.from_csr(h.row_ptr, h.col, stream=stream) for h in mix]
     t0 = time.perf_counter()
     sizes, _, status, _, mst = vc.solve_batch(dms, node_budget=budget, want_covers=False, raise_on_error=False)
     mvc_s = time.perf_counter() - t0
-    solved = [i for i in range(count) if status[i] == 0]
+    solved = [i for i in range(len(mix)) if status[i] == 0]
     qg = [dms[i] for i in solved] * 2
     ks = [int(sizes[i]) for i in solved] + [int(sizes[i]) - 1 for i in solved]
     tuned, _, _ = vc.autotune(qg, ks, repeats=1, node_budget=budget)
     return {"mix": mix, "dms": dms, "sizes": sizes, "status": status, "solved": solved, "qg": qg, "ks": ks,
-            "tuned": tuned, "mvc_s": mvc_s, "mvc_stats": mst, "budget": budget, "count": count, "seed": seed}
+            "tuned": tuned, "mvc_s": mvc_s, "mvc_stats": mst, "budget": budget, "count": len(mix), "seed": seed,
+            "total": count}
 
 
-def search_block(vc, torch, prep, steps, hbm_peak, hbm_kind, l2_peak, flush):
+def search_block(vc, torch, prep, steps, hbm_peak, hbm_kind, l2_peak, flush, world=1, group=None):
     """The persistent search measured on the batched PVC workload at full
     size: `steps` launches of all its queries (each launch one root phase and
     one persistent search), L2 flushed before each.  The search kernel's time
@@ -412,22 +454,30 @@ def search_block(vc, torch, prep, steps, hbm_peak, hbm_kind, l2_peak, flush):
         nodes += bst["nodes"]
         nbytes += bst["search_bytes"]
         launches += bst["launches"]
-    ksec = sum(ms) / 1e3
+    # ranks solve disjoint shards: the job's time is the slowest rank's
+    c = combine_search({"queries": len(qg), "nodes": nodes, "ms_wall": sum(wall) * 1e3, "ms_kernel": sum(ms),
+                        "wrong": wrong, "over": over, "bytes": nbytes, "dropped": prep["count"] - ns}, world, group)
+    nodes, nbytes, wrong, over = c["nodes"], c["bytes"], c["wrong"], c["over"]
+    ksec = c["ms_kernel"] / 1e3
     achieved = nbytes / ksec / 1e9
-    return {"workload": "pvc_batch_4096", "graphs": prep["count"], "seed": prep["seed"],
-            "node_budget_per_query": budget, "dropped_over_budget_in_mvc": prep["count"] - ns,
-            "queries": len(qg), "steps": steps, "l2": "256 MiB write before every step",
-            "kernel": "search_kernel", "ms_search_kernel": round(statistics.mean(ms), 3),
-            "nodes_per_launch": nodes // steps, "nodes_per_s": round(nodes / ksec, 1),
-            "queries_per_s": round(len(qg) * steps / sum(wall), 1),
-            "time_to_solution_ms": round(statistics.mean(wall) * 1e3, 3),
-            "over_budget_per_launch": over // steps, "wrong_answers": wrong,
-            "bytes_per_node": round(nbytes / max(1, nodes), 1), "achieved_gbs": round(achieved, 3),
-            "hbm_peak_gbs": hbm_peak, "hbm_peak_kind": hbm_kind, "frac_hbm": round(achieved / hbm_peak, 6),
-            "l2_peak_gbs": round(l2_peak, 1), "l2_peak_kind": "measured in this run (vc_measure_l2_read, 32 MiB)",
-            "frac_l2": round(achieved / l2_peak, 6) if l2_peak > 0 else None,
-            "traffic": kernel_traffic("search_kernel", "pvc_batch_4096"),
-            "options": {f: getattr(tuned, f) for f in vc.TUNED_FIELDS}, "gpu_launches": launches}
+    out = {"workload": "pvc_batch_4096", "graphs": prep["total"], "seed": prep["seed"],
+           "node_budget_per_query": budget, "dropped_over_budget_in_mvc_rank0": prep["count"] - ns,
+           "queries": c["queries"], "steps": steps, "l2": "256 MiB write before every step",
+           "kernel": "search_kernel", "ms_search_kernel": round(c["ms_kernel"] / steps, 3),
+           "nodes_per_launch": nodes // steps, "nodes_per_s": round(nodes / ksec, 1),
+           "queries_per_s": round(c["queries"] * steps / (c["ms_wall"] / 1e3), 1),
+           "time_to_solution_ms": round(c["ms_wall"] / steps, 3),
+           "over_budget_per_launch": over // steps, "wrong_answers": wrong,
+           "bytes_per_node": round(nbytes / max(1, nodes), 1), "achieved_gbs": round(achieved, 3),
+           "hbm_peak_gbs": hbm_peak, "hbm_peak_kind": hbm_kind, "frac_hbm": round(achieved / hbm_peak, 6),
+           "l2_peak_gbs": round(l2_peak, 1), "l2_peak_kind": "measured in this run (vc_measure_l2_read, 32 MiB)",
+           "frac_l2": round(achieved / l2_peak, 6) if l2_peak > 0 else None,
+           "traffic": kernel_traffic("search_kernel", "pvc_batch_4096"),
+           "options": {f: getattr(tuned, f) for f in vc.TUNED_FIELDS}, "gpu_launches": launches}
+    if world > 1:
+        out.update(sharding=f"LPT over {world} ranks by n + m, host gather (gloo)",
+                   per_rank_queries=c["per_rank_queries"])
+    return out
 
 
 def extra_pvc_batch(vc, stream, prep):
@@ -743,19 +793,23 @@ def ours_main(args, rank, world, local_rank):
         cpu = {"value": round(v, 6), "unit": "graphs/s", "cores": 1, "kind": "oracle",
                "sample": "2 solves of the same workload graph, single thread", "host": host_cpu()}
 
-    # ---- the persistent search on the batched PVC workload (rank 0)
+    # ---- the persistent search on the batched PVC workload (every rank
+    # solves its shard of the 4,096 graphs)
     search, prep = None, None
-    if rank == 0 and not args.no_search:
+    if not args.no_search:
         l2_peak = vc.measure_l2_read(32 << 20, 50, 5, stream=stream)
-        prep = prepare_pvc_batch(vc, stream)
-        search = search_block(vc, torch, prep, args.search_steps, peak, peak_kind, l2_peak, flush)
-        _log(f"search: {json.dumps(search, default=_json_default)}")
+        group = host_group() if world > 1 else None
+        prep = prepare_pvc_batch(vc, stream, rank=rank, world=world)
+        search = search_block(vc, torch, prep, args.search_steps, peak, peak_kind, l2_peak, flush, world, group)
+        if rank == 0:
+            _log(f"search: {json.dumps(search, default=_json_default)}")
 
     also = None
     if rank == 0 and not args.no_extra:
         legs = [("small_graphs", lambda: extra_workloads(vc, torch, stream, peak)),
                 ("served_stream", lambda: extra_served_stream(vc, stream, count=args.stream_requests)),
-                ("pvc_batch_4096", lambda: extra_pvc_batch(vc, stream, prep or prepare_pvc_batch(vc, stream))),
+                ("pvc_batch_4096", lambda: extra_pvc_batch(vc, stream, prep if prep and world == 1
+                                                           else prepare_pvc_batch(vc, stream))),
                 ("component_heavy_256x48", lambda: extra_component_heavy_full(vc, stream, peak)),
                 ("ablation", lambda: extra_ablation(vc, stream))]
         also = {}
@@ -823,6 +877,17 @@ def main():
     global WORKLOAD
     WORKLOAD = WORKLOADS[args.workload]
     rank, world, local_rank = dist_env()
+    if args.gpus > 1 and "WORLD_SIZE" not in os.environ:
+        # one process per GPU: start the ranks under torchrun (same arguments)
+        import socket
+        with socket.socket() as sk:
+            sk.bind(("127.0.0.1", 0))
+            port = sk.getsockname()[1]
+        cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", f"--nproc-per-node={args.gpus}",
+               "--master-addr=127.0.0.1", f"--master-port={port}", os.path.abspath(__file__), *sys.argv[1:]]
+        sys.exit(subprocess.call(cmd))
+    if world != args.gpus:
+        raise SystemExit(f"bench.py: --gpus {args.gpus} but {world} ranks were started")
     if args.impl == "reference":
         reference_main(args, rank, world)
     else:
