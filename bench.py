@@ -520,11 +520,69 @@ def extra_pvc_batch(vc, stream, prep):
             "plain_matching_answers": plain_ok, "plain_errors": plain_err, "cpu_oracle_all_cores": cpu_all}
 
 
-def extra_component_heavy_full(vc, stream, peak, budget=100_000_000):
+def extra_c4_budget_study(vc, stream, prep, big=2_000_000, sample=32, max_s=120.0):
+    """The batched PVC workload's graphs that exceeded the 200k-node budget
+    in the minimum-cover pass, solved again in one batch under a 2M-node
+    budget: how many finish, and, for a sample of those, the oracle's answer
+    on every host core under the same budget (its rate is the CPU baseline;
+    both must agree)."""
+    import concurrent.futures as cf
+    import oracle
+    oracle.build()
+    dropped = [i for i in range(prep["count"]) if prep["status"][i] == vc.VC_EBUDGET]
+    graphs = [prep["mix"][i] for i in dropped]
+    dgs = [prep["dms"][i] for i in dropped]
+    t0 = time.perf_counter()
+    sizes, _, status, _, st = vc.solve_batch(dgs, node_budget=big, want_covers=False, raise_on_error=False)
+    dev_s = time.perf_counter() - t0
+    fin = [j for j in range(len(dropped)) if status[j] == 0]
+    rng = np.random.default_rng(17)
+    pick = sorted(rng.choice(len(fin), size=min(sample, len(fin)), replace=False).tolist()) if fin else []
+
+    def one(j):
+        g = graphs[fin[j]]
+        try:
+            return oracle.mvc(g.n, g.row_ptr, g.col, node_budget=big)[0]
+        except oracle.OracleBudgetExceeded:
+            return None
+
+    agree = disagree = over = 0
+    t1 = time.perf_counter()
+    with cf.ThreadPoolExecutor(max_workers=os.cpu_count() or 1) as ex:
+        for j, want in zip(pick, ex.map(one, pick)):
+            if want is None:
+                over += 1
+            elif want == int(sizes[fin[j]]):
+                agree += 1
+            else:
+                disagree += 1
+            if time.perf_counter() - t1 > max_s:
+                break
+    return {"graphs": prep["count"], "dropped_at_200k": len(dropped), "node_budget": big,
+            "finished_at_2m": len(fin), "still_over": int(np.sum(status == vc.VC_EBUDGET)),
+            "device_s": round(dev_s, 3), "device_nodes": st["nodes"],
+            "oracle_sample": len(pick), "oracle_agree": agree, "oracle_disagree": disagree,
+            "oracle_over_budget": over, "oracle_s": round(time.perf_counter() - t1, 3),
+            "oracle_cores": os.cpu_count() or 1}
+
+
+def induced_piece(g, lo: int, hi: int):
+    """The subgraph induced by vertices [lo, hi), relabelled from 0."""
+    u, v = gg.edges_of(g)
+    keep = (u >= lo) & (u < hi) & (v >= lo) & (v < hi)
+    return gg.from_edges(hi - lo, u[keep] - lo, v[keep] - lo)
+
+
+def extra_component_heavy_full(vc, stream, peak, budget=100_000_000, copies=256, copy_n=48, chain=32):
     """The component-heavy shape at full size (256 copies of G(48, 0.12) on a
     32-vertex chain, about 12.3k vertices) under a node budget: it does not
-    finish within it, so this measures the search rate and its roofline."""
-    g = gg.component_heavy(0, copies=256, copy_n=48, p=0.12, chain=32)
+    finish within it, so this measures the search rate and its roofline, and
+    certifies what it can: the best cover the search had found when it
+    stopped (an upper bound), beside a lower bound from disjoint induced
+    subgraphs -- each copy and the chain, solved exactly (a cover of the
+    whole graph covers each piece's edges, so the pieces' optima add up to a
+    lower bound on the whole)."""
+    g = gg.component_heavy(0, copies=copies, copy_n=copy_n, p=0.12, chain=chain)
     d = vc.Graph.from_csr(g.row_ptr, g.col, stream=stream)
     try:
         size, _, st = vc.solve_min(d, node_budget=budget)
@@ -534,10 +592,22 @@ def extra_component_heavy_full(vc, stream, peak, budget=100_000_000):
     d.close()
     ms = st["ms_search"]
     gbs = st["search_bytes"] / (ms / 1e3) / 1e9 if ms > 0 else 0.0
+    pieces = [induced_piece(g, 0, chain)]
+    pieces += [induced_piece(g, chain + i * copy_n, chain + (i + 1) * copy_n) for i in range(copies)]
+    dps = [vc.Graph.from_csr(h.row_ptr, h.col, stream=stream) for h in pieces]
+    psz, _, pst, _, _ = vc.solve_batch(dps, want_covers=False, raise_on_error=False)
+    for x in dps:
+        x.close()
+    lower = int(np.sum(psz)) if np.all(pst == 0) else None
+    upper = size if status == 0 else st["best_found"]
     return {"n": g.n, "n_induced": st["n_induced"], "status": status, "answer": size, "node_budget": budget,
             "nodes": st["nodes"], "ms_search_kernel": round(ms, 3),
             "nodes_per_s": round(st["nodes"] / (ms / 1e3), 1) if ms > 0 else None,
             "component_branches": st["component_branches"], "workers": st["workers"], "team": st["team"],
+            "certificate": {"upper_best_cover_found": upper,
+                            "lower_disjoint_pieces": lower,
+                            "gap": (upper - lower) if lower is not None else None,
+                            "pieces": "the 32-vertex chain and each of the 256 copies, solved exactly"},
             "search_roofline": {"bound": "hbm", "kernel": "search_kernel", "achieved": round(gbs, 3),
                                 "peak": peak, "unit": "GB/s", "frac": round(gbs / peak, 6),
                                 "bytes_per_node": round(st["search_bytes"] / max(1, st["nodes"]), 1),
@@ -804,6 +874,12 @@ def ours_main(args, rank, world, local_rank):
         if rank == 0:
             _log(f"search: {json.dumps(search, default=_json_default)}")
 
+    if rank == 0 and args.c4_study and prep is not None and world == 1:
+        study = extra_c4_budget_study(vc, stream, prep)
+        _log(f"c4_study: {json.dumps(study, default=_json_default)}")
+        if search is not None:
+            search["budget_study"] = study
+
     also = None
     if rank == 0 and not args.no_extra:
         legs = [("small_graphs", lambda: extra_workloads(vc, torch, stream, peak)),
@@ -869,6 +945,8 @@ def main():
     ap.add_argument("--no-extra", action="store_true", help="skip the context workloads")
     ap.add_argument("--no-search", action="store_true", help="skip the search block (batched PVC workload)")
     ap.add_argument("--search-steps", type=int, default=3, help="timed launches of the search block")
+    ap.add_argument("--c4-study", action="store_true",
+                    help="also solve the batched workload's over-budget graphs under a 2M-node budget")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="chung_lu_50k")
     ap.add_argument("--stream-requests", type=int, default=1000,
                     help="requests in the served-stream context measurement")

@@ -143,7 +143,14 @@ typedef struct vc_stats {
     int32_t retries;            /* solves repeated with larger capacities
                                    (opt.capacity_retries); the other fields describe
                                    the last attempt                                 */
-    int32_t reserved;
+    int32_t best_found;         /* summed over the queries: the size of the best
+                                   cover known when each stopped -- the answer when
+                                   solved (k + 1 for a PVC no), and for a search
+                                   that ran out of its node budget the forced
+                                   vertices plus the best cover the search had found
+                                   (or the initial bound): an upper bound on the
+                                   minimum that a caller can set beside a lower
+                                   bound of its own                                  */
 } vc_stats;
 
 /* Fill *opt with the defaults. */

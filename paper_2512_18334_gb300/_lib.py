@@ -85,7 +85,7 @@ class Stats(ctypes.Structure):
         ("crown_skipped", ctypes.c_int32),
         ("cuda_graph", ctypes.c_int32),
         ("retries", ctypes.c_int32),
-        ("reserved", ctypes.c_int32),
+        ("best_found", ctypes.c_int32),
     ]
 
     def to_dict(self) -> dict:

@@ -604,6 +604,12 @@ int solve_queries(vc_graph *g0, const std::vector<QueryRef> &qs, const vc_option
         // root [+ crown] [+ init, roots, publish, search] + finalize
         stats->launches = (nroots > 0 ? 6 : 2) + (opt.crown ? 1 : 0);
         stats->cuda_graph = graph_state;
+        for (int i = 0; i < nq; i++) {
+            const QueryDesc &Q = hq[i];
+            const int st_i = Q.status != VC_OK ? Q.status : (root_slot[i] >= 0 && kstatus ? kstatus : VC_OK);
+            if (st_i == VC_OK) stats->best_found += Q.k < 0 ? Q.result : (Q.yes ? Q.result : Q.k + 1);
+            else if (st_i == VC_EBUDGET && root_slot[i] >= 0) stats->best_found += Q.best;
+        }
         stats->ms_root = ms_root;
         stats->ms_search = ms_search;
         stats->ms_total =

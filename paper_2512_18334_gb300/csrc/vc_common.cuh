@@ -93,6 +93,9 @@ struct QueryDesc {
     int *cover_out;      // non-null: finalisation writes the same list here too
                          // (mapped host memory, >= n entries)
     int lane;            // served requests: the size class whose resident search holds it
+    int best;            // a searched query that stopped early (node budget): the
+                         // size of the best cover known then (forced + the search's
+                         // incumbent, or the initial bound)
 };
 
 // One served request as seen after a time slice, written by the device into

@@ -1513,7 +1513,11 @@ __global__ void __launch_bounds__(kRootThreads) finalize_kernel(QueryDesc *qs, c
 {
     __shared__ int red[33];
     QueryDesc &Q = qs[blockIdx.x];
-    if (Q.status != VC_OK) return;
+    if (Q.status != VC_OK) {
+        // a search stopped early keeps its incumbent as the best size known
+        if (mode == 2 && !Q.answered && Q.np > 0 && threadIdx.x == 0) Q.best = Q.forced + reg[Q.root_entry].val;
+        return;
+    }
     if ((mode == 1 && !Q.answered) || (mode == 2 && Q.answered)) return;
     finalize_query(Q, reg, reg_words, wcap, red);
 }
