@@ -216,7 +216,11 @@ int vc_solve_batch(int32_t count, vc_graph *const *graphs, const int32_t *ks,
  * n <= 65536).  Every GPU that loads this library holds it until the
  * process exits.  The first call on a device looks up the array's device
  * address (cudaGetSymbolAddress) and sets a kernel attribute; make that
- * first call before any stream capture.  All calls share the array and it
+ * first call before any stream capture.  With CUDA's lazy module loading
+ * (the default) that first call may also load the library's device code,
+ * which allocates the 2 MiB array and the code itself and synchronises: make
+ * it outside any region that must not allocate (a warm-up call at start-up).
+ * Calls after it on the same device allocate nothing.  All calls share the array and it
  * keeps the last call's contents, so calls whose work overlaps on the GPU
  * (on different streams, or from different host threads) race: serialise
  * them.  Larger graphs are rejected with VC_ECAPACITY; nothing is allocated
@@ -238,6 +242,10 @@ int vc_solve_batch(int32_t count, vc_graph *const *graphs, const int32_t *ks,
  *                              settled the answer), the answer when
  *                              answered (minimum size; PVC: size or -1),
  *                              max degree of the induced subgraph.
+ * Witness: d_forced plus any cover of the induced subgraph is a cover.  When
+ * the root phase settles the answer through the greedy bound (answered = 1
+ * and the answer exceeds the forced count), the greedy cover that reaches it
+ * is NOT exported: no witness is returned for that answer.
  * Asynchronous on `cuda_stream`: d_info is valid once the stream reaches
  * the end of the call.  Returns VC_OK, VC_EINVAL (bad arguments),
  * VC_ECAPACITY (n > 65536) or VC_ECUDA (launch failure). */

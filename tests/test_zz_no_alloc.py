@@ -116,3 +116,70 @@ def test_static_rejects_oversized_graph(env):
     rc = vc._L.lib().vc_root_reduce_static(65537, 0, None, None, -1, None, None, None, None, _p(info), None)
     assert rc == vc.VC_ECAPACITY
     assert "capacity" in vc._L.strerror(rc)
+
+
+@pytest.mark.parametrize("name,make", CASES[:4] + CASES[5:])
+def test_static_decision_queries_match_regular_entry_point(env, name, make):
+    # k = OPT and k = OPT - 1: the root phase bounded by k + 1, against the
+    # regular decision call's root phase and answer
+    torch, vc = env
+    g = make()
+    dg = vc.Graph.from_csr(g.row_ptr, g.col)
+    opt, _, _ = vc.solve_min(dg)
+    for k in (opt, opt - 1):
+        if k < 0:
+            continue
+        yes, _, st = vc.solve_k(dg, k)
+        inf, forced, _, _, _ = call_static(torch, vc, g, k=k)
+        assert inf[1] == st["forced"] and len(forced) == st["forced"]
+        assert inf[2] == st["n_induced"]
+        if inf[5]:
+            assert (inf[6] >= 0) == bool(yes)
+            if yes:
+                assert inf[6] <= k
+    dg.close()
+
+
+def test_static_reports_malformed_graphs(env):
+    torch, vc = env
+    # 0-1 and 1-2 listed once each: not mirrored
+    rp = np.array([0, 1, 2, 2], np.int32)
+    col = np.array([1, 2], np.int32)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    trp = torch.from_numpy(rp).to(dev)
+    tcol = torch.from_numpy(col).to(dev)
+    bufs = [torch.full((8,), -1, dtype=torch.int32, device=dev) for _ in range(4)]
+    info = torch.full((8,), -7, dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    rc = vc._L.lib().vc_root_reduce_static(3, 2, _p(trp), _p(tcol), -1, _p(bufs[0]), _p(bufs[1]), _p(bufs[2]),
+                                            _p(bufs[3]), _p(info), ctypes.c_void_p(stream.cuda_stream))
+    assert rc == vc.VC_OK
+    stream.synchronize()
+    assert int(info[0]) == vc.VC_EINVAL
+
+
+def test_static_call_allocates_nothing(env):
+    # after a warm-up call on this device, the free device memory is the same
+    # before and after two more calls (every buffer is the caller's, made first)
+    torch, vc = env
+    g = gg.chung_lu(20_000, 2.5, 6.0, 800.0, 3)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    n, m2 = g.n, int(g.row_ptr[-1])
+    rp = torch.from_numpy(np.ascontiguousarray(g.row_ptr)).to(dev)
+    col = torch.from_numpy(g.col).to(dev)
+    forced, irp, icol, iorig = (torch.empty((x,), dtype=torch.int32, device=dev) for x in (n, n + 1, m2, n))
+    info = torch.empty((8,), dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    L = vc._L.lib()
+
+    def call():
+        return L.vc_root_reduce_static(n, m2, _p(rp), _p(col), -1, _p(forced), _p(irp), _p(icol), _p(iorig),
+                                       _p(info), ctypes.c_void_p(stream.cuda_stream))
+
+    assert call() == vc.VC_OK
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    assert call() == vc.VC_OK and call() == vc.VC_OK
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
+    assert int(info[0]) == vc.VC_OK
