@@ -98,6 +98,13 @@ typedef struct vc_options {
                                  (worst case about 48 GB for one solve); a solve
                                  that retried frees its grown buffers before it
                                  returns.  vc_autotune does not retry */
+    int32_t label_propagation;/* how a node's graph is split into connected
+                                 components (Section 3.2): 0 (default) union-find,
+                                 one pass over the live edges; 1 label propagation,
+                                 every live vertex pulling the smallest label of its
+                                 live neighbours (rows walked by 8-lane groups of a
+                                 warp) and then its label's label, in rounds until
+                                 one changes nothing.  Answers do not change */
 } vc_options;
 
 /* What a solve did.  All counters are totals over the launch. */

@@ -47,6 +47,7 @@ class Options(ctypes.Structure):
         ("crown", ctypes.c_int32),
         ("cuda_graph", ctypes.c_int32),
         ("capacity_retries", ctypes.c_int32),
+        ("label_propagation", ctypes.c_int32),
     ]
 
 

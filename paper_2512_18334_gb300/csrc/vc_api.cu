@@ -507,6 +507,7 @@ int solve_queries(vc_graph *g0, const std::vector<QueryRef> &qs, const vc_option
         P.no_bounds = opt.disable_bounds ? 1 : 0;
         P.breakdown = opt.breakdown ? 1 : 0;
         P.no_dyn_bounds = opt.disable_dyn_bounds ? 1 : 0;
+        P.comp_lp = opt.label_propagation ? 1 : 0;
         P.wglobal = pl.wglobal_bytes > 0 ? ws.wglobal.as<char>() : nullptr;
         P.wglobal_stride = pl.wglobal_bytes;
         // upload of the root slots, search, finalisation and read-back: one

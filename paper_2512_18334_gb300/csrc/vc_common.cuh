@@ -208,6 +208,7 @@ struct SearchParams {
                               // window (ablation of Section 4.3)
     int breakdown;            // 1: count SM cycles per activity (kPhase*)
     int no_dyn_bounds;        // 1: no dynamic tightening of component bounds (ablation)
+    int comp_lp;              // 1: components by label propagation, 0: union-find
     char *wglobal;            // non-null: each worker's node arrays live here (they do
                               // not fit in shared memory), wglobal_stride bytes apart
     long long wglobal_stride;

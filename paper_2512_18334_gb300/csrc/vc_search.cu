@@ -1319,6 +1319,74 @@ struct Worker {
         return nc;
     }
 
+    // Connected components of the live vertices in [lo, hi] by label
+    // propagation, the alternative to find_components.  In each round every
+    // live vertex takes the smallest label among its own and its live
+    // neighbours' (pull form: the kGroup lanes of a group read the row, a
+    // shuffle takes their minimum), then its label's label (pointer jumping);
+    // rounds repeat until one lowers no label.  A label only falls and always
+    // names a vertex of the same component, and after a round without change
+    // the two ends of every live edge carry the same label, so the fixpoint
+    // labels each component by its smallest relative index: the labels and
+    // the count find_components leaves.  The number of rounds grows with the
+    // logarithm of the components' diameter; each costs a pass over the live
+    // edges and one team reduction.
+    __device__ int find_components_lp()
+    {
+        const int W = hi - lo + 1;
+        volatile int *vl = (volatile int *)lab;
+        for (int i = tm.rank; i < W; i += tm.size()) lab[i] = d[lo + i - wlo] > 0 ? i : -1;
+        tm.sync();
+        // each round that changes a label moves the minimum one more hop at
+        // least, so W + 1 rounds always reach the fixpoint
+        for (int round = 0; round <= W; round++) {
+            int changed = 0;
+            for (int base = 0; base < W; base += ngroups()) {   // uniform over the warp
+                const int i = base + group();
+                int m = INT32_MAX, r0 = 0, r1 = 0;
+                bool live = false;
+                if (i < W) {
+                    const int v = lo + i;
+                    live = d[v - wlo] > 0;
+                    if (live) {
+                        m = vl[i];
+                        r0 = rp[v];
+                        r1 = rp[v + 1];
+                    }
+                }
+                const int wmax = __reduce_max_sync(kFull, (r1 - r0 + kGroup - 1) / kGroup);
+                for (int ch = 0; ch < wmax; ch++) {
+                    const int e = r0 + ch * kGroup + glane();
+                    if (e < r1) {
+                        const int u = col[e];
+                        if (u >= lo && u <= hi && d[u - wlo] > 0) m = min(m, vl[u - lo]);
+                    }
+                }
+                for (int o = kGroup / 2; o > 0; o >>= 1) m = min(m, __shfl_xor_sync(kFull, m, o));
+                if (live && glane() == 0) {
+                    bytes_local += 8 + 4ll * (r1 - r0);
+                    if (m < vl[i]) {
+                        atomicMin(&lab[i], m);
+                        changed = 1;
+                    }
+                }
+            }
+            for (int i = tm.rank; i < W; i += tm.size()) {
+                const int l = vl[i];
+                if (l < 0) continue;
+                const int ll = vl[l];
+                if (ll < l) {
+                    atomicMin(&lab[i], ll);
+                    changed = 1;
+                }
+            }
+            if (tm.sum(changed) == 0) break;
+        }
+        int roots = 0;
+        for (int i = tm.rank; i < W; i += tm.size()) roots += vl[i] == i;
+        return tm.sum(roots);
+    }
+
     // Cover of a chordless cycle component starting at vertex s: every other
     // vertex along the cycle (ceil(L/2) of them).  One thread.
     __device__ void cover_cycle(int s)
@@ -1650,7 +1718,7 @@ struct Worker {
             if (P.use_components) {
                 const bool clique = (long long)st.live * (st.live - 1) == st.e2;
                 const bool cycle = st.dmax == 2 && st.e2 == 2ll * st.live;
-                const int ncomp = find_components(clique || cycle);
+                const int ncomp = P.comp_lp ? find_components_lp() : find_components(clique || cycle);
                 if (ncomp >= 2 || clique || cycle) {
                     const int r = handle_components(B);
                     lap(kPhComp);

@@ -570,6 +570,7 @@ int vc_server_create(const vc_server_config *cfg_in, void *cuda_stream, vc_serve
         P.no_bounds = 0;
         P.breakdown = 0;
         P.no_dyn_bounds = 0;
+        P.comp_lp = 0;
         P.wglobal = pl.wglobal_bytes > 0 ? L.wglobal.as<char>() : nullptr;
         P.wglobal_stride = pl.wglobal_bytes;
         for (DevBuf *b : {&L.stack, &L.wl, &L.wl_seq, &L.reg, &L.reg_words, &L.comp_scratch, &L.ctl, &L.stack_top,

@@ -11,7 +11,7 @@ import oracle
 pytestmark = pytest.mark.gpu
 
 SWITCHES = [dict(disable_bounds=1), dict(disable_root_rules=1), dict(use_components=0), dict(load_balance=0),
-            dict(disable_dyn_bounds=1),
+            dict(disable_dyn_bounds=1), dict(label_propagation=1), dict(label_propagation=1, team=32),
             dict(disable_bounds=1, disable_root_rules=1), dict(disable_bounds=1, team=256),
             dict(disable_root_rules=1, team=32)]
 

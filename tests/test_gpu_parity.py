@@ -134,6 +134,50 @@ def test_chung_lu_50k(vc):
     assert st["n_induced"] <= 64
 
 
+def _spiders(hubs, legs, leg_len):
+    # hubs, each with `legs` paths of leg_len vertices hanging off it: the
+    # leaves peel inwards until the hubs, still of high degree, are forced
+    u, v, n = [], [], 0
+    for _ in range(hubs):
+        h = n
+        n += 1
+        for _ in range(legs):
+            prev = h
+            for _ in range(leg_len):
+                u.append(prev)
+                v.append(n)
+                prev = n
+                n += 1
+    return gg.from_edges(n, u, v, "spiders")
+
+
+def test_residual_rounds_on_one_cta(vc):
+    # n >= 8192: once the live graph fits in one CTA's shared memory, the last
+    # rounds of the unbounded rules run there on a renumbered copy; answers
+    # (and witnesses) must stay exact whether the graph vanishes, keeps a
+    # core for the greedy bound, bounded rules and search, or keeps hubs
+    # whose long rows are applied by whole warps
+    cases = [gg.chung_lu(20_000, 2.5, 6.0, 800.0, 7), gg.chung_lu(60_000, 2.5, 6.0, 2000.0, 3),
+             gg.chung_lu(30_000, 2.2, 8.0, 3000.0, 5), _spiders(12, 300, 3), _spiders(40, 120, 2)]
+    for g in cases:
+        want = oracle.mvc(g.n, g.row_ptr, g.col, node_budget=2_000_000)[0]
+        for _ in range(2):
+            assert gpu_min(vc, g)[0] == want, g.name
+    parts = [gg.random_forest(9000, 40, 11)] + [gg.gnm(40, 90, s) for s in range(20)] + [_spiders(3, 200, 3)]
+    g = gg.disjoint_union(parts)
+    want = sum(oracle.mvc(p.n, p.row_ptr, p.col)[0] for p in parts)
+    size, st = gpu_min(vc, g)
+    assert size == want and st["n_induced"] > 0
+    dg = vc.Graph.from_csr(g.row_ptr, g.col)
+    try:
+        yes, cover, _ = vc.solve_k(dg, want)
+        assert yes and len(cover) <= want
+        check_cover(g, cover, len(cover))
+        assert not vc.solve_k(dg, want - 1)[0]
+    finally:
+        dg.close()
+
+
 def test_chung_lu_50k_decision_and_independent_set(vc):
     # the cluster root phase settles this graph and writes the cover list
     # itself; the decision form and the complement go through finalisation
@@ -332,6 +376,35 @@ def test_component_labels_with_every_block_size(vc, team):
     want = oracle.mvc(u.n, u.row_ptr, u.col)[0]
     for _ in range(3):
         assert gpu_min(vc, u, team=team)[0] == want
+
+
+@pytest.mark.parametrize("team", [32, 128, 1024])
+def test_label_propagation_finds_the_same_components(vc, team):
+    # the two ways of splitting a node into components (union-find, label
+    # propagation) must give the same components: long cycles need many
+    # label rounds, the union splits into 350 pieces at its first node, all
+    # closed by the clique and cycle rules
+    for g, want in [(gg.cycle(1001), 501), (gg.cycle(1000), 500), (gg.path(777), 388)]:
+        assert gpu_min(vc, g, team=team, label_propagation=1)[0] == want
+    u = gg.disjoint_union([gg.cycle(5 + (s % 7)) for s in range(300)] + [gg.complete(4 + s % 3) for s in range(50)])
+    want = oracle.mvc(u.n, u.row_ptr, u.col)[0]
+    size, st = gpu_min(vc, u, team=team, label_propagation=1)
+    size_uf, st_uf = gpu_min(vc, u, team=team)
+    assert size == size_uf == want
+    assert st["trivial_components"] == st_uf["trivial_components"]
+    if st_uf["nodes"] > 0:
+        assert st_uf["trivial_components"] == 350
+    g = gg.component_heavy(3, copies=6, copy_n=30, p=0.15, chain=3)
+    opt = oracle.mvc(g.n, g.row_ptr, g.col, node_budget=5_000_000)[0]
+    assert gpu_min(vc, g, team=team, label_propagation=1)[0] == opt
+    dg = vc.Graph.from_csr(g.row_ptr, g.col)
+    try:
+        yes, cover, _ = vc.solve_k(dg, opt, team=team, label_propagation=1)
+        assert yes and len(cover) <= opt
+        check_cover(g, cover, len(cover))
+        assert not vc.solve_k(dg, opt - 1, team=team, label_propagation=1)[0]
+    finally:
+        dg.close()
 
 
 def test_workspace_pool_reuse_and_trim(vc):
