@@ -748,6 +748,7 @@ struct ClusterShared {
     int slot[2][kClusterMax][4];   // rank 0's copy is the exchange area (double-buffered)
     unsigned long long rbase[kClusterMax];   // dynamic smem base of each rank
     unsigned long long rsh[kClusterMax];     // ClusterShared of each rank
+    int solo_forced;  // rank 0: vertices it forced in the rounds it ran alone
 };
 
 // per CTA: 16-bit degrees, then forced / mark / frontier bitmaps
@@ -769,6 +770,8 @@ struct ClusterRoot {
     // (lrp: offsets into lcol, relative to this CTA's first entry); null:
     // the rows are read from the global CSR
     const int *lrp, *lcol;
+    char *lsm;               // this CTA's dynamic shared memory
+    int res_off, smem_cap;   // where the staged rows (or rank 0's residual graph) start; its size
 
     __device__ ClusterRoot(QueryDesc &q, ClusterShared &s, char *smem, int cs_, int smem_bytes)
         : Q(q), sh(s), cl(cgx::this_cluster())
@@ -797,6 +800,9 @@ struct ClusterRoot {
         lrp = nullptr;
         lcol = nullptr;
         const size_t off = (cluster_smem_bytes(chunk) + 15) & ~(size_t)15;
+        lsm = smem;
+        res_off = (int)off;
+        smem_cap = smem_bytes;
         const int e0 = vcnt > 0 ? __ldg(rp + vbeg) : 0, e1 = vcnt > 0 ? __ldg(rp + vbeg + vcnt) : 0;
         const long long need = 4ll * (chunk + 1) + 4ll * (e1 - e0);
         if (vcnt > 0 && (long long)off + need <= (long long)smem_bytes) {
@@ -976,9 +982,16 @@ struct ClusterRoot {
             }
             return;
         }
-        for (int e = a + lane; e < b; e += stride) {
-            const int x = cp[e];
-            if (live(x)) { dec(x); push_frontier(x); }
+        for (int e0 = a + lane; e0 < b; e0 += 4 * stride) {
+            int xs[4];
+            bool lv[4];
+#pragma unroll
+            for (int j = 0; j < 4; j++) xs[j] = e0 + j * stride < b ? cp[e0 + j * stride] : -1;
+#pragma unroll
+            for (int j = 0; j < 4; j++) lv[j] = xs[j] >= 0 && live(xs[j]);
+#pragma unroll
+            for (int j = 0; j < 4; j++)
+                if (lv[j]) { dec(xs[j]); push_frontier(xs[j]); }
         }
     }
 
@@ -1109,6 +1122,302 @@ struct ClusterRoot {
         __syncthreads();
     }
 
+    // ---- the residual graph on rank 0
+    //
+    // Once the live graph is small, rank 0 takes it over as a compact CSR in
+    // its own shared memory and runs the remaining rounds of the unbounded
+    // rules alone: block barriers and local shared-memory atomics instead of
+    // cluster barriers and remote ones, while the other CTAs wait at one
+    // cluster barrier.  The live vertices are renumbered in increasing order,
+    // so every tie-break (lowest index) decides as it would have in the
+    // cluster, and the rounds reach the same fixpoint.  The forced bits and
+    // degrees go back to their owners afterwards, so the later stages (greedy
+    // bound, bounded rules, induced graph, forced list) see the state the
+    // cluster rounds would have left.  Row entries and degrees are 16-bit.
+    static constexpr int kResHeavyRow = 32;     // longer rows are applied by a whole warp
+    static constexpr int kResPerVertex = 11;    // bound on the layout's bytes per vertex
+    static constexpr int kResSlack = 128;
+    static constexpr int kResNever = 1 << 26;   // a per-CTA bound that never fits
+    static constexpr int kResNone = 0xffff;     // no vertex (ids are below it); sorts last
+
+    __device__ static size_t a16(size_t x) { return (x + 15) & ~(size_t)15; }
+    // rank 0's layout: row offsets (int), row entries (u16), degrees (u16),
+    // forced / mark / frontier bitmaps, one vertex list; at most
+    // kResPerVertex * np + 2 * m2p + kResSlack bytes
+    __device__ static size_t residual_bytes(int np, long long m2p)
+    {
+        const size_t w = (size_t)(np + 31) / 32 * 4;
+        return a16(4 * ((size_t)np + 1)) + a16(2 * (size_t)m2p) + a16(2 * (size_t)np) + 3 * a16(w) +
+               a16(4 * (size_t)np);
+    }
+    __device__ int residual_room() const { return smem_cap - res_off; }
+
+    // The rounds on the residual graph run on the first kSoloThreads threads
+    // of rank 0, synchronised by a named barrier (the other warps, if any,
+    // go on to the cluster barrier).  The first rounds after the hand-off
+    // examine a few thousand vertices: every warp of the block has work.
+    static constexpr int kSoloThreads = kRootThreads;
+    __device__ __forceinline__ static void solo_bar() { asm volatile("bar.sync 1, %0;" ::"n"(kSoloThreads) : "memory"); }
+
+    // Append the set bits of words[0, nw) (cleared here) to list as indices,
+    // in any order, counting in *counter; with fold, only bits not yet in
+    // fold[], which gets them.  Called by the solo threads.
+    __device__ __forceinline__ void solo_list(uint32_t *words, int nw, uint32_t *fold, int *list, int *counter)
+    {
+        for (int j = threadIdx.x; j < nw; j += kSoloThreads) {
+            uint32_t x = words[j];
+            if (!x) continue;
+            words[j] = 0;
+            if (fold) {
+                x &= ~fold[j];
+                fold[j] |= x;
+            }
+            if (!x) continue;
+            int k = atomicAdd(counter, __popc(x));
+            while (x) {
+                list[k++] = j * 32 + __ffs(x) - 1;
+                x &= x - 1;
+            }
+        }
+    }
+
+    // The unbounded rules on the residual graph (rank 0 alone), then the
+    // result back to the owners.  Input: Q.rp2 / Q.col2 (the CSR, new ids),
+    // Q.fr1 (degree | frontier bit << 16), Q.orig (new id -> vertex).
+    // Four barriers a round: frontier listed, examined, marks listed, applied.
+    __device__ void solo_rounds(int np, int m2p)
+    {
+        char *p = lsm + res_off;
+        int *rrp = (int *)p;             p += a16(4 * ((size_t)np + 1));
+        uint16_t *rcol = (uint16_t *)p;  p += a16(2 * (size_t)m2p);
+        uint16_t *rdeg = (uint16_t *)p;  p += a16(2 * (size_t)np);
+        const int nw = (np + 31) / 32;
+        uint32_t *rforced = (uint32_t *)p; p += a16(4 * (size_t)nw);
+        uint32_t *rmark = (uint32_t *)p;   p += a16(4 * (size_t)nw);
+        uint32_t *rflag = (uint32_t *)p;   p += a16(4 * (size_t)nw);
+        int *rlist = (int *)p;
+        const int T = blockDim.x, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+        // the copy in: eight independent loads in flight per thread
+        for (int i0 = threadIdx.x; i0 <= np; i0 += 8 * T) {
+            int xs[8];
+#pragma unroll
+            for (int j = 0; j < 8; j++) xs[j] = i0 + j * T <= np ? __ldcg(Q.rp2 + i0 + j * T) : 0;
+#pragma unroll
+            for (int j = 0; j < 8; j++)
+                if (i0 + j * T <= np) rrp[i0 + j * T] = xs[j];
+        }
+        for (int e0 = threadIdx.x; e0 < m2p; e0 += 8 * T) {
+            int xs[8];
+#pragma unroll
+            for (int j = 0; j < 8; j++) xs[j] = e0 + j * T < m2p ? __ldcg(Q.col2 + e0 + j * T) : 0;
+#pragma unroll
+            for (int j = 0; j < 8; j++)
+                if (e0 + j * T < m2p) rcol[e0 + j * T] = (uint16_t)(xs[j] >= 0 && xs[j] < np ? xs[j] : kResNone);
+        }
+        for (int j = warp; j < nw; j += T >> 5) {
+            const int i = j * 32 + lane;
+            const int x = i < np ? __ldcg(Q.fr1 + i) : 0;
+            if (i < np) rdeg[i] = (uint16_t)(x & 0xffff);
+            const unsigned f = __ballot_sync(kFull, (x >> 16) & 1);
+            if (lane == 0) { rflag[j] = f; rforced[j] = 0; rmark[j] = 0; }
+        }
+        if (threadIdx.x == 0) { sh.cnt = 0; sh.fcnt = 0; }
+        __syncthreads();
+        if (threadIdx.x >= kSoloThreads) return;
+        const volatile uint16_t *vdeg = rdeg;
+        const volatile uint32_t *vforced = rforced;
+        auto rlive = [&](int x) { return x < np && !((vforced[x >> 5] >> (x & 31)) & 1u) && vdeg[x] > 0; };
+        auto rdec = [&](int x) {
+            unsigned *w = (unsigned *)((char *)rdeg + 2 * (x & ~1));
+            atomicSub(w, 1u << (16 * (x & 1)));
+        };
+        auto rbit = [&](uint32_t *words, int x) { atomicOr(&words[x >> 5], 1u << (x & 31)); };
+        // a vertex that is not forced and has a neighbour forced in this round
+        // is live: its degree counts every decrement still to come
+        auto unforced = [&](int x) { return x < np && !((vforced[x >> 5] >> (x & 31)) & 1u); };
+        int forced_cnt = 0, rounds = 0;
+        for (int guard = 0; guard <= 2 * np + 2; guard++) {
+            solo_list(rflag, nw, nullptr, rlist, &sh.cnt);
+            solo_bar();                                                   // frontier listed
+            const int fsize = *(volatile int *)&sh.cnt;
+            if (fsize == 0) break;
+            for (int i = threadIdx.x; i < fsize; i += kSoloThreads) {
+                const int v = rlist[i];
+                if ((vforced[v >> 5] >> (v & 31)) & 1u) continue;
+                const int dv = vdeg[v];
+                if (dv == 0 || dv > 2) continue;
+                int u = -1, w = -1;
+                const int a = rrp[v], b = rrp[v + 1];
+                for (int e0 = a; e0 < b; e0 += 8) {
+                    int xs[8];
+                    bool lv[8];
+#pragma unroll
+                    for (int j = 0; j < 8; j++) xs[j] = e0 + j < b ? rcol[e0 + j] : kResNone;
+#pragma unroll
+                    for (int j = 0; j < 8; j++) lv[j] = rlive(xs[j]);
+#pragma unroll
+                    for (int j = 0; j < 8; j++)
+                        if (lv[j] && w < 0) {
+                            if (u < 0) u = xs[j]; else w = xs[j];
+                        }
+                    if (dv == 1 ? u >= 0 : w >= 0) break;
+                }
+                if (dv == 1) {
+                    if (u < 0) continue;
+                    if (vdeg[u] == 1 && u < v) rbit(rflag, u);   // u's rule fires instead
+                    else rbit(rmark, u);
+                } else if (w >= 0) {
+                    // u-w an edge?  search the shorter row (sorted)
+                    const bool by_u = rrp[u + 1] - rrp[u] <= rrp[w + 1] - rrp[w];
+                    int lo = by_u ? rrp[u] : rrp[w], hi = (by_u ? rrp[u + 1] : rrp[w + 1]) - 1;
+                    const int key = by_u ? w : u;
+                    bool tri = false;
+                    while (lo <= hi) {
+                        const int mid = (lo + hi) >> 1, x = rcol[mid];
+                        if (x == key) { tri = true; break; }
+                        if (x < key) lo = mid + 1; else hi = mid - 1;
+                    }
+                    if (tri) {
+                        int pv = INT_MAX;
+                        if (vdeg[u] == 2 && u < v) pv = u;
+                        if (vdeg[w] == 2 && w < v && w < pv) pv = w;
+                        if (pv != INT_MAX) rbit(rflag, pv);
+                        else { rbit(rmark, u); rbit(rmark, w); }
+                    }
+                }
+            }
+            solo_bar();                                                   // examined
+            if (threadIdx.x == 0) sh.cnt = 0;   // (fsize is read; the next listing follows two barriers)
+            solo_list(rmark, nw, rforced, rlist, &sh.fcnt);
+            solo_bar();                                                   // marks listed
+            const int cnt = *(volatile int *)&sh.fcnt;
+            rounds++;
+            forced_cnt += cnt;
+            // apply: a row by its thread, or by the whole warp when long
+            for (int base = warp * 32; base < cnt; base += kSoloThreads) {
+                const int i = base + lane;
+                int u = -1, a = 0, b = 0;
+                if (i < cnt) {
+                    u = rlist[i];
+                    a = rrp[u];
+                    b = rrp[u + 1];
+                }
+                const bool wide = b - a > kResHeavyRow;
+                if (!wide) {
+                    for (int e0 = a; e0 < b; e0 += 8) {
+                        int xs[8];
+                        bool uf[8];
+#pragma unroll
+                        for (int j = 0; j < 8; j++) xs[j] = e0 + j < b ? rcol[e0 + j] : kResNone;
+#pragma unroll
+                        for (int j = 0; j < 8; j++) uf[j] = unforced(xs[j]);
+#pragma unroll
+                        for (int j = 0; j < 8; j++)
+                            if (uf[j]) { rdec(xs[j]); rbit(rflag, xs[j]); }
+                    }
+                }
+                unsigned hm = __ballot_sync(kFull, wide);
+                while (hm) {
+                    const int src = __ffs(hm) - 1;
+                    hm &= hm - 1;
+                    const int aa = __shfl_sync(kFull, a, src), bb = __shfl_sync(kFull, b, src);
+                    for (int e = aa + lane; e < bb; e += 32) {
+                        const int x = rcol[e];
+                        if (unforced(x)) { rdec(x); rbit(rflag, x); }
+                    }
+                }
+            }
+            solo_bar();                                                   // applied
+            if (threadIdx.x == 0) sh.fcnt = 0;  // (cnt is read; the next listing follows two barriers)
+        }
+        // back to the owners: degrees and the new forced bits
+        for (int i = threadIdx.x; i < np; i += kSoloThreads) {
+            const int v = __ldcg(Q.orig + i);
+            const int r = v >> cs, l = v & (chunk - 1);
+            ((volatile uint16_t *)degp(r))[l] = vdeg[i];
+            if ((vforced[i >> 5] >> (i & 31)) & 1u) atomicOr(&forcedp(r)[l >> 5], 1u << (l & 31));
+        }
+        if (threadIdx.x == 0) {
+            sh.solo_forced = forced_cnt;
+            Q.rounds += rounds;
+        }
+    }
+
+    // Hand the live graph to rank 0 when its layout fits there.  Called by
+    // every thread of every CTA at the top of a round of the unbounded rules
+    // (the last round's decrements have landed); returns the same in every
+    // CTA: true when the rounds are finished (ftot updated), false when the
+    // graph did not fit after all (nothing changed).
+    __device__ bool residual_solo()
+    {
+        const int T = blockDim.x;
+        const int per = (vcnt + T - 1) / T;
+        const int beg = vbeg + min(vcnt, (int)threadIdx.x * per), end = vbeg + min(vcnt, ((int)threadIdx.x + 1) * per);
+        int cnt = 0, dsum = 0;
+        for (int v = beg; v < end; v++)
+            if (live(v)) { cnt++; dsum += d(v); }
+        int lnp, lm2;
+        const int loff = block_excl_scan(cnt, sh.red, &lnp);
+        const int leoff = block_excl_scan(dsum, sh.red, &lm2);
+        int coff, np, ceoff, m2p;
+        exchange_prefix(lnp, lm2, coff, np, ceoff, m2p);
+        if (np == 0 || np >= kResNone || residual_bytes(np, m2p) > (size_t)residual_room())
+            return false;
+        // new ids in increasing vertex order; degree and frontier bit travel in Q.fr1
+        int *nid = Q.aux;
+        const uint32_t *fw = flagp(rank);
+        int id = coff + loff, eo = ceoff + leoff;
+        for (int v = beg; v < end; v++) {
+            if (live(v)) {
+                const int l = v - vbeg;
+                const int f = (int)((fw[l >> 5] >> (l & 31)) & 1u);
+                nid[v] = id;
+                Q.orig[id] = v;
+                Q.rp2[id] = eo;
+                Q.fr1[id] = d(v) | (f << 16);
+                id++;
+                eo += d(v);
+            } else {
+                nid[v] = -1;
+            }
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < (chunk >> 5); i += T) flagp(rank)[i] = 0;   // carried in Q.fr1 now
+        if (rank == 0 && threadIdx.x == 0) Q.rp2[np] = m2p;
+        cl.sync();
+        // rows: the live neighbours, renumbered (a live vertex's degree is
+        // its number of live neighbours)
+        for (int i = coff + threadIdx.x; i < coff + lnp; i += T) {
+            const int v = Q.orig[i];
+            int o = Q.rp2[i];
+            const int lim = o + d(v);
+            int a, b;
+            const int *cp;
+            own_row(v, a, b, cp);
+            for (int e0 = a; e0 < b && o < lim; e0 += 8) {
+                int xs[8];
+#pragma unroll
+                for (int j = 0; j < 8; j++) xs[j] = e0 + j < b ? cp[e0 + j] : -1;
+#pragma unroll
+                for (int j = 0; j < 8; j++) xs[j] = xs[j] >= 0 ? __ldcg(nid + xs[j]) : -1;
+#pragma unroll
+                for (int j = 0; j < 8; j++)
+                    if (xs[j] >= 0 && o < lim) Q.col2[o++] = xs[j];
+            }
+            while (o < lim) Q.col2[o++] = -1;   // (never: the degree counts the live neighbours)
+        }
+        cl.sync();
+        if (rank == 0) solo_rounds(np, m2p);
+        cl.sync();   // the owners' degrees and forced bits are final
+        ftot += *(volatile int *)&shp(0)->solo_forced;
+        if (rank == 0) {
+            if (threadIdx.x == 0) Q.forced = ftot;
+            lrp = nullptr;   // the residual graph overwrote rank 0's staged rows
+            lcol = nullptr;
+        }
+        return true;
+    }
+
     // Synchronous rounds, two cluster barriers each:
     //   B1  last round's decrements and frontier bits have landed, and its
     //       totals (published before B1) are read: stop when it marked
@@ -1131,6 +1440,8 @@ struct ClusterRoot {
                 ftot += (int)tcnt;
                 if (rank == 0 && threadIdx.x == 0) Q.forced = ftot;
                 if (tcnt == 0 && tpend == 0) return true;
+                // the bound on the live graph's layout, from the last round
+                if (!hd && sh.tot[2] + kResSlack <= residual_room() && residual_solo()) return true;
             }
             const int bud = hd ? bound - ftot - 1 : INT_MAX;
             if (hd && bud < 0) return false;
@@ -1162,13 +1473,22 @@ struct ClusterRoot {
             cl.sync();                                                    // B2
             // this round's marks that I own: list them, fold them into forced
             const int cnt = bits_to_list(markp(rank), ml, true);
-            int pend = 0;
+            int pend = 0, est = 0;
             {
                 const uint32_t *fw = flagp(rank);
                 for (int i = threadIdx.x; i < chunk / 32; i += blockDim.x) pend += __popc(fw[i]);
                 pend = block_sum(pend, sh.red);
+                // the live graph only shrinks from here: its vertices and
+                // degrees now bound the residual layout at the next round
+                if (!hd) {
+                    for (int i = threadIdx.x; i < vcnt; i += blockDim.x) {
+                        const int v = vbeg + i;
+                        if (live(v)) est += kResPerVertex + 2 * d(v);
+                    }
+                    est = block_sum(est, sh.red);
+                }
             }
-            publish(cnt, pend, 0, dm);   // read by every CTA after the next B1
+            publish(cnt, pend, hd ? kResNever : min(est, kResNever), dm);   // read by every CTA after the next B1
             if (rank == 0 && threadIdx.x == 0) Q.rounds++;
             if (cnt == 0) continue;
             // (the forced set is the forced bitmap here; Q.forced gets its
