@@ -961,44 +961,42 @@ struct ClusterRoot {
         }
     }
 
-    // u is in the cover: every live neighbour loses one degree and joins the
-    // next frontier (forced bits already include this round's marks)
+    // u is in the cover: every neighbour loses one degree and joins the next
+    // frontier, with no test, so the walk issues only remote reductions.  A
+    // degree is the initial degree less the forced neighbours (each forced
+    // vertex's row is applied once), so it never goes below zero; for a
+    // vertex that is not forced it is the number of its live neighbours, and
+    // a forced vertex's degree and frontier bit are never used.
     __device__ void apply_row(int u, int lane, int stride)
     {
         int a, b;
         const int *cp;
         own_row(u, a, b, cp);
-        if (stride == 1) {
-            for (int e0 = a; e0 < b; e0 += 8) {
-                int xs[8];
-                bool lv[8];
-#pragma unroll
-                for (int j = 0; j < 8; j++) xs[j] = e0 + j < b ? cp[e0 + j] : -1;
-#pragma unroll
-                for (int j = 0; j < 8; j++) lv[j] = xs[j] >= 0 && live(xs[j]);
-#pragma unroll
-                for (int j = 0; j < 8; j++)
-                    if (lv[j]) { dec(xs[j]); push_frontier(xs[j]); }
-            }
-            return;
+        for (int e = a + lane; e < b; e += stride) {
+            const int x = cp[e];
+            dec(x);
+            push_frontier(x);
         }
-        for (int e0 = a + lane; e0 < b; e0 += 4 * stride) {
-            int xs[4];
-            bool lv[4];
-#pragma unroll
-            for (int j = 0; j < 4; j++) xs[j] = e0 + j * stride < b ? cp[e0 + j * stride] : -1;
-#pragma unroll
-            for (int j = 0; j < 4; j++) lv[j] = xs[j] >= 0 && live(xs[j]);
-#pragma unroll
-            for (int j = 0; j < 4; j++)
-                if (lv[j]) { dec(xs[j]); push_frontier(xs[j]); }
+    }
+
+    // The bits of x (vertices base[0..31]) whose degree is 1 or 2: the only
+    // frontier vertices a rule can fire at (the high-degree rule looks at
+    // every vertex, in full rounds).
+    __device__ __forceinline__ static uint32_t low_degree_bits(uint32_t x, const uint16_t *base)
+    {
+        uint32_t y = x;
+        while (y) {
+            const int b = __ffs(y) - 1;
+            y &= y - 1;
+            if ((unsigned)((const volatile uint16_t *)base)[b] - 1u > 1u) x &= ~(1u << b);
         }
+        return x;
     }
 
     // Take the set bits of `words` (my chunk; fetched and cleared atomically,
     // other CTAs may be setting bits meanwhile) into list[] as vertex ids;
-    // returns the count.  new_forced: keep only bits whose forced bit is clear
-    // and add them to the forced bitmap.  Each thread owns words tid + j*T,
+    // returns the count.  Only bits whose forced bit is clear are kept;
+    // new_forced: they are added to the forced bitmap.  Each thread owns words tid + j*T,
     // j < 4 (chunk <= 4 * 32 * blockDim).
     __device__ int bits_to_list(uint32_t *words, int *list, bool new_forced)
     {
@@ -1012,7 +1010,12 @@ struct ClusterRoot {
             uint32_t x = 0;
             if (i < nw) {
                 x = atomicExch(&words[i], 0u);
-                if (new_forced) { x &= ~fw[i]; fw[i] |= x; }
+                if (new_forced) {
+                    x &= ~fw[i];
+                    fw[i] |= x;
+                } else {
+                    x &= ~fw[i];
+                }
             }
             m[j] = x;
             c += __popc(x);
@@ -1159,19 +1162,20 @@ struct ClusterRoot {
     static constexpr int kSoloThreads = kRootThreads;
     __device__ __forceinline__ static void solo_bar() { asm volatile("bar.sync 1, %0;" ::"n"(kSoloThreads) : "memory"); }
 
-    // Append the set bits of words[0, nw) (cleared here) to list as indices,
-    // in any order, counting in *counter; with fold, only bits not yet in
-    // fold[], which gets them.  Called by the solo threads.
-    __device__ __forceinline__ void solo_list(uint32_t *words, int nw, uint32_t *fold, int *list, int *counter)
+    // Append the set bits of words[0, nw) (cleared here) that are not in
+    // forced[] to list as indices, in any order, counting in *counter; with
+    // fold, forced[] gets them, else (a frontier) only those of degree 1 or 2
+    // are kept.  Called by the solo threads.
+    __device__ __forceinline__ void solo_list(uint32_t *words, int nw, uint32_t *forced, bool fold,
+                                              const uint16_t *deg, int *list, int *counter)
     {
         for (int j = threadIdx.x; j < nw; j += kSoloThreads) {
             uint32_t x = words[j];
             if (!x) continue;
             words[j] = 0;
-            if (fold) {
-                x &= ~fold[j];
-                fold[j] |= x;
-            }
+            x &= ~forced[j];
+            if (fold) forced[j] |= x;
+            else x = low_degree_bits(x, deg + j * 32);
             if (!x) continue;
             int k = atomicAdd(counter, __popc(x));
             while (x) {
@@ -1232,12 +1236,10 @@ struct ClusterRoot {
             atomicSub(w, 1u << (16 * (x & 1)));
         };
         auto rbit = [&](uint32_t *words, int x) { atomicOr(&words[x >> 5], 1u << (x & 31)); };
-        // a vertex that is not forced and has a neighbour forced in this round
-        // is live: its degree counts every decrement still to come
-        auto unforced = [&](int x) { return x < np && !((vforced[x >> 5] >> (x & 31)) & 1u); };
+        // (the apply step needs no test either: see apply_row)
         int forced_cnt = 0, rounds = 0;
         for (int guard = 0; guard <= 2 * np + 2; guard++) {
-            solo_list(rflag, nw, nullptr, rlist, &sh.cnt);
+            solo_list(rflag, nw, rforced, false, rdeg, rlist, &sh.cnt);
             solo_bar();                                                   // frontier listed
             const int fsize = *(volatile int *)&sh.cnt;
             if (fsize == 0) break;
@@ -1288,7 +1290,7 @@ struct ClusterRoot {
             }
             solo_bar();                                                   // examined
             if (threadIdx.x == 0) sh.cnt = 0;   // (fsize is read; the next listing follows two barriers)
-            solo_list(rmark, nw, rforced, rlist, &sh.fcnt);
+            solo_list(rmark, nw, rforced, true, rdeg, rlist, &sh.fcnt);
             solo_bar();                                                   // marks listed
             const int cnt = *(volatile int *)&sh.fcnt;
             rounds++;
@@ -1304,16 +1306,9 @@ struct ClusterRoot {
                 }
                 const bool wide = b - a > kResHeavyRow;
                 if (!wide) {
-                    for (int e0 = a; e0 < b; e0 += 8) {
-                        int xs[8];
-                        bool uf[8];
-#pragma unroll
-                        for (int j = 0; j < 8; j++) xs[j] = e0 + j < b ? rcol[e0 + j] : kResNone;
-#pragma unroll
-                        for (int j = 0; j < 8; j++) uf[j] = unforced(xs[j]);
-#pragma unroll
-                        for (int j = 0; j < 8; j++)
-                            if (uf[j]) { rdec(xs[j]); rbit(rflag, xs[j]); }
+                    for (int e = a; e < b; e++) {
+                        const int x = rcol[e];
+                        if (x < np) { rdec(x); rbit(rflag, x); }
                     }
                 }
                 unsigned hm = __ballot_sync(kFull, wide);
@@ -1323,7 +1318,7 @@ struct ClusterRoot {
                     const int aa = __shfl_sync(kFull, a, src), bb = __shfl_sync(kFull, b, src);
                     for (int e = aa + lane; e < bb; e += 32) {
                         const int x = rcol[e];
-                        if (unforced(x)) { rdec(x); rbit(rflag, x); }
+                        if (x < np) { rdec(x); rbit(rflag, x); }
                     }
                 }
             }
