@@ -82,12 +82,15 @@ typedef struct vc_options {
     int32_t crown;            /* 1: crown reduction at the root (Section 4.2), applied
                                  as the Nemhauser-Trotter LP reduction on the device
                                  after the other root rules; answers do not change */
-    int32_t cuda_graph;       /* 1 (default): the search phase (root-slot upload,
-                                 registry and worklist set-up, root placement, the
-                                 persistent search, finalisation, read-back) is
-                                 captured once per launch shape into a CUDA graph
+    int32_t cuda_graph;       /* 1 (default): the root phase (descriptor upload,
+                                 root [and crown] kernel, finalisation of settled
+                                 queries, read-back) and the search phase (root-
+                                 slot upload, registry and worklist set-up, root
+                                 placement, the persistent search, finalisation,
+                                 read-back) are each captured into a CUDA graph
+                                 the second time a launch shape comes in a row,
                                  kept with the workspace and replayed with one
-                                 launch; 0: its kernels are launched one by one */
+                                 launch; 0: their kernels are launched one by one */
     int32_t capacity_retries; /* when the search runs out of capacity, solve again
                                  up to this many times (default 2; 0: report
                                  VC_ECAPACITY at once), doubling only what ran out:

@@ -40,10 +40,17 @@ def _stream_handle(stream) -> ctypes.c_void_p:
     return ctypes.c_void_p(int(stream.cuda_stream))   # torch.cuda.Stream
 
 
+_DEFAULTS: bytes | None = None
+
+
 def options(**kw) -> Options:
     """vc_options with the library defaults, overridden by keyword."""
-    o = Options()
-    _L.check(_L.lib().vc_options_default(ctypes.byref(o)))
+    global _DEFAULTS
+    if _DEFAULTS is None:
+        o = Options()
+        _L.check(_L.lib().vc_options_default(ctypes.byref(o)))
+        _DEFAULTS = bytes(o)
+    o = Options.from_buffer_copy(_DEFAULTS)
     for k, v in kw.items():
         if not hasattr(o, k):
             raise TypeError(f"unknown option {k}")
@@ -124,13 +131,13 @@ def solve_min(g: Graph, opts: Options | None = None, want_cover: bool = True, **
     """Minimum vertex cover: (size, cover int32 array or None, stats dict)."""
     o = _opts(opts, kw)
     size = ctypes.c_int32(-1)
-    cover = np.zeros(max(g.n, 1), np.int32)
+    cover = np.empty(max(g.n, 1), np.int32) if want_cover else None
     clen = ctypes.c_int32(0)
     st = Stats()
     _L.check(_L.lib().vc_solve_min(g._h, ctypes.byref(o), ctypes.byref(size),
-                                   cover.ctypes.data_as(ctypes.c_void_p) if want_cover else None,
+                                   cover.ctypes.data if want_cover else None,
                                    ctypes.byref(clen), ctypes.byref(st)), st)
-    return size.value, (cover[:clen.value].copy() if want_cover else None), st.to_dict()
+    return size.value, (cover[:clen.value] if want_cover else None), st.to_dict()
 
 
 def solve_k(g: Graph, k: int, opts: Options | None = None, want_cover: bool = True, **kw):

@@ -90,18 +90,16 @@ class Stats(ctypes.Structure):
     ]
 
     def to_dict(self) -> dict:
-        d = {}
-        for name, _ in self._fields_:
-            v = getattr(self, name)
-            if name == "comp_hist":
-                d[name] = {i + 2: int(v[i]) for i in range(16) if v[i]}
-            elif name == "root_cycles":
-                d[name] = [int(x) for x in v]
-            elif name == "phase_cycles":
-                d[name] = {PHASES[i]: int(v[i]) for i in range(6)}
-            else:
-                d[name] = v
+        d = {name: getattr(self, name) for name in _STATS_SCALARS}
+        h = self.comp_hist
+        d["comp_hist"] = {i + 2: int(h[i]) for i in range(16) if h[i]}
+        d["root_cycles"] = list(self.root_cycles)
+        pc = self.phase_cycles
+        d["phase_cycles"] = {PHASES[i]: int(pc[i]) for i in range(6)}
         return d
+
+
+_STATS_SCALARS = [name for name, _ in Stats._fields_ if name not in ("comp_hist", "root_cycles", "phase_cycles")]
 
 
 class ServerConfig(ctypes.Structure):

@@ -61,6 +61,7 @@ struct Workspace {
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
     cudaStream_t cap = nullptr;   // capture stream (the caller's may be the legacy default stream)
     GraphSlot search_graph;
+    GraphSlot root_graph;   // phase 1: descriptor upload, root [+ crown], finalisation, read-back
     int init()
     {
         for (auto &e : ev)
@@ -78,6 +79,7 @@ struct Workspace {
         for (auto &e : ev)
             if (e) { cudaEventDestroy(e); e = nullptr; }
         search_graph.release();
+        root_graph.release();
         if (cap) cudaStreamDestroy(cap);
         cap = nullptr;
     }
@@ -378,21 +380,49 @@ int solve_queries(vc_graph *g0, const std::vector<QueryRef> &qs, const vc_option
         Q.cover_out = want_cov && covers[i] ? ws.hcov.dev_as<int>() + coff[i] : nullptr;
     }
     QueryDesc *dq = ws.queries.as<QueryDesc>();
-    VC_CK(cudaMemcpyAsync(dq, hq, sizeof(QueryDesc) * nq, cudaMemcpyHostToDevice, s));
 
-    // ---- phase 1: root reduction and induced subgraphs
-    VC_CK(cudaEventRecord(ws.ev[0], s));
+    // ---- phase 1: root reduction and induced subgraphs (descriptor upload,
+    // root [+ crown] kernel, finalisation of the queries the root phase
+    // settled, read-back): one graph launch once this shape has been seen
     int max_n_in = 0, max_deg_in = 0;
     for (int i = 0; i < nq; i++) {
         max_n_in = std::max(max_n_in, qs[i].g->n);
         max_deg_in = std::max(max_deg_in, qs[i].g->maxdeg);
     }
-    VC_CK(root_run(dq, nq, max_n_in, max_deg_in, s));
-    if (opt.crown) VC_CK(crown_run(dq, nq, s));
-    VC_CK(cudaEventRecord(ws.ev[1], s));
-    // the queries the root phase settled are final now
-    VC_CK(finalize_run(dq, nq, nullptr, nullptr, 0, s, 1));
-    VC_CK(cudaMemcpyAsync(hq, dq, sizeof(QueryDesc) * nq, cudaMemcpyDeviceToHost, s));
+    auto phase1 = [&](cudaStream_t st, bool capturing) -> cudaError_t {
+        const unsigned fl = capturing ? cudaEventRecordExternal : 0u;
+        cudaError_t e = cudaMemcpyAsync(dq, hq, sizeof(QueryDesc) * nq, cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess) e = cudaEventRecordWithFlags(ws.ev[0], st, fl);
+        if (e == cudaSuccess) e = root_run(dq, nq, max_n_in, max_deg_in, st);
+        if (e == cudaSuccess && opt.crown) e = crown_run(dq, nq, st);
+        if (e == cudaSuccess) e = cudaEventRecordWithFlags(ws.ev[1], st, fl);
+        if (e == cudaSuccess) e = finalize_run(dq, nq, nullptr, nullptr, 0, st, 1);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(hq, dq, sizeof(QueryDesc) * nq, cudaMemcpyDeviceToHost, st);
+        return e;
+    };
+    {
+        cudaError_t e = cudaSuccess;
+        if (opt.cuda_graph) {
+            struct {
+                QueryDesc *dq, *hq;
+                int nq, max_n, max_deg, crown;
+                cudaEvent_t ev0, ev1;
+            } key;
+            memset(&key, 0, sizeof(key));
+            key.dq = dq;
+            key.hq = hq;
+            key.nq = nq;
+            key.max_n = max_n_in;
+            key.max_deg = max_deg_in;
+            key.crown = opt.crown ? 1 : 0;
+            key.ev0 = ws.ev[0];
+            key.ev1 = ws.ev[1];
+            graph_enqueue(ws, ws.root_graph, &key, sizeof(key), s, phase1, &e);
+        } else {
+            e = phase1(s, false);
+        }
+        VC_CK(e);
+    }
     VC_CK(cudaStreamSynchronize(s));
 
     int max_np = 0, max_deg = 0, nroots = 0;

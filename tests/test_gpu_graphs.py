@@ -107,3 +107,36 @@ def test_batches_match_direct_launches(vc):
     assert 2 in seen
     for d in dgs:
         d.close()
+
+
+@pytest.mark.parametrize("big", [False, True])
+def test_root_phase_replayed_with_new_descriptors(vc, big):
+    # The root phase is one graph launch once a shape (query count, largest
+    # n and degree) comes twice in a row.  Relabelled copies share the shape
+    # but not the CSR, and the decision bound changes between calls: each
+    # replay must read the descriptors of its own call.  big: n >= 8192, the
+    # root phase on a thread-block cluster.
+    if big:
+        parts = [gg.random_forest(9000, 40, 3)] + [gg.gnm(40, 90, s) for s in range(12)]
+        base = gg.disjoint_union(parts)
+        want = sum(oracle.mvc(p.n, p.row_ptr, p.col)[0] for p in parts)
+    else:
+        base = gg.chung_lu(3000, 2.5, 6.0, 300.0, 9)
+        want = opt_of(base)
+    gs = [base, gg.relabel(base, 1), gg.relabel(base, 2)]
+    dgs = [vc.Graph.from_csr(g.row_ptr, g.col) for g in gs]
+    try:
+        for rep in range(3):
+            for g, dg in zip(gs, dgs):
+                size, cover, _ = vc.solve_min(dg)
+                assert size == want
+                check_cover(g, cover, size)
+                yes, cover, _ = vc.solve_k(dg, want)
+                assert yes
+                check_cover(g, cover, want)
+                assert not vc.solve_k(dg, want - 1)[0]
+        # the same calls launched kernel by kernel agree
+        assert vc.solve_min(dgs[0], cuda_graph=0)[0] == want
+    finally:
+        for dg in dgs:
+            dg.close()
