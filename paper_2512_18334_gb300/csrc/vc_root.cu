@@ -141,6 +141,59 @@ __device__ __forceinline__ int block_max(int x, int *red)
     return red[32];
 }
 
+// two block-wide sums at once (one set of barriers); both results replace
+// the inputs in every thread
+__device__ __forceinline__ void block_sum2(int &a, int &b, int *red, int *red2)
+{
+    int x = __reduce_add_sync(kFull, a), y = __reduce_add_sync(kFull, b);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
+    __syncthreads();
+    if (l == 0) { red[w] = x; red2[w] = y; }
+    __syncthreads();
+    if (w == 0) {
+        x = l < nw ? red[l] : 0;
+        y = l < nw ? red2[l] : 0;
+        x = __reduce_add_sync(kFull, x);
+        y = __reduce_add_sync(kFull, y);
+        if (l == 0) { red[32] = x; red2[32] = y; }
+    }
+    __syncthreads();
+    a = red[32];
+    b = red2[32];
+}
+
+// exclusive running maximum of one value per thread (block-wide, in thread
+// order; 0 for thread 0)
+__device__ __forceinline__ int block_excl_max(int x, int *red)
+{
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
+    int inc = x;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(kFull, inc, o);
+        if (l >= o) inc = max(inc, y);
+    }
+    int exc = __shfl_up_sync(kFull, inc, 1);
+    if (l == 0) exc = 0;
+    __syncthreads();
+    if (l == 31) red[w] = inc;
+    __syncthreads();
+    if (w == 0) {
+        const int y = l < nw ? red[l] : 0;
+        int sc = y;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int z = __shfl_up_sync(kFull, sc, o);
+            if (l >= o) sc = max(sc, z);
+        }
+        int ex = __shfl_up_sync(kFull, sc, 1);
+        if (l == 0) ex = 0;
+        if (l < nw) red[l] = ex;
+    }
+    __syncthreads();
+    const int r = max(red[w], exc);
+    __syncthreads();
+    return r;
+}
+
 // exclusive scan of one value per thread (block-wide); returns the prefix and
 // the total in *tot
 __device__ __forceinline__ int block_excl_scan(int x, int *red, int *tot)
@@ -740,10 +793,12 @@ constexpr int kClusterMax = 16;
 constexpr int kClusterMinN = 8192;    // smaller graphs use one block
 
 struct ClusterShared {
-    int cnt;          // marks owned by this CTA in this round
-    int fcnt;         // frontier entries owned by this CTA
-    int hcnt, gcnt;   // heavy / giant row lists of this CTA
+    int cnt;          // solo rounds: frontier entries listed
+    int fcnt;         // solo rounds: marks listed
+    int hcnt;         // heavy rows of this CTA's examination
+    int tcnt;         // triangle checks of this CTA's examination
     int red[33];
+    int red2[33];
     long long tot[4]; // exchanged totals (local copy)
     int slot[2][kClusterMax][4];   // rank 0's copy is the exchange area (double-buffered)
     unsigned long long rbase[kClusterMax];   // dynamic smem base of each rank
@@ -751,10 +806,45 @@ struct ClusterShared {
     int solo_forced;  // rank 0: vertices it forced in the rounds it ran alone
 };
 
-// per CTA: 16-bit degrees, then forced / mark / frontier bitmaps
-__host__ __device__ inline size_t cluster_smem_bytes(int chunk)
+// Per CTA of a C-CTA cluster, for chunk owned vertices: 16-bit degrees; a
+// copy of the forced bitmap of the whole graph (C chunks); the vertices
+// forced in the current round (whole graph); two mark bitmaps (alternate
+// rounds) and the frontier bitmap of the owned vertices; the degrees at the
+// end of the previous round.  Every part is a multiple of 16 bytes (chunk
+// >= 1024).
+__host__ __device__ inline size_t cluster_smem_bytes(int chunk, int C)
 {
-    return (size_t)chunk * 2 + 3 * ((size_t)chunk / 8);
+    return (size_t)chunk * 2 + 2 * ((size_t)C * chunk / 8) + 3 * ((size_t)chunk / 8) + (size_t)chunk * 2;
+}
+
+// The degree update of one CTA of the cluster root kernel after a round's
+// marks, over its staged rows: lcol[0, E) are the row entries of its owned
+// vertices, lsrc[e] the owned vertex whose row holds entry e, nw the
+// vertices forced in the round (whole graph), fw the forced bits of the
+// owned vertices (this round's included), dw the owned 16-bit degrees (two
+// to a word).  Every owned vertex that is not forced loses one degree per
+// newly forced neighbour (a fire-and-forget reduction; the next frontier is
+// found afterwards by comparing degrees).  The entries are scanned flat,
+// four per thread in flight.  Only local shared memory is touched.  Not
+// inlined: the round loop around it keeps many values live, and this loop
+// runs without spills on a register allocation of its own.
+__device__ __noinline__ void cluster_pull_flat(const int *lcol, const uint16_t *lsrc, const uint32_t *nw,
+                                               const uint32_t *fw, unsigned *dw, int E)
+{
+    const int T = blockDim.x;
+    for (int e0 = threadIdx.x; e0 < E; e0 += 4 * T) {
+        int xs[4];
+#pragma unroll
+        for (int j = 0; j < 4; j++) xs[j] = e0 + j * T < E ? lcol[e0 + j * T] : -1;
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            const int x = xs[j];
+            if (x < 0 || !((nw[x >> 5] >> (x & 31)) & 1u)) continue;
+            const int v = lsrc[e0 + j * T];
+            if (!((fw[v >> 5] >> (v & 31)) & 1u))        // (a forced vertex's degree is not used again)
+                atomicSub(dw + (v >> 1), 1u << (16 * (v & 1)));
+        }
+    }
 }
 
 struct ClusterRoot {
@@ -766,12 +856,16 @@ struct ClusterRoot {
     const int *rp, *col;
     int ftot;                // cluster-wide forced count (same in every CTA)
     int xround;              // exchange buffer selector
+    int mbuf;                // mark bitmap of the current round (0 / 1)
+    int repb;                // bytes of a whole-graph bitmap (C chunks)
     // rows of the vertices owned here, staged in shared memory when they fit
     // (lrp: offsets into lcol, relative to this CTA's first entry); null:
     // the rows are read from the global CSR
     const int *lrp, *lcol;
+    const uint16_t *lsrc;    // with staged rows, when it fits: the owned vertex of each row entry
     char *lsm;               // this CTA's dynamic shared memory
     int res_off, smem_cap;   // where the staged rows (or rank 0's residual graph) start; its size
+    int e_first;             // global index of this CTA's first row entry
 
     __device__ ClusterRoot(QueryDesc &q, ClusterShared &s, char *smem, int cs_, int smem_bytes)
         : Q(q), sh(s), cl(cgx::this_cluster())
@@ -787,31 +881,59 @@ struct ClusterRoot {
         col = Q.col;
         ftot = 0;
         xround = 0;
+        mbuf = 0;
+        repb = C * (chunk / 8);
         if (threadIdx.x < C) {
             sh.rbase[threadIdx.x] = (unsigned long long)cl.map_shared_rank(smem, threadIdx.x);
             sh.rsh[threadIdx.x] = (unsigned long long)cl.map_shared_rank(&sh, threadIdx.x);
         }
         uint32_t *bits = (uint32_t *)(smem + 2 * (size_t)chunk);
-        for (int i = threadIdx.x; i < 3 * (chunk / 32); i += blockDim.x) bits[i] = 0;
+        const int nbits = (int)((cluster_smem_bytes(chunk, C) - 2 * (size_t)chunk) / 4);
+        for (int i = threadIdx.x; i < nbits; i += blockDim.x) bits[i] = 0;
         // Stage this CTA's rows: every examination and application of the
         // rules, the greedy bound and the induced graph read only rows of
         // vertices owned here (a shared-memory load instead of an L2 round
         // trip); the triangle test's rows of other vertices stay global.
         lrp = nullptr;
         lcol = nullptr;
-        const size_t off = (cluster_smem_bytes(chunk) + 15) & ~(size_t)15;
+        lsrc = nullptr;
+        const size_t off = (cluster_smem_bytes(chunk, C) + 15) & ~(size_t)15;
         lsm = smem;
         res_off = (int)off;
         smem_cap = smem_bytes;
         const int e0 = vcnt > 0 ? __ldg(rp + vbeg) : 0, e1 = vcnt > 0 ? __ldg(rp + vbeg + vcnt) : 0;
-        const long long need = 4ll * (chunk + 1) + 4ll * (e1 - e0);
+        e_first = e0;
+        const int E = e1 - e0;
+        const long long need = 4ll * (chunk + 1) + 4ll * E;
         if (vcnt > 0 && (long long)off + need <= (long long)smem_bytes) {
             int *r = (int *)(smem + off), *c = r + chunk + 1;
             for (int i = threadIdx.x; i <= vcnt; i += blockDim.x) r[i] = __ldg(rp + vbeg + i) - e0;
-            for (int e = threadIdx.x; e < e1 - e0; e += blockDim.x) c[e] = __ldg(col + e0 + e);
+            for (int e = threadIdx.x; e < E; e += blockDim.x) c[e] = __ldg(col + e0 + e);
             lrp = r;
             lcol = c;
+            const size_t soff = (off + (size_t)need + 15) & ~(size_t)15;
+            if (soff + 2 * (size_t)E <= (size_t)smem_bytes) {
+                // lsrc[e]: 0 everywhere, each non-empty row's vertex at its
+                // first entry, then a running maximum (rows are in vertex order)
+                uint16_t *src = (uint16_t *)(smem + soff);
+                for (int e = threadIdx.x; e < E; e += blockDim.x) src[e] = 0;
+                __syncthreads();
+                for (int i = threadIdx.x; i < vcnt; i += blockDim.x)
+                    if (r[i] < r[i + 1]) src[r[i]] = (uint16_t)i;
+                __syncthreads();
+                const int s0 = (int)((long long)E * threadIdx.x / blockDim.x);
+                const int s1 = (int)((long long)E * (threadIdx.x + 1) / blockDim.x);
+                int m = 0;
+                for (int e = s0; e < s1; e++) m = max(m, (int)src[e]);
+                int carry = block_excl_max(m, sh.red);
+                for (int e = s0; e < s1; e++) {
+                    carry = max(carry, (int)src[e]);
+                    src[e] = (uint16_t)carry;
+                }
+                lsrc = src;
+            }
         }
+        __syncthreads();
     }
 
     // Row of a vertex owned here: entries [a, b) of *cp.
@@ -832,23 +954,41 @@ struct ClusterRoot {
     // ---- distributed state
     __device__ __forceinline__ char *base(int r) const { return (char *)sh.rbase[r]; }
     __device__ __forceinline__ uint16_t *degp(int r) const { return (uint16_t *)base(r); }
-    __device__ __forceinline__ uint32_t *forcedp(int r) const { return (uint32_t *)(base(r) + 2 * (size_t)chunk); }
-    __device__ __forceinline__ uint32_t *markp(int r) const
+    // rank r's copy of the forced bitmap (whole graph)
+    __device__ __forceinline__ uint32_t *repp(int r) const { return (uint32_t *)(base(r) + 2 * (size_t)chunk); }
+    // the forced bits of rank r's own vertices in rank r's copy: always current
+    __device__ __forceinline__ uint32_t *forcedp(int r) const { return repp(r) + ((size_t)r << (cs - 5)); }
+    __device__ __forceinline__ uint32_t *markp(int r, int b) const
     {
-        return (uint32_t *)(base(r) + 2 * (size_t)chunk + chunk / 8);
+        return (uint32_t *)(base(r) + 2 * (size_t)chunk + 2 * (size_t)repb + (size_t)b * (chunk / 8));
     }
     __device__ __forceinline__ uint32_t *flagp(int r) const
     {
-        return (uint32_t *)(base(r) + 2 * (size_t)chunk + 2 * (chunk / 8));
+        return (uint32_t *)(base(r) + 2 * (size_t)chunk + 2 * (size_t)repb + 2 * (chunk / 8));
     }
+    // this CTA's own arrays through its local shared-memory window
+    __device__ __forceinline__ uint16_t *ldeg() const { return (uint16_t *)lsm; }
+    __device__ __forceinline__ uint32_t *lrep() const { return (uint32_t *)(lsm + 2 * (size_t)chunk); }
+    __device__ __forceinline__ uint32_t *lnew() const { return (uint32_t *)(lsm + 2 * (size_t)chunk + repb); }
+    __device__ __forceinline__ uint32_t *lmark() const { return (uint32_t *)(lsm + 2 * (size_t)chunk + 2 * (size_t)repb); }
+    __device__ __forceinline__ uint32_t *lflag() const { return lmark() + 2 * (chunk >> 5); }
+    __device__ __forceinline__ uint16_t *lprev() const { return (uint16_t *)(lflag() + (chunk >> 5)); }
     __device__ __forceinline__ ClusterShared *shp(int r) const { return (ClusterShared *)sh.rsh[r]; }
 
-    __device__ __forceinline__ int d(int v) const { return ((volatile uint16_t *)degp(v >> cs))[v & (chunk - 1)]; }
+    __device__ __forceinline__ int d(int v) const
+    {
+        if ((v >> cs) == rank) return ((volatile uint16_t *)ldeg())[v - vbeg];
+        return ((volatile uint16_t *)degp(v >> cs))[v & (chunk - 1)];
+    }
     __device__ __forceinline__ bool forced(int v) const
     {
         const int l = v & (chunk - 1);
         return ((volatile uint32_t *)forcedp(v >> cs))[l >> 5] >> (l & 31) & 1u;
     }
+    // In the rule rounds every CTA's copy of the forced bitmap is complete
+    // (it is refreshed when the rounds start and every round's marks are
+    // added to every copy): a local load.
+    __device__ __forceinline__ bool rforced(int v) const { return lrep()[v >> 5] >> (v & 31) & 1u; }
     // a vertex is in the graph when it was not forced in an earlier round
     // and has a neighbour left
     __device__ __forceinline__ bool live(int x) const { return !forced(x) && d(x) > 0; }
@@ -857,28 +997,39 @@ struct ClusterRoot {
         const int l = v & (chunk - 1);
         atomicOr(&words[l >> 5], 1u << (l & 31));    // result unused: a fire-and-forget reduction
     }
-    __device__ __forceinline__ void dec(int v)
-    {
-        const int l = v & (chunk - 1);
-        unsigned *w = (unsigned *)((char *)degp(v >> cs) + 2 * (l & ~1));
-        atomicSub(w, 1u << (16 * (l & 1)));          // result unused
-    }
-    __device__ __forceinline__ void mark(int u) { set_bit(markp(u >> cs), u); }
+    __device__ __forceinline__ void mark(int u) { set_bit(markp(u >> cs, mbuf), u); }
     __device__ __forceinline__ void push_frontier(int x) { set_bit(flagp(x >> cs), x); }
 
-    // Is u-w an edge?  The CSR is symmetric, so the shorter of the two rows
-    // is searched: a hub's row would cost a binary search of dependent loads.
-    __device__ bool row_has(int u, int w) const
+    // Is key in the sorted global row[0, len)?  Eight probes at a time: each
+    // step loads eight evenly spaced entries together (one round trip) and
+    // keeps the gap that can hold key, so a 2,000-entry row takes three
+    // steps and a short scan instead of eleven dependent loads.
+    __device__ static bool row_find(const int *row, int len, int key)
     {
-        const int au = __ldg(rp + u), bu = __ldg(rp + u + 1);
-        const int aw = __ldg(rp + w), bw = __ldg(rp + w + 1);
-        const bool by_u = bu - au <= bw - aw;
-        const int a = by_u ? au : aw, b = by_u ? bu : bw, key = by_u ? w : u;
-        if (b - a > 16) return bsearch_row(col + a, b - a, key);
-        for (int e0 = a; e0 < b; e0 += 8) {
+        int lo = 0, hi = len;                      // key can only be in [lo, hi)
+        while (hi - lo > 16) {
+            const int step = (hi - lo) / 9;        // >= 1
             int xs[8];
 #pragma unroll
-            for (int j = 0; j < 8; j++) xs[j] = e0 + j < b ? __ldg(col + e0 + j) : -1;
+            for (int j = 0; j < 8; j++) xs[j] = __ldg(row + lo + (j + 1) * step);
+            int below = 0;
+            bool hit = false;
+#pragma unroll
+            for (int j = 0; j < 8; j++) {
+                below += xs[j] < key;
+                hit |= xs[j] == key;
+            }
+            if (hit) return true;
+            // the first `below` probes are < key, the rest > key
+            const int nlo = below == 0 ? lo : lo + below * step + 1;
+            const int nhi = below == 8 ? hi : lo + (below + 1) * step;
+            lo = nlo;
+            hi = nhi;
+        }
+        for (int e0 = lo; e0 < hi; e0 += 8) {
+            int xs[8];
+#pragma unroll
+            for (int j = 0; j < 8; j++) xs[j] = e0 + j < hi ? __ldg(row + e0 + j) : -1;
             bool hit = false;
 #pragma unroll
             for (int j = 0; j < 8; j++) hit |= xs[j] == key;
@@ -887,28 +1038,57 @@ struct ClusterRoot {
         return false;
     }
 
-    __device__ void decide(int v, int dv, int u, int w)
+    // Is u-w an edge?  The CSR is symmetric, so the shorter of the two rows
+    // is searched.
+    __device__ bool row_has(int u, int w) const
     {
-        if (dv == 1) {
-            if (u < 0) return;
-            if (d(u) == 1 && u < v) push_frontier(u);   // u's rule fires instead
-            else mark(u);
-        } else if (dv == 2) {
-            if (w < 0) return;
-            if (row_has(u, w)) {
-                int p = INT_MAX;
-                if (d(u) == 2 && u < v) p = u;
-                if (d(w) == 2 && w < v && w < p) p = w;
-                if (p != INT_MAX) push_frontier(p);
-                else { mark(u); mark(w); }
-            }
-        }
+        const int au = __ldg(rp + u), bu = __ldg(rp + u + 1);
+        const int aw = __ldg(rp + w), bw = __ldg(rp + w + 1);
+        const bool by_u = bu - au <= bw - aw;
+        return by_u ? row_find(col + au, bu - au, w) : row_find(col + aw, bw - aw, u);
     }
 
+    // The degree-one rule at v (its only live neighbour u); the lower end of
+    // an edge whose ends both have degree one decides, so the other end
+    // hands its turn to it.
+    __device__ __forceinline__ void decide_one(int v, int u)
+    {
+        if (u < v && d(u) == 1) push_frontier(u);   // u's rule fires instead
+        else mark(u);
+    }
+
+    // The degree-two-triangle rule at v with live neighbours u, w: lists the
+    // check for the triangle pass of the round (Q.deg / Q.heavy / Q.flag
+    // hold this CTA's list in its own range; at most one entry per owned
+    // vertex).
+    __device__ __forceinline__ void list_triangle(int v, int u, int w)
+    {
+        const int i = vbeg + atomicAdd(&sh.tcnt, 1);
+        Q.deg[i] = v;
+        Q.heavy[i] = u;
+        Q.flag[i] = w;
+    }
+
+    // A listed triangle check: when u-w is an edge the lowest degree-two
+    // vertex of the triangle fires (the others hand it their turn).
+    __device__ __forceinline__ void decide_triangle(int v, int u, int w)
+    {
+        if (!row_has(u, w)) return;
+        int p = INT_MAX;
+        if (u < v && d(u) == 2) p = u;
+        if (w < v && w < p && d(w) == 2) p = w;
+        if (p != INT_MAX) push_frontier(p);
+        else { mark(u); mark(w); }
+    }
+
+    // The rules at the owned vertex v.  Its live neighbours are exactly its
+    // neighbours that are not forced: a live vertex's degree counts them, so
+    // each of them keeps an edge (to v) and a degree of at least one.
     __device__ void examine(int *hv, int v, int bud)
     {
-        if (forced(v)) return;
-        const int dv = d(v);
+        const int i = v - vbeg;
+        if (rforced(v)) return;
+        const int dv = ldeg()[i];
         if (dv == 0) return;
         if (dv > bud) mark(v);
         if (dv > 2) return;
@@ -926,7 +1106,7 @@ struct ClusterRoot {
 #pragma unroll
             for (int j = 0; j < 8; j++) xs[j] = e0 + j < b ? cp[e0 + j] : -1;
 #pragma unroll
-            for (int j = 0; j < 8; j++) lv[j] = xs[j] >= 0 && live(xs[j]);
+            for (int j = 0; j < 8; j++) lv[j] = xs[j] >= 0 && !rforced(xs[j]);
 #pragma unroll
             for (int j = 0; j < 8; j++) {
                 if (lv[j] && w < 0) {
@@ -935,7 +1115,11 @@ struct ClusterRoot {
             }
             if (dv == 1 ? u >= 0 : w >= 0) break;
         }
-        decide(v, dv, u, w);
+        if (dv == 1) {
+            if (u >= 0) decide_one(v, u);
+        } else if (w >= 0) {
+            list_triangle(v, u, w);
+        }
     }
 
     __device__ void warp_live_nbrs(int v, int need, int &u, int &w) const
@@ -950,7 +1134,7 @@ struct ClusterRoot {
         for (int base0 = a; base0 < b && found < need; base0 += 32) {
             const int e = base0 + lane;
             const int x = e < b ? cp[e] : -1;
-            unsigned m = __ballot_sync(kFull, x >= 0 && live(x));
+            unsigned m = __ballot_sync(kFull, x >= 0 && !rforced(x));
             while (m && found < need) {
                 const int pos = __ffs(m) - 1;
                 const int val = __shfl_sync(kFull, x, pos);
@@ -961,22 +1145,92 @@ struct ClusterRoot {
         }
     }
 
-    // u is in the cover: every neighbour loses one degree and joins the next
-    // frontier, with no test, so the walk issues only remote reductions.  A
-    // degree is the initial degree less the forced neighbours (each forced
-    // vertex's row is applied once), so it never goes below zero; for a
-    // vertex that is not forced it is the number of its live neighbours, and
-    // a forced vertex's degree and frontier bit are never used.
-    __device__ void apply_row(int u, int lane, int stride)
+    // Row offsets and entries of the owned vertices, relative to this CTA's
+    // first entry: staged in shared memory, or the global CSR.
+    __device__ __forceinline__ int row_off(int i) const { return lcol ? lrp[i] : __ldg(rp + vbeg + i) - e_first; }
+    __device__ __forceinline__ int row_entry(int e) const { return lcol ? lcol[e] : __ldg(col + e_first + e); }
+
+    // This thread's share of the owned row entries for pull_walk: a
+    // contiguous range [pe0, pe1) of about equal size, starting in the row of
+    // owned vertex pi0 (the rows do not change, so it is found once).
+    __device__ void pull_range(int &pi0, int &pe0, int &pe1) const
     {
-        int a, b;
-        const int *cp;
-        own_row(u, a, b, cp);
-        for (int e = a + lane; e < b; e += stride) {
-            const int x = cp[e];
-            dec(x);
-            push_frontier(x);
+        const int E = vcnt > 0 ? row_off(vcnt) : 0;
+        pe0 = (int)((long long)E * threadIdx.x / blockDim.x);
+        pe1 = (int)((long long)E * (threadIdx.x + 1) / blockDim.x);
+        int lo = 0, hi = vcnt - 1;                   // the last row starting at or before pe0
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (row_off(mid) <= pe0) lo = mid; else hi = mid - 1;
         }
+        pi0 = lo;
+    }
+
+    // The degrees of the owned vertices after this round's marks (lnew()):
+    // every vertex that is still live loses one per newly forced neighbour
+    // (cluster_pull_flat, given lsrc).
+    __device__ __forceinline__ void pull_flat()
+    {
+        cluster_pull_flat(lcol, lsrc, lnew(), lrep() + (rank << (cs - 5)), (unsigned *)ldeg(), row_off(vcnt));
+    }
+
+    // The same without lsrc: each thread walks its range of entries row by
+    // row, skipping the rows of vertices that are forced or isolated, and
+    // subtracts each row's count at once.
+    __device__ void pull_walk(int pi0, int pe0, int pe1)
+    {
+        const uint32_t *nw = lnew(), *fw = lrep() + (rank << (cs - 5));
+        int i = pi0, e = pe0;
+        while (e < pe1) {
+            const int re = min(row_off(i + 1), pe1);
+            if (re > e) {
+                if (!((fw[i >> 5] >> (i & 31)) & 1u) && ldeg()[i] > 0) {
+                    int c = 0;
+                    for (; e < re; e++) {
+                        const int x = row_entry(e);
+                        c += (nw[x >> 5] >> (x & 31)) & 1u;
+                    }
+                    if (c) atomicSub((unsigned *)ldeg() + (i >> 1), (unsigned)c << (16 * (i & 1)));
+                }
+                e = re;
+            }
+            i++;
+        }
+    }
+
+    // Every CTA's copy of the forced bitmap from the owners' parts (the
+    // owners' parts are final: called after a cluster barrier).
+    __device__ void refresh_forced_copy()
+    {
+        const int wpr = chunk >> 5;
+        uint32_t *rep = lrep();
+        for (int w = threadIdx.x; w < C * wpr; w += blockDim.x) {
+            const int r = w / wpr;
+            if (r != rank) rep[w] = ((volatile uint32_t *)forcedp(r))[w - r * wpr];
+        }
+    }
+
+    // After the marks of a round have landed: every CTA reads every CTA's
+    // mark bitmap of the round, keeps the vertices not forced before in
+    // lnew() and adds them to its copy of the forced bitmap; returns their
+    // number (the same in every CTA).  16-byte loads.
+    __device__ int gather_marks()
+    {
+        const int wpr = chunk >> 5;                  // a multiple of 4
+        const int q4 = (C * wpr) >> 2;
+        uint4 *rep = (uint4 *)lrep(), *nw = (uint4 *)lnew();
+        int c = 0;
+        for (int q = threadIdx.x; q < q4; q += blockDim.x) {
+            const int w = q << 2, r = w / wpr;
+            const uint4 m = *(const uint4 *)(markp(r, mbuf) + (w - r * wpr));
+            const uint4 o = rep[q];
+            uint4 x;
+            x.x = m.x & ~o.x; x.y = m.y & ~o.y; x.z = m.z & ~o.z; x.w = m.w & ~o.w;
+            nw[q] = x;
+            rep[q] = make_uint4(o.x | x.x, o.y | x.y, o.z | x.z, o.w | x.w);
+            c += __popc(x.x) + __popc(x.y) + __popc(x.z) + __popc(x.w);
+        }
+        return block_sum(c, sh.red);
     }
 
     // The bits of x (vertices base[0..31]) whose degree is 1 or 2: the only
@@ -993,14 +1247,14 @@ struct ClusterRoot {
         return x;
     }
 
-    // Take the set bits of `words` (my chunk; fetched and cleared atomically,
-    // other CTAs may be setting bits meanwhile) into list[] as vertex ids;
-    // returns the count.  Only bits whose forced bit is clear are kept;
-    // new_forced: they are added to the forced bitmap.  Each thread owns words tid + j*T,
-    // j < 4 (chunk <= 4 * 32 * blockDim).
-    __device__ int bits_to_list(uint32_t *words, int *list, bool new_forced)
+    // Take the set bits of my frontier bitmap (fetched and cleared
+    // atomically: other CTAs may be setting bits meanwhile) into list[] as
+    // vertex ids, leaving out forced vertices; returns the count.  Each
+    // thread owns words tid + j*T, j < 4 (chunk <= 4 * 32 * blockDim).
+    __device__ int frontier_to_list(int *list)
     {
-        uint32_t *fw = forcedp(rank);
+        uint32_t *words = lflag();
+        const uint32_t *fw = lrep() + (rank << (cs - 5));
         const int nw = chunk >> 5;
         uint32_t m[4];
         int c = 0;
@@ -1008,15 +1262,7 @@ struct ClusterRoot {
         for (int j = 0; j < 4; j++) {
             const int i = threadIdx.x + j * blockDim.x;
             uint32_t x = 0;
-            if (i < nw) {
-                x = atomicExch(&words[i], 0u);
-                if (new_forced) {
-                    x &= ~fw[i];
-                    fw[i] |= x;
-                } else {
-                    x &= ~fw[i];
-                }
-            }
+            if (i < nw) x = atomicExch(&words[i], 0u) & ~fw[i];
             m[j] = x;
             c += __popc(x);
         }
@@ -1155,21 +1401,35 @@ struct ClusterRoot {
     }
     __device__ int residual_room() const { return smem_cap - res_off; }
 
-    // The rounds on the residual graph run on the first kSoloThreads threads
-    // of rank 0, synchronised by a named barrier (the other warps, if any,
-    // go on to the cluster barrier).  The first rounds after the hand-off
-    // examine a few thousand vertices: every warp of the block has work.
+    // The rounds on the residual graph run on the whole of rank 0's block
+    // (named barrier 1).  Even a round of a few dozen vertices is faster on
+    // the block than on one warp: its cost is the dependent shared-memory
+    // chain of examining one vertex, and a warp examines several in turn.
     static constexpr int kSoloThreads = kRootThreads;
-    __device__ __forceinline__ static void solo_bar() { asm volatile("bar.sync 1, %0;" ::"n"(kSoloThreads) : "memory"); }
+    template <int NT>
+    __device__ __forceinline__ static void solo_sync()
+    {
+        asm volatile("bar.sync 1, %0;" ::"n"(NT) : "memory");
+    }
+
+    // rank 0's residual graph and its state (new ids)
+    struct Solo {
+        int *rrp;
+        uint16_t *rcol, *rdeg;
+        uint32_t *rforced, *rmark, *rflag;
+        int *rlist;
+        int np, nw;
+    };
 
     // Append the set bits of words[0, nw) (cleared here) that are not in
     // forced[] to list as indices, in any order, counting in *counter; with
     // fold, forced[] gets them, else (a frontier) only those of degree 1 or 2
-    // are kept.  Called by the solo threads.
-    __device__ __forceinline__ void solo_list(uint32_t *words, int nw, uint32_t *forced, bool fold,
-                                              const uint16_t *deg, int *list, int *counter)
+    // are kept.  Called by the first NT threads.
+    template <int NT>
+    __device__ __forceinline__ static void solo_list(uint32_t *words, int nw, uint32_t *forced, bool fold,
+                                                     const uint16_t *deg, int *list, int *counter)
     {
-        for (int j = threadIdx.x; j < nw; j += kSoloThreads) {
+        for (int j = threadIdx.x; j < nw; j += NT) {
             uint32_t x = words[j];
             if (!x) continue;
             words[j] = 0;
@@ -1185,21 +1445,126 @@ struct ClusterRoot {
         }
     }
 
+    // One round of the unbounded rules on the listed frontier rlist[0,
+    // fsize), by the first NT threads of rank 0: examine, list the marks
+    // (folded into the forced bits), apply their rows.  Three barriers;
+    // returns the number of vertices forced.
+    template <int NT>
+    __device__ int solo_round(const Solo &R, int fsize)
+    {
+        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+        const int np = R.np;
+        const int *rrp = R.rrp;
+        const uint16_t *rcol = R.rcol;
+        const volatile uint16_t *vdeg = R.rdeg;
+        const volatile uint32_t *vforced = R.rforced;
+        auto rlive = [&](int x) { return x < np && !((vforced[x >> 5] >> (x & 31)) & 1u) && vdeg[x] > 0; };
+        auto rdec = [&](int x) {
+            unsigned *w = (unsigned *)((char *)R.rdeg + 2 * (x & ~1));
+            atomicSub(w, 1u << (16 * (x & 1)));
+        };
+        auto rbit = [&](uint32_t *words, int x) { atomicOr(&words[x >> 5], 1u << (x & 31)); };
+        for (int i = threadIdx.x; i < fsize; i += NT) {
+            const int v = R.rlist[i];
+            if ((vforced[v >> 5] >> (v & 31)) & 1u) continue;
+            const int dv = vdeg[v];
+            if (dv == 0 || dv > 2) continue;
+            int u = -1, w = -1;
+            const int a = rrp[v], b = rrp[v + 1];
+            for (int e0 = a; e0 < b; e0 += 8) {
+                int xs[8];
+                bool lv[8];
+#pragma unroll
+                for (int j = 0; j < 8; j++) xs[j] = e0 + j < b ? rcol[e0 + j] : kResNone;
+#pragma unroll
+                for (int j = 0; j < 8; j++) lv[j] = rlive(xs[j]);
+#pragma unroll
+                for (int j = 0; j < 8; j++)
+                    if (lv[j] && w < 0) {
+                        if (u < 0) u = xs[j]; else w = xs[j];
+                    }
+                if (dv == 1 ? u >= 0 : w >= 0) break;
+            }
+            if (dv == 1) {
+                if (u < 0) continue;
+                if (vdeg[u] == 1 && u < v) rbit(R.rflag, u);   // u's rule fires instead
+                else rbit(R.rmark, u);
+            } else if (w >= 0) {
+                // u-w an edge?  search the shorter row (sorted)
+                const bool by_u = rrp[u + 1] - rrp[u] <= rrp[w + 1] - rrp[w];
+                int lo = by_u ? rrp[u] : rrp[w], hi = (by_u ? rrp[u + 1] : rrp[w + 1]) - 1;
+                const int key = by_u ? w : u;
+                bool tri = false;
+                while (lo <= hi) {
+                    const int mid = (lo + hi) >> 1, x = rcol[mid];
+                    if (x == key) { tri = true; break; }
+                    if (x < key) lo = mid + 1; else hi = mid - 1;
+                }
+                if (tri) {
+                    int pv = INT_MAX;
+                    if (vdeg[u] == 2 && u < v) pv = u;
+                    if (vdeg[w] == 2 && w < v && w < pv) pv = w;
+                    if (pv != INT_MAX) rbit(R.rflag, pv);
+                    else { rbit(R.rmark, u); rbit(R.rmark, w); }
+                }
+            }
+        }
+        solo_sync<NT>();                                              // examined
+        if (threadIdx.x == 0) sh.cnt = 0;   // (fsize is read; the next listing follows two barriers)
+        solo_list<NT>(R.rmark, R.nw, R.rforced, true, R.rdeg, R.rlist, &sh.fcnt);
+        solo_sync<NT>();                                              // marks listed
+        const int cnt = *(volatile int *)&sh.fcnt;
+        // apply: a row by its thread, or by the whole warp when long; a
+        // forced vertex's row is applied with no test: its neighbours'
+        // degrees count it, so none goes below zero
+        for (int base = warp * 32; base < cnt; base += NT) {
+            const int i = base + lane;
+            int u = -1, a = 0, b = 0;
+            if (i < cnt) {
+                u = R.rlist[i];
+                a = rrp[u];
+                b = rrp[u + 1];
+            }
+            const bool wide = b - a > kResHeavyRow;
+            if (!wide) {
+                for (int e = a; e < b; e++) {
+                    const int x = rcol[e];
+                    if (x < np) { rdec(x); rbit(R.rflag, x); }
+                }
+            }
+            unsigned hm = __ballot_sync(kFull, wide);
+            while (hm) {
+                const int src = __ffs(hm) - 1;
+                hm &= hm - 1;
+                const int aa = __shfl_sync(kFull, a, src), bb = __shfl_sync(kFull, b, src);
+                for (int e = aa + lane; e < bb; e += 32) {
+                    const int x = rcol[e];
+                    if (x < np) { rdec(x); rbit(R.rflag, x); }
+                }
+            }
+        }
+        solo_sync<NT>();                                              // applied
+        if (threadIdx.x == 0) sh.fcnt = 0;  // (cnt is read; the next listing follows two barriers)
+        return cnt;
+    }
+
     // The unbounded rules on the residual graph (rank 0 alone), then the
     // result back to the owners.  Input: Q.rp2 / Q.col2 (the CSR, new ids),
     // Q.fr1 (degree | frontier bit << 16), Q.orig (new id -> vertex).
-    // Four barriers a round: frontier listed, examined, marks listed, applied.
     __device__ void solo_rounds(int np, int m2p)
     {
+        Solo R;
         char *p = lsm + res_off;
-        int *rrp = (int *)p;             p += a16(4 * ((size_t)np + 1));
-        uint16_t *rcol = (uint16_t *)p;  p += a16(2 * (size_t)m2p);
-        uint16_t *rdeg = (uint16_t *)p;  p += a16(2 * (size_t)np);
+        R.rrp = (int *)p;               p += a16(4 * ((size_t)np + 1));
+        R.rcol = (uint16_t *)p;         p += a16(2 * (size_t)m2p);
+        R.rdeg = (uint16_t *)p;         p += a16(2 * (size_t)np);
         const int nw = (np + 31) / 32;
-        uint32_t *rforced = (uint32_t *)p; p += a16(4 * (size_t)nw);
-        uint32_t *rmark = (uint32_t *)p;   p += a16(4 * (size_t)nw);
-        uint32_t *rflag = (uint32_t *)p;   p += a16(4 * (size_t)nw);
-        int *rlist = (int *)p;
+        R.rforced = (uint32_t *)p;      p += a16(4 * (size_t)nw);
+        R.rmark = (uint32_t *)p;        p += a16(4 * (size_t)nw);
+        R.rflag = (uint32_t *)p;        p += a16(4 * (size_t)nw);
+        R.rlist = (int *)p;
+        R.np = np;
+        R.nw = nw;
         const int T = blockDim.x, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
         // the copy in: eight independent loads in flight per thread
         for (int i0 = threadIdx.x; i0 <= np; i0 += 8 * T) {
@@ -1208,7 +1573,7 @@ struct ClusterRoot {
             for (int j = 0; j < 8; j++) xs[j] = i0 + j * T <= np ? __ldcg(Q.rp2 + i0 + j * T) : 0;
 #pragma unroll
             for (int j = 0; j < 8; j++)
-                if (i0 + j * T <= np) rrp[i0 + j * T] = xs[j];
+                if (i0 + j * T <= np) R.rrp[i0 + j * T] = xs[j];
         }
         for (int e0 = threadIdx.x; e0 < m2p; e0 += 8 * T) {
             int xs[8];
@@ -1216,117 +1581,31 @@ struct ClusterRoot {
             for (int j = 0; j < 8; j++) xs[j] = e0 + j * T < m2p ? __ldcg(Q.col2 + e0 + j * T) : 0;
 #pragma unroll
             for (int j = 0; j < 8; j++)
-                if (e0 + j * T < m2p) rcol[e0 + j * T] = (uint16_t)(xs[j] >= 0 && xs[j] < np ? xs[j] : kResNone);
+                if (e0 + j * T < m2p) R.rcol[e0 + j * T] = (uint16_t)(xs[j] >= 0 && xs[j] < np ? xs[j] : kResNone);
         }
         for (int j = warp; j < nw; j += T >> 5) {
             const int i = j * 32 + lane;
             const int x = i < np ? __ldcg(Q.fr1 + i) : 0;
-            if (i < np) rdeg[i] = (uint16_t)(x & 0xffff);
+            if (i < np) R.rdeg[i] = (uint16_t)(x & 0xffff);
             const unsigned f = __ballot_sync(kFull, (x >> 16) & 1);
-            if (lane == 0) { rflag[j] = f; rforced[j] = 0; rmark[j] = 0; }
+            if (lane == 0) { R.rflag[j] = f; R.rforced[j] = 0; R.rmark[j] = 0; }
         }
         if (threadIdx.x == 0) { sh.cnt = 0; sh.fcnt = 0; }
         __syncthreads();
-        if (threadIdx.x >= kSoloThreads) return;
-        const volatile uint16_t *vdeg = rdeg;
-        const volatile uint32_t *vforced = rforced;
-        auto rlive = [&](int x) { return x < np && !((vforced[x >> 5] >> (x & 31)) & 1u) && vdeg[x] > 0; };
-        auto rdec = [&](int x) {
-            unsigned *w = (unsigned *)((char *)rdeg + 2 * (x & ~1));
-            atomicSub(w, 1u << (16 * (x & 1)));
-        };
-        auto rbit = [&](uint32_t *words, int x) { atomicOr(&words[x >> 5], 1u << (x & 31)); };
-        // (the apply step needs no test either: see apply_row)
         int forced_cnt = 0, rounds = 0;
         for (int guard = 0; guard <= 2 * np + 2; guard++) {
-            solo_list(rflag, nw, rforced, false, rdeg, rlist, &sh.cnt);
-            solo_bar();                                                   // frontier listed
+            solo_list<kSoloThreads>(R.rflag, nw, R.rforced, false, R.rdeg, R.rlist, &sh.cnt);
+            solo_sync<kSoloThreads>();                                // frontier listed
             const int fsize = *(volatile int *)&sh.cnt;
             if (fsize == 0) break;
-            for (int i = threadIdx.x; i < fsize; i += kSoloThreads) {
-                const int v = rlist[i];
-                if ((vforced[v >> 5] >> (v & 31)) & 1u) continue;
-                const int dv = vdeg[v];
-                if (dv == 0 || dv > 2) continue;
-                int u = -1, w = -1;
-                const int a = rrp[v], b = rrp[v + 1];
-                for (int e0 = a; e0 < b; e0 += 8) {
-                    int xs[8];
-                    bool lv[8];
-#pragma unroll
-                    for (int j = 0; j < 8; j++) xs[j] = e0 + j < b ? rcol[e0 + j] : kResNone;
-#pragma unroll
-                    for (int j = 0; j < 8; j++) lv[j] = rlive(xs[j]);
-#pragma unroll
-                    for (int j = 0; j < 8; j++)
-                        if (lv[j] && w < 0) {
-                            if (u < 0) u = xs[j]; else w = xs[j];
-                        }
-                    if (dv == 1 ? u >= 0 : w >= 0) break;
-                }
-                if (dv == 1) {
-                    if (u < 0) continue;
-                    if (vdeg[u] == 1 && u < v) rbit(rflag, u);   // u's rule fires instead
-                    else rbit(rmark, u);
-                } else if (w >= 0) {
-                    // u-w an edge?  search the shorter row (sorted)
-                    const bool by_u = rrp[u + 1] - rrp[u] <= rrp[w + 1] - rrp[w];
-                    int lo = by_u ? rrp[u] : rrp[w], hi = (by_u ? rrp[u + 1] : rrp[w + 1]) - 1;
-                    const int key = by_u ? w : u;
-                    bool tri = false;
-                    while (lo <= hi) {
-                        const int mid = (lo + hi) >> 1, x = rcol[mid];
-                        if (x == key) { tri = true; break; }
-                        if (x < key) lo = mid + 1; else hi = mid - 1;
-                    }
-                    if (tri) {
-                        int pv = INT_MAX;
-                        if (vdeg[u] == 2 && u < v) pv = u;
-                        if (vdeg[w] == 2 && w < v && w < pv) pv = w;
-                        if (pv != INT_MAX) rbit(rflag, pv);
-                        else { rbit(rmark, u); rbit(rmark, w); }
-                    }
-                }
-            }
-            solo_bar();                                                   // examined
-            if (threadIdx.x == 0) sh.cnt = 0;   // (fsize is read; the next listing follows two barriers)
-            solo_list(rmark, nw, rforced, true, rdeg, rlist, &sh.fcnt);
-            solo_bar();                                                   // marks listed
-            const int cnt = *(volatile int *)&sh.fcnt;
+            forced_cnt += solo_round<kSoloThreads>(R, fsize);
             rounds++;
-            forced_cnt += cnt;
-            // apply: a row by its thread, or by the whole warp when long
-            for (int base = warp * 32; base < cnt; base += kSoloThreads) {
-                const int i = base + lane;
-                int u = -1, a = 0, b = 0;
-                if (i < cnt) {
-                    u = rlist[i];
-                    a = rrp[u];
-                    b = rrp[u + 1];
-                }
-                const bool wide = b - a > kResHeavyRow;
-                if (!wide) {
-                    for (int e = a; e < b; e++) {
-                        const int x = rcol[e];
-                        if (x < np) { rdec(x); rbit(rflag, x); }
-                    }
-                }
-                unsigned hm = __ballot_sync(kFull, wide);
-                while (hm) {
-                    const int src = __ffs(hm) - 1;
-                    hm &= hm - 1;
-                    const int aa = __shfl_sync(kFull, a, src), bb = __shfl_sync(kFull, b, src);
-                    for (int e = aa + lane; e < bb; e += 32) {
-                        const int x = rcol[e];
-                        if (x < np) { rdec(x); rbit(rflag, x); }
-                    }
-                }
-            }
-            solo_bar();                                                   // applied
-            if (threadIdx.x == 0) sh.fcnt = 0;  // (cnt is read; the next listing follows two barriers)
         }
+        __syncthreads();
         // back to the owners: degrees and the new forced bits
-        for (int i = threadIdx.x; i < np; i += kSoloThreads) {
+        const volatile uint16_t *vdeg = R.rdeg;
+        const volatile uint32_t *vforced = R.rforced;
+        for (int i = threadIdx.x; i < np; i += T) {
             const int v = __ldcg(Q.orig + i);
             const int r = v >> cs, l = v & (chunk - 1);
             ((volatile uint16_t *)degp(r))[l] = vdeg[i];
@@ -1409,32 +1688,44 @@ struct ClusterRoot {
             if (threadIdx.x == 0) Q.forced = ftot;
             lrp = nullptr;   // the residual graph overwrote rank 0's staged rows
             lcol = nullptr;
+            lsrc = nullptr;
         }
         return true;
     }
 
     // Synchronous rounds, two cluster barriers each:
-    //   B1  last round's decrements and frontier bits have landed, and its
-    //       totals (published before B1) are read: stop when it marked
-    //       nothing and left no frontier
-    //   B2  this round's marks and partner bits have landed
+    //   B1  every CTA has brought its degrees and frontier up to date with
+    //       the last round's marks, and that round's totals (published
+    //       before B1) are read: stop when it marked nothing and left no
+    //       frontier
+    //   B2  this round's marks and handed-over frontier bits have landed;
+    //       every CTA then reads all of the round's marks into its copy of
+    //       the forced bitmap and updates the degrees of its own vertices
+    //       (no remote writes after B2)
+    // Marks alternate between two bitmaps: the bitmap of round r is read by
+    // every CTA between B2 of round r and the next B1, and its owner clears
+    // it in round r + 1, before round r + 2 marks it again.
     __device__ bool reduce_rounds(bool hd, int bound)
     {
         int *fl = Q.fr0 + vbeg;        // my frontier list
-        int *ml = Q.heavy + vbeg;      // my marks of this round
-        int *hv = Q.aux + vbeg;        // heavy rows (front) / giant rows (back)
+        int *hv = Q.aux + vbeg;        // vertices whose rows are scanned by a warp
         const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+        uint32_t *lm = lmark();        // my two mark bitmaps (contiguous)
+        if (hd) refresh_forced_copy();
+        for (int i = threadIdx.x; i < chunk / 16; i += blockDim.x) lm[i] = 0;
+        for (int i = threadIdx.x; i < vcnt; i += blockDim.x) lprev()[i] = ldeg()[i];
+        int pi0 = 0, pe0 = 0, pe1 = 0;
+        if (!lsrc) pull_range(pi0, pe0, pe1);
         bool first = true, last_full = false;
         long long delta = INT_MAX;
-        for (;;) {
+        int last_all = 0;
+        for (int rnd = 0;; rnd++) {
             cl.sync();                                                    // B1
             if (!first) {
                 collect();
-                const long long tcnt = sh.tot[0], tpend = sh.tot[1];
+                const long long tpend = sh.tot[1];
                 if (last_full) delta = sh.tot[3];
-                ftot += (int)tcnt;
-                if (rank == 0 && threadIdx.x == 0) Q.forced = ftot;
-                if (tcnt == 0 && tpend == 0) return true;
+                if (last_all == 0 && tpend == 0) return true;
                 // the bound on the live graph's layout, from the last round
                 if (!hd && sh.tot[2] + kResSlack <= residual_room() && residual_solo()) return true;
             }
@@ -1443,14 +1734,14 @@ struct ClusterRoot {
             const bool full = first || (hd && delta > bud);
             first = false;
             last_full = full;
-            if (threadIdx.x == 0) { sh.hcnt = 0; sh.gcnt = 0; }
-            const int fsize = bits_to_list(flagp(rank), fl, false);       // my frontier
+            mbuf = rnd & 1;
+            for (int i = threadIdx.x; i < (chunk >> 5); i += blockDim.x) lm[(mbuf ^ 1) * (chunk >> 5) + i] = 0;
+            if (threadIdx.x == 0) { sh.hcnt = 0; sh.tcnt = 0; }
+            const int fsize = frontier_to_list(fl);                       // (ends with a block barrier)
             int dmax = 0;
             if (full) {
-                for (int i = threadIdx.x; i < vcnt; i += blockDim.x) {
-                    const int v = vbeg + i;
-                    if (!forced(v)) dmax = max(dmax, d(v));
-                }
+                for (int i = threadIdx.x; i < vcnt; i += blockDim.x)
+                    if (!rforced(vbeg + i)) dmax = max(dmax, (int)ldeg()[i]);
                 for (int i = threadIdx.x; i < vcnt; i += blockDim.x) examine(hv, vbeg + i, bud);
             } else {
                 for (int i = threadIdx.x; i < fsize; i += blockDim.x) examine(hv, fl[i], bud);
@@ -1459,53 +1750,59 @@ struct ClusterRoot {
             const int hc = sh.hcnt;
             for (int i = warp; i < hc; i += nwarps) {
                 const int v = hv[i];
-                const int dv = d(v);
+                const int dv = ldeg()[v - vbeg];
                 int u, w;
                 warp_live_nbrs(v, dv, u, w);
-                if (lane == 0) decide(v, dv, u, w);
-            }
-            const int dm = full ? block_max(dmax, sh.red) : 0;
-            cl.sync();                                                    // B2
-            // this round's marks that I own: list them, fold them into forced
-            const int cnt = bits_to_list(markp(rank), ml, true);
-            int pend = 0, est = 0;
-            {
-                const uint32_t *fw = flagp(rank);
-                for (int i = threadIdx.x; i < chunk / 32; i += blockDim.x) pend += __popc(fw[i]);
-                pend = block_sum(pend, sh.red);
-                // the live graph only shrinks from here: its vertices and
-                // degrees now bound the residual layout at the next round
-                if (!hd) {
-                    for (int i = threadIdx.x; i < vcnt; i += blockDim.x) {
-                        const int v = vbeg + i;
-                        if (live(v)) est += kResPerVertex + 2 * d(v);
-                    }
-                    est = block_sum(est, sh.red);
+                if (lane == 0) {
+                    if (dv == 1) { if (u >= 0) decide_one(v, u); }
+                    else if (w >= 0) list_triangle(v, u, w);
                 }
             }
-            publish(cnt, pend, hd ? kResNever : min(est, kResNever), dm);   // read by every CTA after the next B1
-            if (rank == 0 && threadIdx.x == 0) Q.rounds++;
-            if (cnt == 0) continue;
-            // (the forced set is the forced bitmap here; Q.forced gets its
-            // size when the rounds end)
-            if (threadIdx.x == 0) { sh.hcnt = 0; sh.gcnt = 0; }
             __syncthreads();
-            // apply: short rows by one thread, long by a warp, giant by the block
-            for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
-                const int u = ml[i];
-                int a, b;
-                const int *cp;
-                own_row(u, a, b, cp);
-                const int len = b - a;
-                if (len > kGiantRow) hv[vcnt - 1 - atomicAdd(&sh.gcnt, 1)] = u;
-                else if (len > kHeavyRow) hv[atomicAdd(&sh.hcnt, 1)] = u;
-                else apply_row(u, 0, 1);
+            // the triangle checks of the round, spread evenly over the block
+            const int tc = sh.tcnt;
+            for (int i = threadIdx.x; i < tc; i += blockDim.x)
+                decide_triangle(Q.deg[vbeg + i], Q.heavy[vbeg + i], Q.flag[vbeg + i]);
+            const int dm = full ? block_max(dmax, sh.red) : 0;
+            cl.sync();                                                    // B2
+            const int all = gather_marks();                               // (ends with a block barrier)
+            ftot += all;
+            last_all = all;
+            if (rank == 0 && threadIdx.x == 0) { Q.forced = ftot; Q.rounds++; }
+            if (all > 0) {
+                if (lsrc) pull_flat();
+                else pull_walk(pi0, pe0, pe1);
             }
+            int pend = 0, est = 0;
             __syncthreads();
-            const int hc2 = sh.hcnt, gc = sh.gcnt;
-            for (int i = warp; i < hc2; i += nwarps) apply_row(hv[i], lane, 32);
-            for (int i = 0; i < gc; i++) apply_row(hv[vcnt - 1 - i], threadIdx.x, blockDim.x);
-            __syncthreads();
+            // The next frontier: the live vertices whose degree changed to 1
+            // or 2, added to the bits other CTAs handed over (a warp takes
+            // 32 consecutive vertices, one frontier word).  The live graph
+            // only shrinks from here: its vertices and degrees bound the
+            // residual layout at the next round.
+            {
+                const uint32_t *fw = lrep() + (rank << (cs - 5));
+                uint16_t *pv = lprev();
+                for (int w = warp; w < (chunk >> 5); w += nwarps) {
+                    const int i = w * 32 + lane;
+                    int dv = 0;
+                    bool fr = false;
+                    if (i < vcnt && !((fw[w] >> lane) & 1u)) {
+                        dv = ldeg()[i];
+                        fr = dv != pv[i] && (dv == 1 || dv == 2);
+                        pv[i] = (uint16_t)dv;
+                        if (!hd && dv > 0) est += kResPerVertex + 2 * dv;
+                    }
+                    const unsigned f = __ballot_sync(kFull, fr);
+                    if (lane == 0) {
+                        const uint32_t x = lflag()[w] | f;
+                        lflag()[w] = x;
+                        pend += __popc(x);
+                    }
+                }
+            }
+            block_sum2(pend, est, sh.red, sh.red2);
+            publish(0, pend, hd ? kResNever : min(est, kResNever), dm);   // read by every CTA after the next B1
         }
     }
 
@@ -2201,7 +2498,8 @@ int root_cluster_shift(int nq, int max_n, int max_deg)
     if (nq != 1 || max_n < kClusterMinN || max_deg > 65535) return -1;
     int cs = 10;
     while (((long long)kClusterMax << cs) < max_n) cs++;
-    if (cluster_smem_bytes(1 << cs) > kRootSmemMax || (1 << cs) > 4 * 32 * kRootThreads) return -1;
+    const int C = (int)((max_n + (1 << cs) - 1) >> cs);
+    if (cluster_smem_bytes(1 << cs, C) > kRootSmemMax || (1 << cs) > 4 * 32 * kRootThreads) return -1;
     return cs;
 }
 
@@ -2211,6 +2509,7 @@ int root_cluster_shift(int nq, int max_n, int max_deg)
 struct ClusterMemo {
     std::mutex mu;
     std::set<int> attrs_set;
+    std::map<int, int> smem;                     // device -> dynamic shared memory per CTA
     std::map<std::pair<int, int>, int> shift;   // (device, max_n) -> cluster shift, -1: none fits
 };
 static ClusterMemo &cluster_memo()
@@ -2225,6 +2524,7 @@ cudaError_t root_run(QueryDesc *d_q, int nq, int max_n, int max_deg, cudaStream_
     int cs = root_cluster_shift(nq, max_n, max_deg);
     int dev = 0;
     bool memo_hit = false;
+    size_t cluster_dyn = kRootSmemMax;
     if (cs >= 0) {
         cudaError_t e = cudaGetDevice(&dev);
         if (e != cudaSuccess) return e;
@@ -2233,11 +2533,21 @@ cudaError_t root_run(QueryDesc *d_q, int nq, int max_n, int max_deg, cudaStream_
         if (!M.attrs_set.count(dev)) {
             e = cudaFuncSetAttribute(root_cluster_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
             if (e != cudaSuccess) return e;
-            e = cudaFuncSetAttribute(root_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)kRootSmemMax);
+            // all the shared memory a block may have (one CTA per SM): the
+            // rows, their source index and rank 0's residual graph use it
+            int optin = 0;
+            cudaFuncAttributes fa;
+            e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
             if (e != cudaSuccess) return e;
+            e = cudaFuncGetAttributes(&fa, root_cluster_kernel);
+            if (e != cudaSuccess) return e;
+            const int dyn = std::max((int)kRootSmemMax, optin - (int)fa.sharedSizeBytes) & ~15;
+            e = cudaFuncSetAttribute(root_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
+            if (e != cudaSuccess) return e;
+            M.smem[dev] = dyn;
             M.attrs_set.insert(dev);
         }
+        cluster_dyn = M.smem[dev];
         auto it = M.shift.find({dev, max_n});
         if (it != M.shift.end()) {
             cs = it->second;
@@ -2251,7 +2561,7 @@ cudaError_t root_run(QueryDesc *d_q, int nq, int max_n, int max_deg, cudaStream_
             cudaLaunchConfig_t probe = {};
             probe.gridDim = dim3(C, 1, 1);
             probe.blockDim = dim3(kRootThreads, 1, 1);
-            probe.dynamicSmemBytes = kRootSmemMax;   // (the rows are staged in what is left)
+            probe.dynamicSmemBytes = cluster_dyn;   // (the rows are staged in what is left)
             cudaLaunchAttribute pa[1];
             pa[0].id = cudaLaunchAttributeClusterDimension;
             pa[0].val.clusterDim.x = C;
@@ -2263,7 +2573,8 @@ cudaError_t root_run(QueryDesc *d_q, int nq, int max_n, int max_deg, cudaStream_
             if (cudaOccupancyMaxActiveClusters(&clusters, root_cluster_kernel, &probe) == cudaSuccess && clusters > 0)
                 break;
             cudaGetLastError();
-            if (C <= 1 || cluster_smem_bytes(2 << cs) > kRootSmemMax || (2 << cs) > 4 * 32 * kRootThreads) {
+            const int C2 = (int)((max_n + (2 << cs) - 1) >> (cs + 1));
+            if (C <= 1 || cluster_smem_bytes(2 << cs, C2) > kRootSmemMax || (2 << cs) > 4 * 32 * kRootThreads) {
                 cs = -1;
                 break;
             }
@@ -2277,7 +2588,7 @@ cudaError_t root_run(QueryDesc *d_q, int nq, int max_n, int max_deg, cudaStream_
     }
     if (cs >= 0) {
         const int C = (int)((max_n + (1 << cs) - 1) >> cs);
-        const size_t smem = kRootSmemMax;   // one CTA per SM in any case: room for staged rows
+        const size_t smem = cluster_dyn;   // one CTA per SM in any case: room for staged rows
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3(C, 1, 1);
         cfg.blockDim = dim3(kRootThreads, 1, 1);
