@@ -4,6 +4,7 @@ from __future__ import annotations
 
 import ctypes
 import os
+import struct
 import threading
 
 HERE = os.path.dirname(os.path.abspath(__file__))
@@ -90,16 +91,47 @@ class Stats(ctypes.Structure):
     ]
 
     def to_dict(self) -> dict:
-        d = {name: getattr(self, name) for name in _STATS_SCALARS}
-        h = self.comp_hist
-        d["comp_hist"] = {i + 2: int(h[i]) for i in range(16) if h[i]}
-        d["root_cycles"] = list(self.root_cycles)
-        pc = self.phase_cycles
-        d["phase_cycles"] = {PHASES[i]: int(pc[i]) for i in range(6)}
+        # one unpack of the whole struct (a getattr per field costs more than
+        # the rest of a small solve's host time)
+        vals = _STATS_STRUCT.unpack_from(self)
+        d = {}
+        i = 0
+        for name, ln in _STATS_LAYOUT:
+            if ln:
+                d[name] = vals[i:i + ln]
+                i += ln
+            else:
+                d[name] = vals[i]
+                i += 1
+        h = d["comp_hist"]
+        d["comp_hist"] = {k + 2: h[k] for k in range(16) if h[k]}
+        d["root_cycles"] = list(d["root_cycles"])
+        d["phase_cycles"] = dict(zip(PHASES, d["phase_cycles"]))
         return d
 
 
-_STATS_SCALARS = [name for name, _ in Stats._fields_ if name not in ("comp_hist", "root_cycles", "phase_cycles")]
+def _struct_of(cls):
+    """A struct.Struct reading a ctypes Structure of int32 / int64 / double
+    fields and arrays of them, and the (name, array length or 0) layout."""
+    codes = {ctypes.c_int64: "q", ctypes.c_int32: "i", ctypes.c_double: "d"}
+    fmt, layout, pos = "=", [], 0
+    for name, ct in cls._fields_:
+        off = getattr(cls, name).offset
+        if off > pos:
+            fmt += f"{off - pos}x"
+        if issubclass(ct, ctypes.Array):
+            fmt += codes[ct._type_] * ct._length_
+            layout.append((name, ct._length_))
+        else:
+            fmt += codes[ct]
+            layout.append((name, 0))
+        pos = off + ctypes.sizeof(ct)
+    if ctypes.sizeof(cls) > pos:
+        fmt += f"{ctypes.sizeof(cls) - pos}x"
+    return struct.Struct(fmt), layout
+
+
+_STATS_STRUCT, _STATS_LAYOUT = _struct_of(Stats)
 
 
 class ServerConfig(ctypes.Structure):

@@ -907,8 +907,25 @@ struct ClusterRoot {
         const long long need = 4ll * (chunk + 1) + 4ll * E;
         if (vcnt > 0 && (long long)off + need <= (long long)smem_bytes) {
             int *r = (int *)(smem + off), *c = r + chunk + 1;
-            for (int i = threadIdx.x; i <= vcnt; i += blockDim.x) r[i] = __ldg(rp + vbeg + i) - e0;
-            for (int e = threadIdx.x; e < E; e += blockDim.x) c[e] = __ldg(col + e0 + e);
+            // eight independent loads in flight per thread (the CSR comes
+            // from DRAM on a cold L2)
+            const int T = blockDim.x;
+            for (int i0 = threadIdx.x; i0 <= vcnt; i0 += 8 * T) {
+                int xs[8];
+#pragma unroll
+                for (int j = 0; j < 8; j++) xs[j] = i0 + j * T <= vcnt ? __ldg(rp + vbeg + i0 + j * T) : 0;
+#pragma unroll
+                for (int j = 0; j < 8; j++)
+                    if (i0 + j * T <= vcnt) r[i0 + j * T] = xs[j] - e0;
+            }
+            for (int f0 = threadIdx.x; f0 < E; f0 += 8 * T) {
+                int xs[8];
+#pragma unroll
+                for (int j = 0; j < 8; j++) xs[j] = f0 + j * T < E ? __ldg(col + e0 + f0 + j * T) : 0;
+#pragma unroll
+                for (int j = 0; j < 8; j++)
+                    if (f0 + j * T < E) c[f0 + j * T] = xs[j];
+            }
             lrp = r;
             lcol = c;
             const size_t soff = (off + (size_t)need + 15) & ~(size_t)15;
@@ -1388,6 +1405,7 @@ struct ClusterRoot {
     static constexpr int kResSlack = 128;
     static constexpr int kResNever = 1 << 26;   // a per-CTA bound that never fits
     static constexpr int kResNone = 0xffff;     // no vertex (ids are below it); sorts last
+    static constexpr int kResWarpScan = 32;     // longer original rows are compacted by a warp at the hand-off
 
     __device__ static size_t a16(size_t x) { return (x + 15) & ~(size_t)15; }
     // rank 0's layout: row offsets (int), row entries (u16), degrees (u16),
@@ -1624,12 +1642,26 @@ struct ClusterRoot {
     // graph did not fit after all (nothing changed).
     __device__ bool residual_solo()
     {
-        const int T = blockDim.x;
+        const int T = blockDim.x, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+        const int wpr = chunk >> 5, nwa = C * wpr;
+        const uint32_t *fw = lrep() + (rank << (cs - 5));
+        // My live vertices as a bitmap, in my part of lnew() (the round's
+        // degree update is done with it); the other CTAs read it after the
+        // cluster barrier of the prefix exchange.
+        uint32_t *lv = lnew();
+        for (int w = warp; w < wpr; w += T >> 5) {
+            const int i = w * 32 + lane;
+            const bool l = i < vcnt && !((fw[w] >> lane) & 1u) && ldeg()[i] > 0;
+            const unsigned b = __ballot_sync(kFull, l);
+            if (lane == 0) lv[rank * wpr + w] = b;
+        }
         const int per = (vcnt + T - 1) / T;
-        const int beg = vbeg + min(vcnt, (int)threadIdx.x * per), end = vbeg + min(vcnt, ((int)threadIdx.x + 1) * per);
+        const int beg = min(vcnt, (int)threadIdx.x * per), end = min(vcnt, ((int)threadIdx.x + 1) * per);
         int cnt = 0, dsum = 0;
-        for (int v = beg; v < end; v++)
-            if (live(v)) { cnt++; dsum += d(v); }
+        for (int i = beg; i < end; i++) {
+            const int dv = ldeg()[i];
+            if (dv > 0 && !((fw[i >> 5] >> (i & 31)) & 1u)) { cnt++; dsum += dv; }
+        }
         int lnp, lm2;
         const int loff = block_excl_scan(cnt, sh.red, &lnp);
         const int leoff = block_excl_scan(dsum, sh.red, &lm2);
@@ -1637,49 +1669,103 @@ struct ClusterRoot {
         exchange_prefix(lnp, lm2, coff, np, ceoff, m2p);
         if (np == 0 || np >= kResNone || residual_bytes(np, m2p) > (size_t)residual_room())
             return false;
-        // new ids in increasing vertex order; degree and frontier bit travel in Q.fr1
-        int *nid = Q.aux;
-        const uint32_t *fw = flagp(rank);
-        int id = coff + loff, eo = ceoff + leoff;
-        for (int v = beg; v < end; v++) {
-            if (live(v)) {
-                const int l = v - vbeg;
-                const int f = (int)((fw[l >> 5] >> (l & 31)) & 1u);
-                nid[v] = id;
-                Q.orig[id] = v;
-                Q.rp2[id] = eo;
-                Q.fr1[id] = d(v) | (f << 16);
-                id++;
-                eo += d(v);
-            } else {
-                nid[v] = -1;
+        // The whole live bitmap in every CTA, and the live vertices before
+        // each word (in lprev(), whose degrees no later round needs): a live
+        // vertex x gets the new id pref[x / 32] + (live vertices of its word
+        // below it), the same id its owner gives it below.
+        for (int w = threadIdx.x; w < nwa; w += T) {
+            const int r = w / wpr;
+            if (r != rank) lv[w] = ((volatile uint32_t *)(base(r) + 2 * (size_t)chunk + repb))[w];
+        }
+        __syncthreads();
+        int *pref = (int *)lprev();
+        {
+            const int k = (nwa + T - 1) / T;
+            const int w0 = min(nwa, (int)threadIdx.x * k), w1 = min(nwa, ((int)threadIdx.x + 1) * k);
+            int c = 0;
+            for (int w = w0; w < w1; w++) c += __popc(lv[w]);
+            int tot;
+            int o = block_excl_scan(c, sh.red, &tot);
+            for (int w = w0; w < w1; w++) {
+                pref[w] = o;
+                o += __popc(lv[w]);
             }
         }
         __syncthreads();
-        for (int i = threadIdx.x; i < (chunk >> 5); i += T) flagp(rank)[i] = 0;   // carried in Q.fr1 now
-        if (rank == 0 && threadIdx.x == 0) Q.rp2[np] = m2p;
-        cl.sync();
-        // rows: the live neighbours, renumbered (a live vertex's degree is
-        // its number of live neighbours)
-        for (int i = coff + threadIdx.x; i < coff + lnp; i += T) {
-            const int v = Q.orig[i];
-            int o = Q.rp2[i];
-            const int lim = o + d(v);
+        // New ids in increasing vertex order (thread ranges are in order);
+        // degree and frontier bit travel in Q.fr1.  Each live vertex's row
+        // is its live neighbours, renumbered, in the order of the original
+        // row (its degree counts them, so the row is full when that many
+        // are found): written here, or, for an original row longer than
+        // kResWarpScan, listed (Q.deg / Q.heavy / Q.flag: vertex, offset,
+        // degree) and written by a warp below.
+        const uint32_t *flw = lflag();
+        if (threadIdx.x == 0) sh.tcnt = 0;
+        __syncthreads();
+        int id = coff + loff, eo = ceoff + leoff;
+        for (int i = beg; i < end; i++) {
+            const int dv = ldeg()[i];
+            if (dv == 0 || ((fw[i >> 5] >> (i & 31)) & 1u)) continue;
+            const int v = vbeg + i;
+            Q.orig[id] = v;
+            Q.rp2[id] = eo;
+            Q.fr1[id] = dv | (int)(((flw[i >> 5] >> (i & 31)) & 1u) << 16);
+            id++;
             int a, b;
             const int *cp;
             own_row(v, a, b, cp);
+            int o = eo;
+            const int lim = eo + dv;
+            if (b - a > kResWarpScan) {
+                const int k = vbeg + atomicAdd(&sh.tcnt, 1);
+                Q.deg[k] = v;
+                Q.heavy[k] = eo;
+                Q.flag[k] = dv;
+                eo = lim;
+                continue;
+            }
             for (int e0 = a; e0 < b && o < lim; e0 += 8) {
                 int xs[8];
 #pragma unroll
                 for (int j = 0; j < 8; j++) xs[j] = e0 + j < b ? cp[e0 + j] : -1;
 #pragma unroll
-                for (int j = 0; j < 8; j++) xs[j] = xs[j] >= 0 ? __ldcg(nid + xs[j]) : -1;
-#pragma unroll
-                for (int j = 0; j < 8; j++)
-                    if (xs[j] >= 0 && o < lim) Q.col2[o++] = xs[j];
+                for (int j = 0; j < 8; j++) {
+                    const int x = xs[j];
+                    if (x < 0 || o >= lim) continue;
+                    const uint32_t word = lv[x >> 5], bit = 1u << (x & 31);
+                    if (word & bit) Q.col2[o++] = pref[x >> 5] + __popc(word & (bit - 1));
+                }
             }
             while (o < lim) Q.col2[o++] = -1;   // (never: the degree counts the live neighbours)
+            eo = lim;
         }
+        __syncthreads();
+        const int nlong = sh.tcnt;
+        for (int k = warp; k < nlong; k += T >> 5) {
+            const int v = Q.deg[vbeg + k];
+            int o = Q.heavy[vbeg + k];
+            const int lim = o + Q.flag[vbeg + k];
+            int a, b;
+            const int *cp;
+            own_row(v, a, b, cp);
+            for (int e0 = a; e0 < b && o < lim; e0 += 32) {           // (o is the same in every lane)
+                const int e = e0 + lane;
+                const int x = e < b ? cp[e] : -1;
+                uint32_t word = 0, bit = 0;
+                if (x >= 0) {
+                    word = lv[x >> 5];
+                    bit = 1u << (x & 31);
+                }
+                const bool l = (word & bit) != 0;
+                const unsigned m = __ballot_sync(kFull, l);
+                const int at = o + __popc(m & ((1u << lane) - 1u));
+                if (l && at < lim) Q.col2[at] = pref[x >> 5] + __popc(word & (bit - 1));
+                o += __popc(m);
+            }
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < wpr; i += T) lflag()[i] = 0;   // carried in Q.fr1 now
+        if (rank == 0 && threadIdx.x == 0) Q.rp2[np] = m2p;
         cl.sync();
         if (rank == 0) solo_rounds(np, m2p);
         cl.sync();   // the owners' degrees and forced bits are final
@@ -1941,7 +2027,10 @@ struct ClusterRoot {
     // (cover_list, and cover_out when set) here instead of in a separate
     // finalisation launch.  Each thread takes four consecutive words of this
     // CTA's forced bitmap, so thread order is id order; CTAs are ordered by
-    // rank.  One cluster barrier.  Called by every thread of every CTA.
+    // rank.  The ids are gathered in shared memory first (the staged rows
+    // are not needed any more), so that consecutive threads store
+    // consecutive entries.  One cluster barrier.  Called by every thread of
+    // every CTA.
     __device__ void list_forced()
     {
         const volatile uint32_t *fw = forcedp(rank);
@@ -1956,20 +2045,41 @@ struct ClusterRoot {
         }
         int mine;
         int off = block_excl_scan(c, sh.red, &mine);
-        int cta_off, all, o2, t2;
-        exchange_prefix(mine, 0, cta_off, all, o2, t2);
-        off += cta_off;
         int *list = Q.cover_list, *out = Q.cover_out;
+        const bool staged = (size_t)smem_cap >= (size_t)res_off + 4 * (size_t)chunk;   // (uniform)
+        int *stage = (int *)(lsm + res_off);
+        if (staged) {
 #pragma unroll
-        for (int j = 0; j < 4; j++) {
-            uint32_t x = m[j];
-            const int v0 = vbeg + (threadIdx.x * 4 + j) * 32;
-            while (x) {
-                const int v = v0 + __ffs(x) - 1;
-                list[off] = v;
-                if (out) out[off] = v;
-                off++;
-                x &= x - 1;
+            for (int j = 0; j < 4; j++) {
+                uint32_t x = m[j];
+                const int v0 = vbeg + (threadIdx.x * 4 + j) * 32;
+                while (x) {
+                    stage[off++] = v0 + __ffs(x) - 1;
+                    x &= x - 1;
+                }
+            }
+        }
+        int cta_off, all, o2, t2;
+        exchange_prefix(mine, 0, cta_off, all, o2, t2);   // (its block barriers order the staging)
+        if (staged) {
+            for (int k = threadIdx.x; k < mine; k += blockDim.x) {
+                const int v = stage[k];
+                list[cta_off + k] = v;
+                if (out) out[cta_off + k] = v;
+            }
+        } else {
+            off += cta_off;
+#pragma unroll
+            for (int j = 0; j < 4; j++) {
+                uint32_t x = m[j];
+                const int v0 = vbeg + (threadIdx.x * 4 + j) * 32;
+                while (x) {
+                    const int v = v0 + __ffs(x) - 1;
+                    list[off] = v;
+                    if (out) out[off] = v;
+                    off++;
+                    x &= x - 1;
+                }
             }
         }
         if (rank == 0 && threadIdx.x == 0) {
@@ -1986,7 +2096,7 @@ struct ClusterRoot {
         }
         for (int i = threadIdx.x; i < vcnt; i += blockDim.x) {
             const int v = vbeg + i;
-            degp(rank)[i] = (uint16_t)(__ldg(rp + v + 1) - __ldg(rp + v));
+            ldeg()[i] = (uint16_t)(lcol ? lrp[i + 1] - lrp[i] : __ldg(rp + v + 1) - __ldg(rp + v));
             Q.aux[v] = 0;
             Q.cover_flags[v] = 0;
         }
