@@ -1405,7 +1405,7 @@ struct ClusterRoot {
     static constexpr int kResSlack = 128;
     static constexpr int kResNever = 1 << 26;   // a per-CTA bound that never fits
     static constexpr int kResNone = 0xffff;     // no vertex (ids are below it); sorts last
-    static constexpr int kResWarpScan = 32;     // longer original rows are compacted by a warp at the hand-off
+    static constexpr int kResWarpScan = 8;      // longer original rows are compacted by a warp at the hand-off
 
     __device__ static size_t a16(size_t x) { return (x + 15) & ~(size_t)15; }
     // rank 0's layout: row offsets (int), row entries (u16), degrees (u16),
@@ -1566,9 +1566,9 @@ struct ClusterRoot {
         return cnt;
     }
 
-    // The unbounded rules on the residual graph (rank 0 alone), then the
-    // result back to the owners.  Input: Q.rp2 / Q.col2 (the CSR, new ids),
-    // Q.fr1 (degree | frontier bit << 16), Q.orig (new id -> vertex).
+    // The unbounded rules on the residual graph (rank 0 alone); the owners
+    // read the results from rank 0's shared memory afterwards.  Input: Q.rp2
+    // / Q.col2 (the CSR, new ids), Q.fr1 (degree | frontier bit << 16).
     __device__ void solo_rounds(int np, int m2p)
     {
         Solo R;
@@ -1620,15 +1620,6 @@ struct ClusterRoot {
             rounds++;
         }
         __syncthreads();
-        // back to the owners: degrees and the new forced bits
-        const volatile uint16_t *vdeg = R.rdeg;
-        const volatile uint32_t *vforced = R.rforced;
-        for (int i = threadIdx.x; i < np; i += T) {
-            const int v = __ldcg(Q.orig + i);
-            const int r = v >> cs, l = v & (chunk - 1);
-            ((volatile uint16_t *)degp(r))[l] = vdeg[i];
-            if ((vforced[i >> 5] >> (i & 31)) & 1u) atomicOr(&forcedp(r)[l >> 5], 1u << (l & 31));
-        }
         if (threadIdx.x == 0) {
             sh.solo_forced = forced_cnt;
             Q.rounds += rounds;
@@ -1707,7 +1698,6 @@ struct ClusterRoot {
             const int dv = ldeg()[i];
             if (dv == 0 || ((fw[i >> 5] >> (i & 31)) & 1u)) continue;
             const int v = vbeg + i;
-            Q.orig[id] = v;
             Q.rp2[id] = eo;
             Q.fr1[id] = dv | (int)(((flw[i >> 5] >> (i & 31)) & 1u) << 16);
             id++;
@@ -1768,7 +1758,30 @@ struct ClusterRoot {
         if (rank == 0 && threadIdx.x == 0) Q.rp2[np] = m2p;
         cl.sync();
         if (rank == 0) solo_rounds(np, m2p);
-        cl.sync();   // the owners' degrees and forced bits are final
+        cl.sync();   // the residual graph's degrees and forced bits are final
+        // My vertices that were live at the hand-off take their degree and
+        // forced bit from rank 0's residual layout (new id from the live
+        // bitmap and the prefix counts, which are unchanged); a warp takes
+        // one word of my vertices.  The next cluster barrier (the caller's)
+        // orders these for the other CTAs.
+        {
+            const char *q0 = base(0) + res_off + a16(4 * ((size_t)np + 1)) + a16(2 * (size_t)m2p);
+            const volatile uint16_t *rdeg0 = (const volatile uint16_t *)q0;
+            const volatile uint32_t *rforced0 = (const volatile uint32_t *)(q0 + a16(2 * (size_t)np));
+            uint32_t *own = lrep() + (rank << (cs - 5));
+            for (int w = warp; w < wpr; w += T >> 5) {
+                const int gw = rank * wpr + w;
+                const uint32_t word = lv[gw];
+                bool f = false;
+                if ((word >> lane) & 1u) {
+                    const int nid = pref[gw] + __popc(word & ((1u << lane) - 1u));
+                    ldeg()[w * 32 + lane] = rdeg0[nid];
+                    f = (rforced0[nid >> 5] >> (nid & 31)) & 1u;
+                }
+                const unsigned fm = __ballot_sync(kFull, f);
+                if (lane == 0 && fm) own[w] |= fm;
+            }
+        }
         ftot += *(volatile int *)&shp(0)->solo_forced;
         if (rank == 0) {
             if (threadIdx.x == 0) Q.forced = ftot;
