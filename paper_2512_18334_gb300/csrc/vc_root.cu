@@ -1601,12 +1601,24 @@ struct ClusterRoot {
             for (int j = 0; j < 8; j++)
                 if (e0 + j * T < m2p) R.rcol[e0 + j * T] = (uint16_t)(xs[j] >= 0 && xs[j] < np ? xs[j] : kResNone);
         }
-        for (int j = warp; j < nw; j += T >> 5) {
-            const int i = j * 32 + lane;
-            const int x = i < np ? __ldcg(Q.fr1 + i) : 0;
-            if (i < np) R.rdeg[i] = (uint16_t)(x & 0xffff);
-            const unsigned f = __ballot_sync(kFull, (x >> 16) & 1);
-            if (lane == 0) { R.rflag[j] = f; R.rforced[j] = 0; R.rmark[j] = 0; }
+        // degrees and frontier bits: four words per warp in flight
+        const int nwarps = T >> 5;
+        for (int j0 = warp; j0 < nw; j0 += 4 * nwarps) {
+            int xs[4];
+#pragma unroll
+            for (int k = 0; k < 4; k++) {
+                const int i = (j0 + k * nwarps) * 32 + lane;
+                xs[k] = i < np ? __ldcg(Q.fr1 + i) : 0;
+            }
+#pragma unroll
+            for (int k = 0; k < 4; k++) {
+                const int j = j0 + k * nwarps;
+                if (j >= nw) break;   // (uniform over the warp)
+                const int i = j * 32 + lane;
+                if (i < np) R.rdeg[i] = (uint16_t)(xs[k] & 0xffff);
+                const unsigned f = __ballot_sync(kFull, (xs[k] >> 16) & 1);
+                if (lane == 0) { R.rflag[j] = f; R.rforced[j] = 0; R.rmark[j] = 0; }
+            }
         }
         if (threadIdx.x == 0) { sh.cnt = 0; sh.fcnt = 0; }
         __syncthreads();
@@ -2031,9 +2043,15 @@ struct ClusterRoot {
         cl.sync();
     }
 
+    // forced bit of owned vertex i, through the local window
+    __device__ __forceinline__ bool own_forced(int i) const
+    {
+        return ((const volatile uint32_t *)lrep())[(rank << (cs - 5)) + (i >> 5)] >> (i & 31) & 1u;
+    }
+
     __device__ void publish()
     {
-        for (int i = threadIdx.x; i < vcnt; i += blockDim.x) Q.st[vbeg + i] = forced(vbeg + i) ? 1 : 0;
+        for (int i = threadIdx.x; i < vcnt; i += blockDim.x) Q.st[vbeg + i] = own_forced(i) ? 1 : 0;
     }
 
     // The answer is the forced set: write it as the ascending output list
@@ -2046,7 +2064,7 @@ struct ClusterRoot {
     // every CTA.
     __device__ void list_forced()
     {
-        const volatile uint32_t *fw = forcedp(rank);
+        const volatile uint32_t *fw = lrep() + (rank << (cs - 5));
         const int nw = chunk >> 5;
         uint32_t m[4];
         int c = 0;
@@ -2128,7 +2146,7 @@ struct ClusterRoot {
         if (rank == 0 && threadIdx.x == 0) Q.root_cycles[0] = t1 - t0;
         if (live_edges2() == 0) {
             publish();
-            for (int i = threadIdx.x; i < vcnt; i += blockDim.x) Q.cover_flags[vbeg + i] = forced(vbeg + i);
+            for (int i = threadIdx.x; i < vcnt; i += blockDim.x) Q.cover_flags[vbeg + i] = own_forced(i);
             if (rank == 0 && threadIdx.x == 0) {
                 Q.answered = 1;
                 Q.bound = ftot;
@@ -2163,7 +2181,7 @@ struct ClusterRoot {
             return;
         }
         if (e2 == 0) {
-            for (int i = threadIdx.x; i < vcnt; i += blockDim.x) Q.cover_flags[vbeg + i] = forced(vbeg + i);
+            for (int i = threadIdx.x; i < vcnt; i += blockDim.x) Q.cover_flags[vbeg + i] = own_forced(i);
             if (rank == 0 && threadIdx.x == 0) {
                 Q.answered = 1; Q.bound = bound; Q.result = ftot; Q.yes = 1;
             }
