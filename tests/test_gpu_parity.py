@@ -178,6 +178,33 @@ def test_residual_rounds_on_one_cta(vc):
         dg.close()
 
 
+def test_cluster_rows_too_many_to_stage(vc):
+    # 9,048 vertices, 1,024 per CTA.  The first CTA's vertices are nine
+    # copies of K(56, 56): about 56k row entries, more than its shared memory
+    # holds, so it reads its rows from the global CSR.  The second CTA's are
+    # twelve copies of K(40, 40): about 38k entries, staged, but with no room
+    # for the per-entry source index, so its degree updates walk the rows.
+    # The rest is a forest and two paths for the rule rounds to peel.
+    # A minimum cover of K(a, a) has a vertices.
+    forest = gg.random_forest(7000, 60, 13)
+    parts = ([gg.complete_bipartite(56, 56) for _ in range(9)] + [gg.path(16)] +
+             [gg.complete_bipartite(40, 40) for _ in range(12)] + [gg.path(64)] + [forest])
+    g = gg.disjoint_union(parts)
+    assert g.n == 9048
+    want = 9 * 56 + 8 + 12 * 40 + 32 + oracle.mvc(forest.n, forest.row_ptr, forest.col)[0]
+    for _ in range(2):
+        size, st = gpu_min(vc, g)
+        assert size == want
+    dg = vc.Graph.from_csr(g.row_ptr, g.col)
+    try:
+        yes, cover, _ = vc.solve_k(dg, want)
+        assert yes and len(cover) <= want
+        check_cover(g, cover, len(cover))
+        assert not vc.solve_k(dg, want - 1)[0]
+    finally:
+        dg.close()
+
+
 def test_chung_lu_50k_decision_and_independent_set(vc):
     # the cluster root phase settles this graph and writes the cover list
     # itself; the decision form and the complement go through finalisation
