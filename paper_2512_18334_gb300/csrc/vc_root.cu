@@ -37,16 +37,87 @@ __device__ __forceinline__ bool bsearch_row(const int *row, int len, int key)
     return false;
 }
 
+// Is key in the sorted global row[0, len)?  Eight probes at a time: each
+// step loads eight evenly spaced entries together (one round trip) and
+// keeps the gap that can hold key, so a 2,000-entry row takes three steps
+// and a short scan instead of eleven dependent loads.
+__device__ bool kary_find(const int *row, int len, int key)
+{
+    int lo = 0, hi = len;                      // key can only be in [lo, hi)
+    while (hi - lo > 16) {
+        const int step = (hi - lo) / 9;        // >= 1
+        int xs[8];
+#pragma unroll
+        for (int j = 0; j < 8; j++) xs[j] = __ldg(row + lo + (j + 1) * step);
+        int below = 0;
+        bool hit = false;
+#pragma unroll
+        for (int j = 0; j < 8; j++) {
+            below += xs[j] < key;
+            hit |= xs[j] == key;
+        }
+        if (hit) return true;
+        // the first `below` probes are < key, the rest > key
+        const int nlo = below == 0 ? lo : lo + below * step + 1;
+        const int nhi = below == 8 ? hi : lo + (below + 1) * step;
+        lo = nlo;
+        hi = nhi;
+    }
+    for (int e0 = lo; e0 < hi; e0 += 8) {
+        int xs[8];
+#pragma unroll
+        for (int j = 0; j < 8; j++) xs[j] = e0 + j < hi ? __ldg(row + e0 + j) : -1;
+        bool hit = false;
+#pragma unroll
+        for (int j = 0; j < 8; j++) hit |= xs[j] == key;
+        if (hit) return true;
+    }
+    return false;
+}
+
+// The largest i in [lo, hi] with a[i] <= key, for a non-decreasing global
+// array with a[lo] <= key; eight probes a step as in kary_find.
+__device__ int kary_last_le(const int *a, int lo, int hi, int key)
+{
+    while (hi - lo >= 16) {
+        const int step = (hi - lo) / 9;        // >= 1
+        int xs[8];
+#pragma unroll
+        for (int j = 0; j < 8; j++) xs[j] = __ldg(a + lo + (j + 1) * step);
+        int le = 0;
+#pragma unroll
+        for (int j = 0; j < 8; j++) le += xs[j] <= key;
+        // probes 1..le hold, the rest do not: the answer lies in
+        // [lo + le * step, lo + (le + 1) * step - 1] (up to hi when all hold)
+        const int nhi = le == 8 ? hi : lo + (le + 1) * step - 1;
+        lo += le * step;
+        hi = nhi;
+    }
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(a + mid) <= key) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
 // Grid-stride checks of the CSR contract.  err[0] collects failures,
-// err[1] counts entries (v, u) with u > v.
+// err[1] counts entries (v, u) with u > v, err[2] is the maximum degree
+// (row length; meaningful only when the row pointers are valid).
 __global__ void validate_rowptr_kernel(int n, int m2, const int *rp, int *err)
 {
+    int dm = 0;
     for (int v = blockIdx.x * blockDim.x + threadIdx.x; v <= n; v += gridDim.x * blockDim.x) {
         int a = rp[v];
         bool bad = (v == 0 && a != 0) || (v == n && a != m2) || a < 0 || a > m2;
-        if (v < n && rp[v + 1] < a) bad = true;
+        if (v < n) {
+            const int b = rp[v + 1];
+            if (b < a) bad = true;
+            dm = max(dm, b - a);
+        }
         if (bad) atomicOr(err, 1);
     }
+    dm = __reduce_max_sync(kFull, dm);
+    if ((threadIdx.x & 31) == 0 && dm) atomicMax(err + 2, dm);
 }
 
 // One entry per thread (edge-parallel, so a hub's long row is spread over
@@ -59,19 +130,14 @@ __global__ void validate_col_kernel(int n, int m2, const int *rp, const int *col
     int up = 0;
     bool bad = false;
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < m2; e += gridDim.x * blockDim.x) {
-        // the row holding e: the largest v with rp[v] <= e
-        int lo = 0, hi = n - 1;
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (__ldg(rp + mid) <= e) lo = mid; else hi = mid - 1;
-        }
-        const int v = lo;
+        // the row holding e: the largest v with rp[v] <= e (rp[0] = 0)
+        const int v = kary_last_le(rp, 0, n - 1, e);
         const int u = __ldg(col + e);
         if (u < 0 || u >= n || u == v) { bad = true; continue; }
         if (e > __ldg(rp + v) && __ldg(col + e - 1) >= u) { bad = true; continue; }
         if (u > v) {
             up++;
-            if (!bsearch_row(col + __ldg(rp + u), __ldg(rp + u + 1) - __ldg(rp + u), v)) bad = true;
+            if (!kary_find(col + __ldg(rp + u), __ldg(rp + u + 1) - __ldg(rp + u), v)) bad = true;
         }
     }
     if (bad) atomicOr(err, 1);
@@ -1017,44 +1083,6 @@ struct ClusterRoot {
     __device__ __forceinline__ void mark(int u) { set_bit(markp(u >> cs, mbuf), u); }
     __device__ __forceinline__ void push_frontier(int x) { set_bit(flagp(x >> cs), x); }
 
-    // Is key in the sorted global row[0, len)?  Eight probes at a time: each
-    // step loads eight evenly spaced entries together (one round trip) and
-    // keeps the gap that can hold key, so a 2,000-entry row takes three
-    // steps and a short scan instead of eleven dependent loads.
-    __device__ static bool row_find(const int *row, int len, int key)
-    {
-        int lo = 0, hi = len;                      // key can only be in [lo, hi)
-        while (hi - lo > 16) {
-            const int step = (hi - lo) / 9;        // >= 1
-            int xs[8];
-#pragma unroll
-            for (int j = 0; j < 8; j++) xs[j] = __ldg(row + lo + (j + 1) * step);
-            int below = 0;
-            bool hit = false;
-#pragma unroll
-            for (int j = 0; j < 8; j++) {
-                below += xs[j] < key;
-                hit |= xs[j] == key;
-            }
-            if (hit) return true;
-            // the first `below` probes are < key, the rest > key
-            const int nlo = below == 0 ? lo : lo + below * step + 1;
-            const int nhi = below == 8 ? hi : lo + (below + 1) * step;
-            lo = nlo;
-            hi = nhi;
-        }
-        for (int e0 = lo; e0 < hi; e0 += 8) {
-            int xs[8];
-#pragma unroll
-            for (int j = 0; j < 8; j++) xs[j] = e0 + j < hi ? __ldg(row + e0 + j) : -1;
-            bool hit = false;
-#pragma unroll
-            for (int j = 0; j < 8; j++) hit |= xs[j] == key;
-            if (hit) return true;
-        }
-        return false;
-    }
-
     // Is u-w an edge?  The CSR is symmetric, so the shorter of the two rows
     // is searched.
     __device__ bool row_has(int u, int w) const
@@ -1062,7 +1090,7 @@ struct ClusterRoot {
         const int au = __ldg(rp + u), bu = __ldg(rp + u + 1);
         const int aw = __ldg(rp + w), bw = __ldg(rp + w + 1);
         const bool by_u = bu - au <= bw - aw;
-        return by_u ? row_find(col + au, bu - au, w) : row_find(col + aw, bw - aw, u);
+        return by_u ? kary_find(col + au, bu - au, w) : kary_find(col + aw, bw - aw, u);
     }
 
     // The degree-one rule at v (its only live neighbour u); the lower end of
@@ -2623,9 +2651,7 @@ cudaError_t validate_run(int n, int m2, const int *rp, const int *col, int *d_er
     if (n > 0) {
         const int eblocks = std::max(1, std::min(4096, (m2 + threads - 1) / threads));
         validate_col_kernel<<<eblocks, threads, 0, s>>>(n, m2, rp, col, d_err);
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
-        max_degree_kernel<<<blocks > 0 ? blocks : 1, threads, 0, s>>>(n, rp, d_err);
-        e = cudaGetLastError();
+        e = cudaGetLastError();   // (the row-pointer check also took the maximum degree)
     }
     return e;
 }
