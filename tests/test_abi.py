@@ -130,3 +130,34 @@ def test_server_config_default_without_gpu(lib):
 def test_trim_without_gpu(lib):
     # nothing pooled yet in this process: frees nothing and needs no device
     assert lib.lib().vc_trim() == 0
+
+
+def test_stats_dict_reads_every_field():
+    # the binding converts vc_stats with one struct unpack built from the
+    # ctypes layout; every field must come back as ctypes itself reads it
+    import random
+    from paper_2512_18334_gb300 import _lib as L
+    rng = random.Random(3)
+    for _ in range(20):
+        st = L.Stats()
+        for name, ct in L.Stats._fields_:
+            if issubclass(ct, ctypes.Array):
+                arr = getattr(st, name)
+                for i in range(ct._length_):
+                    arr[i] = rng.randrange(-2**40, 2**40) if ct._type_ is ctypes.c_int64 else rng.randrange(-2**31, 2**31)
+            elif ct is ctypes.c_double:
+                setattr(st, name, rng.uniform(-1e6, 1e6))
+            elif ct is ctypes.c_int64:
+                setattr(st, name, rng.randrange(-2**62, 2**62))
+            else:
+                setattr(st, name, rng.randrange(-2**31, 2**31))
+        d = st.to_dict()
+        for name, ct in L.Stats._fields_:
+            if name == "comp_hist":
+                assert d[name] == {i + 2: st.comp_hist[i] for i in range(16) if st.comp_hist[i]}
+            elif name == "root_cycles":
+                assert d[name] == list(st.root_cycles)
+            elif name == "phase_cycles":
+                assert d[name] == {L.PHASES[i]: st.phase_cycles[i] for i in range(6)}
+            else:
+                assert d[name] == getattr(st, name), name
