@@ -413,7 +413,10 @@ int solve_queries(vc_graph *g0, const std::vector<QueryRef> &qs, const vc_option
             key.hq = hq;
             key.nq = nq;
             key.max_n = max_n_in;
-            key.max_deg = max_deg_in;
+            // the root launches depend on the maximum degree only through
+            // this threshold (block kernel state and cluster eligibility), so
+            // graphs of one size share the captured phase
+            key.max_deg = max_deg_in > 65535 ? 1 : 0;
             key.crown = opt.crown ? 1 : 0;
             key.ev0 = ws.ev[0];
             key.ev1 = ws.ev[1];
